@@ -1,0 +1,454 @@
+"""Benchmark: FP64 SPC5 SpMV on one GB300 (or N independent replicas).
+
+Workload (FP64 plain SpMV over synthetic matrices, every beta(r,c) in
+{1x8, 2x4, 2x8, 4x4, 4x8, 8x4}):
+  - 3D 27-point stencil on 100^3 (n = 1e6, nnz = 26,463,592), values N(0,1)
+  - FEM-like 3x3 dense node blocks on a random-geometric mesh of 1e6 nodes
+    (n = 3e6, about 80 entries per row), Morton-ordered, values N(0,1)
+  - power-law row lengths (Zipf s = 2, mean 20, n = 2e6), columns near the
+    diagonal (sigma = 1000), values N(0,1)
+  - uniform-random columns, 16 per row (n = 1e6), values N(0,1)
+  x ~ U[-1, 1).  The matrices are converted once (timed separately); one
+  step = one y = A x for each of the 24 (matrix, beta) pairs.
+
+Reported: GFlop/s = 2 * nnz / time over the whole step (device-resident
+inputs, CUDA events on the launching stream), the HBM roofline of the SpMV
+kernel (algorithmic bytes = values + block column indices + masks + panel
+pointers + x + y, per launch, over the kernel's own event-timed duration),
+an end-to-end figure through the C-ABI with host vectors (pinned x and y
+copied every step), and the CPU oracle timed on the host cores on a
+bounded sample.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "SPC5 SpMV GFlop/s & HBM GB/s vs peak; FP64 vs FP32/BF16 at stated error"
+UNIT = "GFlop/s"
+BETAS = [(1, 8), (2, 4), (2, 8), (4, 4), (4, 8), (8, 4)]
+MATRICES = ["stencil27", "fem3d", "powerlaw", "uniform"]
+DESCR = {
+    "stencil27": "3D 27-point stencil 100^3 (n=1e6)",
+    "fem3d": "FEM 3x3 node blocks, random-geometric mesh, 1e6 nodes (n=3e6)",
+    "powerlaw": "power-law rows Zipf(2) mean 20, n=2e6, column sigma 1000",
+    "uniform": "uniform random columns, 16 per row, n=1e6",
+}
+SAMPLE_FRACTION = 16  # CPU baseline / reference arm: first 1/16 of each matrix's rows
+L2_BYTES = 129 * 1024 * 1024
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--matrices", default=",".join(MATRICES))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cases-out", default=None, help="write the per-case table here")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def algorithmic_bytes(info: dict) -> int:
+    """Bytes an FP64 SpMV must move: values + block column indices + masks +
+    panel pointers (block_rowptr and panel value offsets) + x + y."""
+    nb, npan = info["nblocks"], info["npanels"]
+    return (8 * info["nnz"] + 4 * nb + info["mask_bytes"] * nb + 8 * (npan + 1)
+            + 8 * info["ncols"] + 8 * info["nrows"])
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for name in ("spc5_spmv.cu",):
+        with open(os.path.join(ROOT, "paper_2307_14774_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic():
+    """DRAM bytes per SpMV launch from the committed ncu summary, if it was
+    taken on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "spc5_spmv_dram.txt")
+    if not os.path.exists(path):
+        return None
+    src, per_case = None, {}
+    for line in open(path):
+        line = line.strip()
+        if line.startswith("source_sha256:"):
+            src = line.split(":", 1)[1].strip()
+        elif line and not line.startswith("#") and line.count(" ") >= 2 and "=" not in line:
+            parts = line.split()
+            if len(parts) >= 3 and parts[0] in MATRICES:
+                try:
+                    per_case[(parts[0], parts[1])] = float(parts[2])
+                except ValueError:
+                    pass
+    if src != kernel_source_hash() or not per_case:
+        return None
+    return per_case
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return None
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ native --
+
+def build_cases(names, torch, spc5, synth, log):
+    """Generate, upload and convert every (matrix, beta); return cases and
+    the host matrices (kept for the CPU baseline sample)."""
+    cases, hosts = [], {}
+    for name in names:
+        t0 = time.time()
+        A = synth.workload(name, "full")
+        x = synth.vector_uniform(A.ncols, seed=1)
+        hosts[name] = (A, x)
+        log(f"generated {name}: n={A.nrows} nnz={A.nnz} in {time.time() - t0:.1f}s")
+        dev = [torch.from_numpy(a).cuda() for a in (A.rowptr, A.colidx, A.vals)]
+        dx = torch.from_numpy(x).cuda()
+        dy = torch.empty(A.nrows, dtype=torch.float64, device="cuda")
+        for r, c in BETAS:
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            M = spc5.spc5_convert_csr(A.nrows, A.ncols, A.nnz, *dev, r=r, c=c)
+            t_conv = time.perf_counter() - t1
+            info = M.info()
+            cases.append({"matrix": name, "r": r, "c": c, "M": M, "x": dx, "y": dy,
+                          "info": info, "bytes": algorithmic_bytes(info), "nnz": A.nnz,
+                          "convert_s": t_conv})
+        del dev
+        torch.cuda.synchronize()
+    return cases, hosts
+
+
+def cpu_baseline_sample(hosts, oracle, log):
+    """Algorithm 1 (the oracle's scalar path) on the first 1/16 of every
+    matrix's rows, every beta; one host thread.  Returns GFlop/s and the
+    description of the sample."""
+    import numpy as np
+    total_flops, total_time = 0.0, 0.0
+    for name, (A, x) in hosts.items():
+        nrows = max(8, (A.nrows // SAMPLE_FRACTION) // 8 * 8)
+        end = int(A.rowptr[nrows])
+
+        import synth
+        sub = synth.CSR(nrows, A.ncols, np.ascontiguousarray(A.rowptr[:nrows + 1]),
+                        np.ascontiguousarray(A.colidx[:end]), np.ascontiguousarray(A.vals[:end]))
+        for r, c in BETAS:
+            S = oracle.convert(sub, r, c)
+            t0 = time.perf_counter()
+            oracle.spc5_spmv(S, x)
+            total_time += time.perf_counter() - t0
+            total_flops += 2.0 * end
+    log(f"cpu baseline: {total_flops / 2:.3g} nnz in {total_time:.2f}s")
+    return total_flops / total_time / 1e9, total_time
+
+
+def run_native(args):
+    import numpy as np
+    import torch
+
+    import paper_2307_14774_gb300 as spc5
+    import synth
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    log = (lambda m: print(f"[bench] {m}", file=sys.stderr, flush=True)) if rank == 0 else (
+        lambda m: None)
+    spc5.load()
+    names = [n for n in args.matrices.split(",") if n]
+    cases, hosts = build_cases(names, torch, spc5, synth, log)
+    stream = torch.cuda.current_stream()
+    nlaunch = len(cases)
+
+    def step(events=None):
+        for i, cs in enumerate(cases):
+            if events is not None:
+                events[i][0].record(stream)
+            spc5.spc5_spmv(cs["M"], cs["x"], cs["y"], 1.0, 0.0, stream)
+            if events is not None:
+                events[i][1].record(stream)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    ev = [[[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)]
+           for _ in cases] for _ in range(args.steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        time.sleep(0.3)
+        t_start.record(stream)
+        for k in range(args.steps):
+            step(ev[k])
+        t_end.record(stream)
+        torch.cuda.synchronize()
+        time.sleep(0.3)
+    if world > 1:
+        torch.distributed.barrier()
+    total_ms = t_start.elapsed_time(t_end)
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    flops_per_step = sum(2.0 * cs["nnz"] for cs in cases)
+    value = world * flops_per_step / (ms_per_step * 1e-3) / 1e9
+
+    # per-launch durations (CUDA events on the launching stream)
+    per_case_ms = [statistics.median(ev[k][i][0].elapsed_time(ev[k][i][1])
+                                     for k in range(args.steps)) for i in range(nlaunch)]
+    sum_launch_ms = sum(sum(ev[k][i][0].elapsed_time(ev[k][i][1]) for i in range(nlaunch))
+                        for k in range(args.steps))
+    bytes_per_step = sum(cs["bytes"] for cs in cases)
+    hbm, peak_kind = measured_peaks()
+    achieved = bytes_per_step * args.steps / (sum_launch_ms * 1e-3) / 1e9
+    launches_per_spmv = max(cs["info"].get("launches_per_spmv", 1) for cs in cases)
+    traffic_tab = ncu_traffic()
+    traffic = None
+    if traffic_tab:
+        vals = [traffic_tab.get((cs["matrix"], f"{cs['r']}x{cs['c']}")) for cs in cases]
+        if all(v is not None for v in vals):
+            traffic = sum(vals) / len(vals)
+    case_rows = []
+    for cs, ms in zip(cases, per_case_ms):
+        gbs = cs["bytes"] / (ms * 1e-3) / 1e9
+        case_rows.append({"matrix": cs["matrix"], "beta": f"{cs['r']}x{cs['c']}",
+                          "nnz": cs["nnz"], "nblocks": cs["info"]["nblocks"],
+                          "filling": round(cs["info"]["filling"], 4),
+                          "us": round(ms * 1e3, 2),
+                          "gflops": round(2.0 * cs["nnz"] / (ms * 1e-3) / 1e9, 1),
+                          "gbs": round(gbs, 1), "frac": round(gbs / hbm, 3),
+                          "convert_ms": round(cs["convert_s"] * 1e3, 2)})
+
+    result = {
+        "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": max(args.warmup, 3),
+        "ms_per_step": round(ms_per_step, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "FP64 SpMV, every beta(r,c) in {1x8,2x4,2x8,4x4,4x8,8x4}, over: "
+                   + "; ".join(DESCR[n] for n in names),
+                   "matrices": names, "betas": [f"{r}x{c}" for r, c in BETAS],
+                   "spmv_per_step": nlaunch, "nnz_per_step": int(flops_per_step / 2),
+                   "l2": "inputs larger than L2: every SpMV streams >= "
+                         f"{min(cs['bytes'] for cs in cases) / 1e6:.0f} MB (L2 129 MB)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm,
+                     "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": traffic,
+                     "peak_kind": peak_kind,
+                     "kernel": "spc5 SpMV kernel, all 24 launches of a step",
+                     "bytes_per_step": bytes_per_step},
+        "gpu_launches": nlaunch * launches_per_spmv * args.steps,
+        "cases": case_rows,
+        "convert": {"ms_total": round(sum(cs["convert_s"] for cs in cases) * 1e3, 1),
+                    "note": "CSR (device) -> beta(r,c), all 24 conversions, wall clock"},
+    }
+    clocks = clk.summary()
+    if clocks:
+        result["clocks"] = clocks
+
+    # end to end through the C-ABI with host vectors: every step copies x from
+    # pinned host memory and reads y back
+    if not args.no_e2e:
+        hx, hy = {}, {}
+        for name in names:
+            A, x = hosts[name]
+            hx[name] = torch.from_numpy(x).pin_memory()
+            hy[name] = torch.empty(A.nrows, dtype=torch.float64).pin_memory()
+        h2d = sum(8 * cs["info"]["ncols"] for cs in cases)
+        d2h = sum(8 * cs["info"]["nrows"] for cs in cases)
+
+        def e2e_step():
+            for cs in cases:
+                spc5.spc5_spmv(cs["M"], hx[cs["matrix"]], hy[cs["matrix"]], 1.0, 0.0, stream)
+
+        for _ in range(3):
+            e2e_step()
+        if world > 1:
+            torch.distributed.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            e2e_step()
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / args.steps
+        if world > 1:
+            t = torch.tensor([dt], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            dt = float(t.item())
+        result["e2e"] = {"value": round(world * flops_per_step / dt / 1e9, 2), "unit": UNIT,
+                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                         "ms_per_step": round(dt * 1e3, 3),
+                         "api": "spc5_spmv with pinned host x and y"}
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        gf, secs = cpu_baseline_sample(hosts, oracle, log)
+        result["cpu_baseline"] = {
+            "value": round(gf, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"Algorithm 1 (oracle scalar path) on the first 1/{SAMPLE_FRACTION} of the "
+                      f"rows of each matrix, every beta, one host thread ({secs:.1f} s)"}
+    if args.cases_out and rank == 0:
+        with open(args.cases_out, "w") as f:
+            json.dump(case_rows, f, indent=1)
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+# --------------------------------------------------------------- reference --
+
+def run_reference(args):
+    """The oracle timed on the host cores: each step runs Algorithm 1 on a
+    bounded sample (first 1/16 of the rows of every matrix, every beta)."""
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+    import synth
+    names = [n for n in args.matrices.split(",") if n]
+    samples = []
+    for name in names:
+        A = synth.workload(name, "full")
+        x = synth.vector_uniform(A.ncols, seed=1)
+        nrows = max(8, (A.nrows // SAMPLE_FRACTION) // 8 * 8)
+        end = int(A.rowptr[nrows])
+        sub = synth.CSR(nrows, A.ncols, np.ascontiguousarray(A.rowptr[:nrows + 1]),
+                        np.ascontiguousarray(A.colidx[:end]),
+                        np.ascontiguousarray(A.vals[:end]))
+        for r, c in BETAS:
+            samples.append((oracle.convert(sub, r, c), x, end))
+        del A
+
+    def step():
+        for S, x, _ in samples:
+            oracle.spc5_spmv(S, x)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = (time.perf_counter() - t0) / args.steps
+    flops = sum(2.0 * nnz for _, _, nnz in samples)
+    value = flops / dt / 1e9
+    sample = (f"Algorithm 1 (CPU oracle, FP64, one host thread) on the first 1/{SAMPLE_FRACTION} "
+              f"of the rows of each matrix, every beta")
+    result = {
+        "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "impl": "reference",
+        "config": {"workload": "FP64 SpMV, every beta(r,c) in {1x8,2x4,2x8,4x4,4x8,8x4}, over: "
+                   + "; ".join(DESCR[n] for n in names), "matrices": names,
+                   "sample_rows_fraction": f"1/{SAMPLE_FRACTION}"},
+        "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(result), flush=True)
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_native(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,152 @@
+/*
+ * spc5.h -- C ABI of the GB300 SPC5 library.
+ *
+ * SPC5 (Regnault & Bramas, "SPC5: an efficient SpMV framework vectorized
+ * using ARM SVE and x86 AVX-512") stores a sparse matrix in the beta(r,c)
+ * block format (Section 2.4): rows are grouped into panels of r rows; each
+ * block of a panel holds one start column and r masks of c bits (bit k of
+ * row q set <=> the entry at column start + k of that row exists); only the
+ * nonzeros are stored, packed in the order in which Algorithm 1 visits them
+ * (block by block, row by row, ascending bit).  y = A x over that format is
+ * Algorithm 1.
+ *
+ * Conventions for every entry point:
+ *   - Sizes and indices are 64-bit in the signatures; the stored matrix uses
+ *     32-bit indices, so nrows, ncols, nnz and the number of blocks must stay
+ *     below 2^31 (else SPC5_EOVERFLOW).
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *     stream).  Work is enqueued on it.
+ *   - Array arguments may live in device memory or in host memory; the
+ *     library asks the CUDA runtime which one (cudaPointerGetAttributes).
+ *     Host arguments are copied through device buffers and make the call
+ *     blocking.
+ *   - No call throws, aborts or uses a device fault to report an error: every
+ *     failure is a returned spc5_status, and spc5_last_error() gives a
+ *     one-line description of the last failure on the calling thread.
+ *   - Layouts are C order; all arrays are borrowed (never freed or kept)
+ *     unless stated otherwise.
+ */
+#ifndef SPC5_H
+#define SPC5_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Opaque handle of a matrix converted to beta(r,c); owns its device arrays. */
+typedef struct spc5_matrix spc5_matrix;
+
+/* Element types.  Values may be stored in FP64 (the default); FP32 and BF16
+ * storage are reserved and currently return SPC5_EUNSUPPORTED. */
+typedef enum { SPC5_F64 = 0, SPC5_F32 = 1, SPC5_BF16 = 2 } spc5_dtype;
+
+typedef enum {
+  SPC5_OK = 0,
+  SPC5_EINVAL = 1,          /* null handle or pointer, negative size, bad alpha/beta use */
+  SPC5_EUNSORTED = 2,       /* a row's column indices are not strictly ascending */
+  SPC5_EUNSUPPORTED_RC = 3, /* (r, c) is not a supported block shape */
+  SPC5_EOVERFLOW = 4,       /* a size does not fit 32-bit indexing */
+  SPC5_ECUDA = 5,           /* a CUDA runtime call failed */
+  SPC5_ENOMEM = 6,          /* a device or pinned-host allocation failed */
+  SPC5_EDEVICE = 7,         /* a kernel reported an internal inconsistency */
+  SPC5_ERANGE = 8,          /* a column index lies outside [0, ncols) */
+  SPC5_EROWPTR = 9,         /* rowptr[0] != 0, rowptr decreasing, or rowptr[nrows] != nnz */
+  SPC5_EUNSUPPORTED = 10    /* a requested option or dtype is not implemented */
+} spc5_status;
+
+/* Description of a converted matrix. */
+typedef struct {
+  int64_t nrows, ncols, nnz;
+  int32_t r, c;            /* block shape beta(r,c) */
+  int64_t npanels;         /* ceil(nrows / r) */
+  int64_t nblocks;         /* number of blocks */
+  double filling;          /* nnz / (nblocks * r * c): Table 1's block filling */
+  spc5_dtype value_dtype;  /* storage type of the values */
+  int32_t mask_bytes;      /* bytes of one block's packed mask word: r * c / 8 */
+  int64_t device_bytes;    /* device memory held by the handle */
+  int32_t device;          /* CUDA device ordinal the matrix lives on */
+  int32_t lanes_per_row;   /* SpMV mapping chosen for this matrix (1, 2, 4, ...) */
+} spc5_info;
+
+/*
+ * spc5_convert_csr -- build beta(r,c) from CSR (Section 2.4).
+ *
+ * Block rule: within each panel of r consecutive rows (the last panel may be
+ * shorter), the smallest column of the rows' union that no block covers yet
+ * opens a block covering columns [start, start + c) in all r rows; blocks
+ * are ordered by ascending start.  For r = 1 this is the paper's rule that a
+ * block starts at a nonzero and takes the next nonzeros up to start + c - 1.
+ *
+ * nrows, ncols, nnz  matrix shape and number of stored entries
+ * rowptr[nrows+1]    CSR row pointers, rowptr[0] = 0, rowptr[nrows] = nnz
+ * colidx[nnz]        column of every entry, strictly ascending in each row
+ * vals[nnz]          values of type vals_dtype (only SPC5_F64 is accepted)
+ * store_dtype        storage type of the converted values (SPC5_F64)
+ * r, c               block shape; (1,8) (2,4) (2,8) (4,4) (4,8) (8,4) are
+ *                    supported, others give SPC5_EUNSUPPORTED_RC
+ * stream             stream the conversion runs on; the call returns after
+ *                    the conversion has finished (it reads back the block
+ *                    count to size the arrays)
+ * out                receives the new handle (unchanged on failure)
+ *
+ * Validation (sorted unique columns, column range, row pointers) runs on
+ * the device before any index is trusted.  Explicitly stored zeros are kept.
+ */
+spc5_status spc5_convert_csr(int64_t nrows, int64_t ncols, int64_t nnz, const int32_t *rowptr,
+                             const int32_t *colidx, const void *vals, spc5_dtype vals_dtype,
+                             spc5_dtype store_dtype, int r, int c, void *stream,
+                             spc5_matrix **out);
+
+/* Fill *info with the matrix description (host-only, no device work). */
+spc5_status spc5_matrix_info(const spc5_matrix *A, spc5_info *info);
+
+/*
+ * spc5_export -- device pointers to the converted arrays (owned by A, valid
+ * until spc5_destroy).  Any output pointer may be NULL.
+ *   block_rowptr[npanels+1] int32  first block of each panel (Algorithm 1's
+ *                                  mat.block_rowptr)
+ *   panel_vptr[npanels+1]   int32  offset of each panel's first value (equal
+ *                                  to the CSR row pointer of the panel's first
+ *                                  row); lets a panel be processed without
+ *                                  summing the popcounts of all earlier blocks
+ *   block_colidx[nblocks]   int32  start column of each block (idxCol)
+ *   block_masks[nblocks]           one little-endian word of r*c bits per
+ *                                  block (uint8 for r*c = 8, uint16 for 16,
+ *                                  uint32 for 32), row q at bits [q*c, (q+1)*c):
+ *                                  for c = 8 the bytes equal the paper's
+ *                                  block_masks[idxBlock * r + idxRowBlock]
+ *   values[nnz]                    packed values in Algorithm 1's idxVal order
+ */
+spc5_status spc5_export(const spc5_matrix *A, const int32_t **block_rowptr,
+                        const int32_t **panel_vptr, const int32_t **block_colidx,
+                        const void **block_masks, const void **values);
+
+/*
+ * spc5_spmv -- y = alpha * A x + beta * y (Algorithm 1 computes y = A x).
+ *
+ * x[ncols], y[nrows] are FP64 vectors in device or host memory.  With
+ * beta == 0, y is not read (no NaN or Inf from a previous y propagates).
+ * Device vectors: asynchronous on `stream`.  Host vectors: copied through
+ * device buffers owned by A; the call returns when y is on the host.  x and y
+ * must not overlap.  Concurrent calls on the same handle with host vectors
+ * must be serialised by the caller.
+ */
+spc5_status spc5_spmv(const spc5_matrix *A, const double *x, double *y, double alpha,
+                      double beta, void *stream);
+
+/* Release the handle and every device array it owns (synchronising). */
+spc5_status spc5_destroy(spc5_matrix *A);
+
+/* Static name of a status code. */
+const char *spc5_status_str(spc5_status s);
+
+/* One-line description of the last failure on the calling thread ("" if none). */
+const char *spc5_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPC5_H */

@@ -1,0 +1,261 @@
+// C-ABI entry points: argument checks, host/device pointer handling, and
+// the lifetime of spc5_matrix handles.  The arithmetic lives in
+// spc5_convert.cu and spc5_spmv.cu.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdlib.h>
+
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "spc5_internal.h"
+
+namespace spc5 {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+spc5_status cuda_check(cudaError_t e, const char *what) {
+  if (e == cudaSuccess) return SPC5_OK;
+  set_error(std::string(what) + ": " + cudaGetErrorString(e));
+  if (e == cudaErrorMemoryAllocation) return SPC5_ENOMEM;
+  return SPC5_ECUDA;
+}
+
+bool supported_rc(int r, int c) {
+  return (r == 1 && c == 8) || (r == 2 && c == 4) || (r == 2 && c == 8) || (r == 4 && c == 4) ||
+         (r == 4 && c == 8) || (r == 8 && c == 4);
+}
+
+namespace {
+
+// True when `p` is host memory (pageable or pinned), false when the device
+// can read it directly (device or managed memory).
+bool is_host_pointer(const void *p) {
+  cudaPointerAttributes attr;
+  cudaError_t e = cudaPointerGetAttributes(&attr, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();  // clear the sticky-free error of an unknown pointer
+    return true;
+  }
+  return attr.type == cudaMemoryTypeUnregistered || attr.type == cudaMemoryTypeHost;
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+void free_matrix(spc5_matrix *A) {
+  if (!A) return;
+  DeviceGuard g(A->device);
+  cudaFree(A->block_rowptr);
+  cudaFree(A->panel_vptr);
+  cudaFree(A->block_colidx);
+  cudaFree(A->masks);
+  cudaFree(A->values);
+  cudaFree(A->x_stage);
+  cudaFree(A->y_stage);
+  delete A;
+}
+
+int default_log2_lanes(const spc5_matrix *A) {
+  const char *env = getenv("SPC5_LOG2_LANES_PER_ROW");
+  if (env && *env) {
+    int v = atoi(env);
+    if (v >= 0 && v <= 5) return v;
+  }
+  return 0;
+}
+
+}  // namespace
+}  // namespace spc5
+
+using namespace spc5;
+
+#define RETURN_IF(cond, code, msg) \
+  do {                             \
+    if (cond) {                    \
+      set_error(msg);              \
+      return (code);               \
+    }                              \
+  } while (0)
+
+extern "C" {
+
+const char *spc5_status_str(spc5_status s) {
+  switch (s) {
+    case SPC5_OK: return "SPC5_OK";
+    case SPC5_EINVAL: return "SPC5_EINVAL";
+    case SPC5_EUNSORTED: return "SPC5_EUNSORTED";
+    case SPC5_EUNSUPPORTED_RC: return "SPC5_EUNSUPPORTED_RC";
+    case SPC5_EOVERFLOW: return "SPC5_EOVERFLOW";
+    case SPC5_ECUDA: return "SPC5_ECUDA";
+    case SPC5_ENOMEM: return "SPC5_ENOMEM";
+    case SPC5_EDEVICE: return "SPC5_EDEVICE";
+    case SPC5_ERANGE: return "SPC5_ERANGE";
+    case SPC5_EROWPTR: return "SPC5_EROWPTR";
+    case SPC5_EUNSUPPORTED: return "SPC5_EUNSUPPORTED";
+  }
+  return "SPC5_UNKNOWN";
+}
+
+const char *spc5_last_error(void) { return g_last_error.c_str(); }
+
+spc5_status spc5_convert_csr(int64_t nrows, int64_t ncols, int64_t nnz, const int32_t *rowptr,
+                             const int32_t *colidx, const void *vals, spc5_dtype vals_dtype,
+                             spc5_dtype store_dtype, int r, int c, void *stream,
+                             spc5_matrix **out) {
+  g_last_error.clear();
+  RETURN_IF(!out, SPC5_EINVAL, "out is NULL");
+  RETURN_IF(nrows < 0 || ncols < 0 || nnz < 0, SPC5_EINVAL, "negative size");
+  RETURN_IF(!rowptr, SPC5_EINVAL, "rowptr is NULL");
+  RETURN_IF(nnz > 0 && (!colidx || !vals), SPC5_EINVAL, "colidx or vals is NULL");
+  RETURN_IF(!supported_rc(r, c), SPC5_EUNSUPPORTED_RC,
+            "block shape must be one of (1,8) (2,4) (2,8) (4,4) (4,8) (8,4)");
+  RETURN_IF(nrows >= INT32_MAX || ncols >= INT32_MAX || nnz >= INT32_MAX, SPC5_EOVERFLOW,
+            "sizes must stay below 2^31");
+  RETURN_IF(vals_dtype != SPC5_F64 || store_dtype != SPC5_F64, SPC5_EUNSUPPORTED,
+            "only FP64 values are implemented");
+  cudaStream_t s = (cudaStream_t)stream;
+
+  spc5_matrix *A = new (std::nothrow) spc5_matrix();
+  RETURN_IF(!A, SPC5_ENOMEM, "host allocation failed");
+  A->nrows = nrows;
+  A->ncols = ncols;
+  A->nnz = nnz;
+  A->r = r;
+  A->c = c;
+  A->npanels = (nrows + r - 1) / r;
+  A->value_dtype = store_dtype;
+  spc5_status st = cuda_check(cudaGetDevice(&A->device), "cudaGetDevice");
+  if (st != SPC5_OK) {
+    delete A;
+    return st;
+  }
+
+  // Host inputs are staged through temporary device copies.
+  const int32_t *d_rowptr = rowptr, *d_colidx = colidx;
+  const double *d_vals = (const double *)vals;
+  void *tmp[3] = {nullptr, nullptr, nullptr};
+  auto stage = [&](const void *src, size_t bytes, int slot, const void **dst) -> spc5_status {
+    if (!src || !is_host_pointer(src)) return SPC5_OK;
+    spc5_status e = cuda_check(cudaMallocAsync(&tmp[slot], bytes > 0 ? bytes : 4, s), "alloc staging");
+    if (e != SPC5_OK) return e;
+    e = cuda_check(cudaMemcpyAsync(tmp[slot], src, bytes, cudaMemcpyHostToDevice, s), "copy CSR");
+    if (e != SPC5_OK) return e;
+    *dst = tmp[slot];
+    return SPC5_OK;
+  };
+  st = stage(rowptr, (size_t)(nrows + 1) * sizeof(int32_t), 0, (const void **)&d_rowptr);
+  if (st == SPC5_OK && nnz > 0)
+    st = stage(colidx, (size_t)nnz * sizeof(int32_t), 1, (const void **)&d_colidx);
+  if (st == SPC5_OK && nnz > 0)
+    st = stage(vals, (size_t)nnz * sizeof(double), 2, (const void **)&d_vals);
+  if (st == SPC5_OK) st = convert_device(A, d_rowptr, d_colidx, d_vals, s);
+  for (void *p : tmp)
+    if (p) cudaFreeAsync(p, s);
+  if (st == SPC5_OK) st = cuda_check(cudaStreamSynchronize(s), "sync conversion");
+  if (st != SPC5_OK) {
+    free_matrix(A);
+    return st;
+  }
+  A->log2_lanes_per_row = default_log2_lanes(A);
+  *out = A;
+  return SPC5_OK;
+}
+
+spc5_status spc5_matrix_info(const spc5_matrix *A, spc5_info *info) {
+  RETURN_IF(!A || !info, SPC5_EINVAL, "NULL argument");
+  std::memset(info, 0, sizeof(*info));
+  info->nrows = A->nrows;
+  info->ncols = A->ncols;
+  info->nnz = A->nnz;
+  info->r = A->r;
+  info->c = A->c;
+  info->npanels = A->npanels;
+  info->nblocks = A->nblocks;
+  info->filling = A->nblocks ? (double)A->nnz / ((double)A->nblocks * A->r * A->c) : 0.0;
+  info->value_dtype = A->value_dtype;
+  info->mask_bytes = A->r * A->c / 8;
+  info->device_bytes = A->device_bytes;
+  info->device = A->device;
+  info->lanes_per_row = 1 << A->log2_lanes_per_row;
+  return SPC5_OK;
+}
+
+spc5_status spc5_export(const spc5_matrix *A, const int32_t **block_rowptr,
+                        const int32_t **panel_vptr, const int32_t **block_colidx,
+                        const void **block_masks, const void **values) {
+  RETURN_IF(!A, SPC5_EINVAL, "NULL handle");
+  if (block_rowptr) *block_rowptr = A->block_rowptr;
+  if (panel_vptr) *panel_vptr = A->panel_vptr;
+  if (block_colidx) *block_colidx = A->block_colidx;
+  if (block_masks) *block_masks = A->masks;
+  if (values) *values = A->values;
+  return SPC5_OK;
+}
+
+spc5_status spc5_spmv(const spc5_matrix *A, const double *x, double *y, double alpha,
+                      double beta, void *stream) {
+  RETURN_IF(!A, SPC5_EINVAL, "NULL handle");
+  RETURN_IF((A->ncols > 0 && !x) || (A->nrows > 0 && !y), SPC5_EINVAL, "NULL vector");
+  cudaStream_t s = (cudaStream_t)stream;
+  DeviceGuard guard(A->device);
+  const bool host_x = A->ncols > 0 && is_host_pointer(x);
+  const bool host_y = A->nrows > 0 && is_host_pointer(y);
+  if (!host_x && !host_y) return spmv_device(A, x, y, alpha, beta, s);
+
+  spc5_matrix *M = const_cast<spc5_matrix *>(A);
+  spc5_status st = SPC5_OK;
+  if (host_x && !M->x_stage)
+    st = cuda_check(cudaMalloc((void **)&M->x_stage, (size_t)A->ncols * sizeof(double) + 16),
+                    "alloc x staging");
+  if (st == SPC5_OK && host_y && !M->y_stage)
+    st = cuda_check(cudaMalloc((void **)&M->y_stage, (size_t)A->nrows * sizeof(double) + 16),
+                    "alloc y staging");
+  if (st != SPC5_OK) return st;
+  const double *dx = x;
+  double *dy = y;
+  if (host_x) {
+    st = cuda_check(cudaMemcpyAsync(M->x_stage, x, (size_t)A->ncols * sizeof(double),
+                                    cudaMemcpyHostToDevice, s),
+                    "copy x");
+    if (st != SPC5_OK) return st;
+    dx = M->x_stage;
+  }
+  if (host_y) {
+    if (beta != 0.0) {
+      st = cuda_check(cudaMemcpyAsync(M->y_stage, y, (size_t)A->nrows * sizeof(double),
+                                      cudaMemcpyHostToDevice, s),
+                      "copy y");
+      if (st != SPC5_OK) return st;
+    }
+    dy = M->y_stage;
+  }
+  st = spmv_device(A, dx, dy, alpha, beta, s);
+  if (st != SPC5_OK) return st;
+  if (host_y) {
+    st = cuda_check(cudaMemcpyAsync(y, dy, (size_t)A->nrows * sizeof(double),
+                                    cudaMemcpyDeviceToHost, s),
+                    "copy y back");
+    if (st != SPC5_OK) return st;
+  }
+  return cuda_check(cudaStreamSynchronize(s), "sync spmv");
+}
+
+spc5_status spc5_destroy(spc5_matrix *A) {
+  if (!A) return SPC5_OK;
+  free_matrix(A);
+  return SPC5_OK;
+}
+
+}  // extern "C"

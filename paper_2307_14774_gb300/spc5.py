@@ -1,0 +1,220 @@
+"""Thin ctypes binding of libspc5.so: the C-ABI names, argument marshalling
+only.  Every step of the conversion and of the product runs in the
+library's CUDA kernels; there is no Python or CPU fallback.  If the library
+is missing or fails to load, import raises.
+
+Tensors are torch CUDA tensors (torch provides device memory and streams)
+or host arrays (numpy or CPU tensors), passed by pointer.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+SPC5_F64, SPC5_F32, SPC5_BF16 = 0, 1, 2
+STATUS = {0: "SPC5_OK", 1: "SPC5_EINVAL", 2: "SPC5_EUNSORTED", 3: "SPC5_EUNSUPPORTED_RC",
+          4: "SPC5_EOVERFLOW", 5: "SPC5_ECUDA", 6: "SPC5_ENOMEM", 7: "SPC5_EDEVICE",
+          8: "SPC5_ERANGE", 9: "SPC5_EROWPTR", 10: "SPC5_EUNSUPPORTED"}
+SUPPORTED_RC = ((1, 8), (2, 4), (2, 8), (4, 4), (4, 8), (8, 4))
+
+# Exported symbols declared in include/spc5.h.
+EXPORTS = ("spc5_convert_csr", "spc5_matrix_info", "spc5_export", "spc5_spmv", "spc5_destroy",
+           "spc5_status_str", "spc5_last_error")
+
+
+class SPC5Error(RuntimeError):
+    def __init__(self, code: int, detail: str = ""):
+        super().__init__(f"{STATUS.get(code, code)}: {detail}")
+        self.code = code
+        self.name = STATUS.get(code, str(code))
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("nrows", ctypes.c_int64), ("ncols", ctypes.c_int64), ("nnz", ctypes.c_int64),
+                ("r", ctypes.c_int32), ("c", ctypes.c_int32), ("npanels", ctypes.c_int64),
+                ("nblocks", ctypes.c_int64), ("filling", ctypes.c_double),
+                ("value_dtype", ctypes.c_int), ("mask_bytes", ctypes.c_int32),
+                ("device_bytes", ctypes.c_int64), ("device", ctypes.c_int32),
+                ("lanes_per_row", ctypes.c_int32)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB_PATH
+
+
+def load(path: str | None = None):
+    """Load (building first if needed) libspc5.so and declare its signatures."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if path is None:
+            path = _build.build() if not _build.up_to_date() else _build.LIB_PATH
+        if not os.path.exists(path):
+            raise ImportError(f"libspc5.so not found at {path}")
+        lib = ctypes.CDLL(path)
+        vp, i64, ci, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+        lib.spc5_convert_csr.argtypes = [i64, i64, i64, vp, vp, vp, ci, ci, ci, ci, vp,
+                                         ctypes.POINTER(vp)]
+        lib.spc5_matrix_info.argtypes = [vp, ctypes.POINTER(Info)]
+        lib.spc5_export.argtypes = [vp] + [ctypes.POINTER(vp)] * 5
+        lib.spc5_spmv.argtypes = [vp, vp, vp, dbl, dbl, vp]
+        lib.spc5_destroy.argtypes = [vp]
+        for f in (lib.spc5_convert_csr, lib.spc5_matrix_info, lib.spc5_export, lib.spc5_spmv,
+                  lib.spc5_destroy):
+            f.restype = ci
+        lib.spc5_status_str.argtypes = [ci]
+        lib.spc5_status_str.restype = ctypes.c_char_p
+        lib.spc5_last_error.argtypes = []
+        lib.spc5_last_error.restype = ctypes.c_char_p
+        _lib = lib
+        return lib
+
+
+def _check(rc: int):
+    if rc != 0:
+        detail = load().spc5_last_error().decode(errors="replace")
+        raise SPC5Error(rc, detail)
+
+
+def _ptr(a) -> int | None:
+    """Raw address of a torch tensor or numpy array (None for None)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _stream_ptr(stream) -> int | None:
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except ImportError:
+            pass
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+class Matrix:
+    """Owning wrapper of an spc5_matrix handle."""
+
+    def __init__(self, handle: int, keepalive=()):
+        self._h = ctypes.c_void_p(handle)
+        self._keep = keepalive
+
+    @property
+    def handle(self) -> ctypes.c_void_p:
+        if not self._h:
+            raise ValueError("matrix has been destroyed")
+        return self._h
+
+    def info(self) -> dict:
+        return spc5_matrix_info(self)
+
+    def __del__(self):
+        try:
+            if self._h:
+                load().spc5_destroy(self._h)
+                self._h = ctypes.c_void_p(None)
+        except Exception:
+            pass
+
+
+def spc5_convert_csr(nrows, ncols, nnz, rowptr, colidx, vals, vals_dtype=SPC5_F64,
+                     store_dtype=SPC5_F64, r=4, c=8, stream=None) -> Matrix:
+    """CSR -> beta(r,c) on the GPU; arrays in device or host memory."""
+    lib = load()
+    out = ctypes.c_void_p()
+    _check(lib.spc5_convert_csr(nrows, ncols, nnz, _ptr(rowptr), _ptr(colidx), _ptr(vals),
+                                vals_dtype, store_dtype, r, c, _stream_ptr(stream),
+                                ctypes.byref(out)))
+    return Matrix(out.value)
+
+
+def spc5_matrix_info(A: Matrix) -> dict:
+    info = Info()
+    _check(load().spc5_matrix_info(A.handle, ctypes.byref(info)))
+    return {name: getattr(info, name) for name, _ in Info._fields_}
+
+
+def spc5_export(A: Matrix) -> dict:
+    """Device pointers of the converted arrays (owned by A)."""
+    ptrs = [ctypes.c_void_p() for _ in range(5)]
+    _check(load().spc5_export(A.handle, *[ctypes.byref(p) for p in ptrs]))
+    names = ("block_rowptr", "panel_vptr", "block_colidx", "block_masks", "values")
+    return {n: p.value for n, p in zip(names, ptrs)}
+
+
+def spc5_spmv(A: Matrix, x, y, alpha: float = 1.0, beta: float = 0.0, stream=None) -> None:
+    """y = alpha * A x + beta * y (FP64 vectors, device or host)."""
+    _check(load().spc5_spmv(A.handle, _ptr(x), _ptr(y), float(alpha), float(beta),
+                            _stream_ptr(stream)))
+
+
+def spc5_destroy(A: Matrix) -> None:
+    if A._h:
+        _check(load().spc5_destroy(A._h))
+        A._h = ctypes.c_void_p(None)
+
+
+def spc5_status_str(code: int) -> str:
+    return load().spc5_status_str(code).decode()
+
+
+def spc5_last_error() -> str:
+    return load().spc5_last_error().decode(errors="replace")
+
+
+# ---------------------------------------------------------------- helpers --
+
+class _DeviceArray:
+    """A non-owning view of device memory exposed through the CUDA array
+    interface, so torch can wrap the library's arrays without copying."""
+
+    def __init__(self, ptr: int, shape, typestr: str, owner):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr,
+                                         "data": (ptr, True), "version": 3, "strides": None}
+        self._owner = owner
+
+
+def export_tensors(A: Matrix) -> dict:
+    """The converted arrays as torch tensors viewing A's device memory."""
+    import torch
+    info = spc5_matrix_info(A)
+    p = spc5_export(A)
+    npan, nb, nnz = info["npanels"], info["nblocks"], info["nnz"]
+    mtype = {1: "|u1", 2: "<u2", 4: "<u4"}[info["mask_bytes"]]
+    dev = torch.device("cuda", info["device"])
+
+    def view(ptr, n, typestr):
+        if n == 0:
+            return torch.empty(0, device=dev, dtype={"<i4": torch.int32, "|u1": torch.uint8,
+                                                     "<u2": torch.uint16, "<u4": torch.uint32,
+                                                     "<f8": torch.float64}[typestr])
+        return torch.as_tensor(_DeviceArray(ptr, (n,), typestr, A), device=dev)
+
+    return {"block_rowptr": view(p["block_rowptr"], npan + 1, "<i4"),
+            "panel_vptr": view(p["panel_vptr"], npan + 1, "<i4"),
+            "block_colidx": view(p["block_colidx"], nb, "<i4"),
+            "block_masks": view(p["block_masks"], nb, mtype),
+            "values": view(p["values"], nnz, "<f8")}

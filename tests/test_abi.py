@@ -1,0 +1,63 @@
+"""The C-ABI library: it builds for sm_103a, loads, and exports every symbol
+that include/spc5.h declares.  Argument checks that happen before any CUDA
+call are exercised here without a GPU."""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_2307_14774_gb300 as spc5
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(__file__)), "include", "spc5.h")
+
+
+def declared_functions() -> list[str]:
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(spc5_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_library_builds_and_exports_every_declared_symbol():
+    lib = spc5.load()
+    names = declared_functions()
+    assert names, "no declarations found"
+    for name in names:
+        assert hasattr(lib, name), f"{name} declared in spc5.h but not exported"
+    assert sorted(spc5.EXPORTS) == names
+
+
+def test_library_is_built_for_sm103a():
+    from paper_2307_14774_gb300 import build
+    assert "arch=compute_103a,code=sm_103a" in build.ARCH
+
+
+def test_status_strings():
+    for code, name in spc5.STATUS.items():
+        assert spc5.spc5_status_str(code) == name
+
+
+def test_rejects_unsupported_shape_before_touching_the_gpu():
+    rowptr = np.array([0, 1], np.int32)
+    col = np.array([0], np.int32)
+    val = np.array([1.0])
+    with pytest.raises(spc5.SPC5Error) as ei:
+        spc5.spc5_convert_csr(1, 1, 1, rowptr, col, val, r=3, c=5, stream=0)
+    assert ei.value.name == "SPC5_EUNSUPPORTED_RC"
+    with pytest.raises(spc5.SPC5Error) as ei:
+        spc5.spc5_convert_csr(-1, 1, 1, rowptr, col, val, r=4, c=8, stream=0)
+    assert ei.value.name == "SPC5_EINVAL"
+    with pytest.raises(spc5.SPC5Error) as ei:
+        spc5.spc5_convert_csr(1, 1, 1, rowptr, col, val, r=4, c=8, vals_dtype=spc5.SPC5_F32,
+                              stream=0)
+    assert ei.value.name == "SPC5_EUNSUPPORTED"
+    with pytest.raises(spc5.SPC5Error) as ei:
+        spc5.spc5_convert_csr(3_000_000_000, 1, 1, rowptr, col, val, r=4, c=8, stream=0)
+    assert ei.value.name == "SPC5_EOVERFLOW"
+    lib = spc5.load()
+    assert lib.spc5_spmv(None, None, None, 1.0, 0.0, None) == 1  # EINVAL on a NULL handle
+    assert lib.spc5_matrix_info(None, None) == 1
+    assert lib.spc5_destroy(None) == 0

@@ -1,0 +1,183 @@
+"""GPU parity against the CPU oracle, through the C-ABI: conversion bit-exact,
+SpMV within the FP64 tolerance |y - y_ref| <= 1e-13 * sum_j |a_ij x_j|.
+
+Sizes span many tiles, ragged tails (rows not a multiple of r, empty rows
+and panels, panels longer than a warp's round) and the degenerate cases."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2307_14774_gb300 as spc5
+import synth
+from gpuhelpers import (assert_conversion_equal, assert_within_tol, convert, exported, spmv,
+                        to_device, torch_cuda)
+
+pytestmark = pytest.mark.gpu
+
+BETAS = [(1, 8), (2, 4), (2, 8), (4, 4), (4, 8), (8, 4)]
+
+
+def _mats():
+    return [
+        synth.laplace2d(128, 128),                       # the 5-point configuration
+        synth.laplace2d(37, 29),                         # n not a multiple of 8
+        synth.stencil27(24, 23, 22, values="normal"),
+        synth.fem3d(6000, seed=2),
+        synth.powerlaw(60_000, seed=3),                  # long rows, empty-free but skewed
+        synth.uniform(20_000, 16, seed=4),
+        synth.bernoulli(301, 157, 0.02, seed=7, integer_values=False),  # empty rows/panels
+        synth.bernoulli(97, 300, 0.6, seed=8, integer_values=False),
+        synth.dense(200, values="normal"),
+    ]
+
+
+@pytest.fixture(scope="module")
+def mats():
+    torch_cuda()
+    return _mats()
+
+
+@pytest.mark.parametrize("r,c", BETAS)
+def test_conversion_bit_exact(mats, r, c):
+    for A in mats:
+        M = convert(A, r, c)
+        S = oracle.convert(A, r, c)
+        assert_conversion_equal(M, S, A)
+        assert M.info()["filling"] == pytest.approx(S.filling(), rel=0, abs=1e-15)
+
+
+@pytest.mark.parametrize("r,c", BETAS)
+def test_spmv_fp64_tolerance(mats, r, c):
+    for A in mats:
+        x = synth.vector_uniform(A.ncols, seed=11)
+        M = convert(A, r, c)
+        y = spmv(M, x)
+        y_ref, scale = oracle.csr_spmv(A, x)
+        assert_within_tol(y, y_ref, scale)
+
+
+@pytest.mark.parametrize("r,c", BETAS)
+def test_spmv_integer_matrices_exact(r, c):
+    """Integer values and x: every partial sum is exact in FP64 in any
+    order, so the GPU must equal the dense product bit for bit."""
+    for seed, (nr, nc, d) in enumerate([(64, 64, 0.3), (129, 77, 0.5), (33, 500, 0.9)]):
+        A = synth.bernoulli(nr, nc, d, seed=seed, integer_values=True)
+        x = synth.vector_int(nc, -7, 7, seed=seed)
+        y = spmv(convert(A, r, c), x)
+        assert np.array_equal(y, A.todense() @ x)
+
+
+@pytest.mark.parametrize("r,c", BETAS)
+def test_laplacian_times_ones(r, c):
+    A = synth.stencil27(21, 19, 17, values="poisson")
+    y = spmv(convert(A, r, c), np.ones(A.ncols))
+    assert np.array_equal(y, 26.0 - (np.diff(A.rowptr) - 1))
+
+
+@pytest.mark.parametrize("r,c", [(1, 8), (4, 8), (8, 4)])
+def test_alpha_beta(r, c):
+    A = synth.fem3d(3000, seed=5)
+    x = synth.vector_uniform(A.ncols, seed=1)
+    y0 = synth.vector_normal(A.nrows, seed=2)
+    M = convert(A, r, c)
+    y_ref, scale = oracle.csr_spmv(A, x)
+    for alpha, beta in [(1.0, 0.0), (-2.5, 0.0), (1.0, 1.0), (0.5, -3.0), (0.0, 2.0)]:
+        y = spmv(M, x, y0.copy(), alpha, beta)
+        expect = alpha * y_ref + beta * y0
+        assert_within_tol(y, expect, abs(alpha) * scale, extra=np.abs(beta * y0))
+    # beta == 0 never reads y: NaN in y must not propagate
+    y = spmv(M, x, np.full(A.nrows, np.nan), 1.0, 0.0)
+    assert np.all(np.isfinite(y))
+
+
+def test_host_vectors_match_device_vectors():
+    A = synth.stencil27(20, 20, 20, values="normal")
+    M = convert(A, 4, 8)
+    x = synth.vector_uniform(A.ncols, seed=3)
+    y_dev = spmv(M, x)
+    y_host = np.full(A.nrows, np.nan)
+    spc5.spc5_spmv(M, x, y_host)  # numpy: host pointers
+    assert np.array_equal(y_host, y_dev)
+    y0 = synth.vector_normal(A.nrows, seed=1)
+    y_host = y0.copy()
+    spc5.spc5_spmv(M, x, y_host, 2.0, -1.0)
+    assert np.array_equal(y_host, spmv(M, x, y0.copy(), 2.0, -1.0))
+
+
+def test_host_csr_input_matches_device_csr_input():
+    A = synth.powerlaw(20_000, seed=9)
+    M_host = spc5.spc5_convert_csr(A.nrows, A.ncols, A.nnz, A.rowptr, A.colidx, A.vals, r=2, c=8)
+    M_dev = convert(A, 2, 8)
+    gh, gd = exported(M_host), exported(M_dev)
+    for k in gh:
+        assert np.array_equal(gh[k], gd[k])
+
+
+@pytest.mark.parametrize("r,c", BETAS)
+def test_degenerate_shapes(r, c):
+    cases = [
+        synth.CSR(1, 1, np.array([0, 1], np.int32), np.array([0], np.int32), np.array([3.0])),
+        synth.CSR(5, 9, np.zeros(6, np.int32), np.zeros(0, np.int32), np.zeros(0)),  # no entries
+        synth.CSR(3, 1, np.array([0, 1, 1, 2], np.int32), np.array([0, 0], np.int32),
+                  np.array([2.0, -1.0])),                                          # one column
+        synth.bernoulli(1, 1000, 0.7, seed=3, integer_values=False),               # one long row
+        synth.bernoulli(9, 17, 0.0, seed=1),                                       # empty again
+        synth.dense(1, 3000, values="normal"),                                     # one dense row
+        synth.dense(3000, 1, values="normal"),                                     # one column
+    ]
+    for A in cases:
+        M = convert(A, r, c)
+        assert_conversion_equal(M, oracle.convert(A, r, c), A)
+        x = synth.vector_uniform(A.ncols, seed=2)
+        y_ref, scale = oracle.csr_spmv(A, x)
+        assert_within_tol(spmv(M, x), y_ref, scale)
+
+
+def test_explicit_zeros_are_kept():
+    A = synth.bernoulli(50, 50, 0.5, seed=4, integer_values=True)
+    assert (A.vals == 0).any()
+    S = oracle.convert(A, 4, 8)
+    assert_conversion_equal(convert(A, 4, 8), S, A)
+
+
+def test_invalid_csr_is_rejected_on_device():
+    torch = torch_cuda()
+    A = synth.bernoulli(40, 40, 0.3, seed=5)
+    row = int(np.argmax(np.diff(A.rowptr) >= 2))
+    a = A.rowptr[row]
+    bad_cols = A.colidx.copy()
+    bad_cols[a], bad_cols[a + 1] = bad_cols[a + 1], bad_cols[a]
+    out_cols = A.colidx.copy()
+    out_cols[-1] = 40
+    bad_rowptr = A.rowptr.copy()
+    bad_rowptr[-1] += 1
+    dec_rowptr = A.rowptr.copy()
+    dec_rowptr[5] = dec_rowptr[6] + 1
+    for rowptr, colidx, code in [(A.rowptr, bad_cols, "SPC5_EUNSORTED"),
+                                 (A.rowptr, out_cols, "SPC5_ERANGE"),
+                                 (bad_rowptr, A.colidx, "SPC5_EROWPTR"),
+                                 (dec_rowptr, A.colidx, "SPC5_EROWPTR")]:
+        with pytest.raises(spc5.SPC5Error) as ei:
+            spc5.spc5_convert_csr(40, 40, A.nnz, torch.from_numpy(rowptr).cuda(),
+                                  torch.from_numpy(colidx).cuda(),
+                                  torch.from_numpy(A.vals).cuda(), r=4, c=8)
+        assert ei.value.name == code
+    # the context is still usable afterwards
+    y = spmv(convert(A, 4, 8), np.ones(40))
+    assert np.array_equal(y, A.todense() @ np.ones(40))
+
+
+@pytest.mark.parametrize("log2g", [0, 1, 2, 3])
+def test_lane_mappings_agree(monkeypatch, log2g):
+    """Every lanes-per-row mapping computes the same products (within
+    tolerance) and identical results on integer data."""
+    monkeypatch.setenv("SPC5_LOG2_LANES_PER_ROW", str(log2g))
+    A = synth.powerlaw(30_000, seed=12)
+    x = synth.vector_uniform(A.ncols, seed=4)
+    y_ref, scale = oracle.csr_spmv(A, x)
+    for r, c in [(1, 8), (4, 4)]:
+        M = convert(A, r, c)
+        assert M.info()["lanes_per_row"] == 1 << log2g
+        assert_within_tol(spmv(M, x), y_ref, scale)
