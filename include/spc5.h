@@ -67,7 +67,13 @@ typedef struct {
   int32_t mask_bytes;      /* bytes of one block's packed mask word: r * c / 8 */
   int64_t device_bytes;    /* device memory held by the handle */
   int32_t device;          /* CUDA device ordinal the matrix lives on */
-  int32_t lanes_per_row;   /* SpMV mapping chosen for this matrix (1, 2, 4, ...) */
+  int32_t lanes_per_row;   /* lanes sharing one row in the SpMV's row groups (1, 2, 4, ...) */
+  int32_t launches_per_spmv; /* kernel launches one spc5_spmv call makes (1, or 2 with pieces) */
+  int64_t ntiles;          /* SpMV work tiles (shared-memory stages of work) */
+  int64_t long_panels;     /* panels split into pieces whose partial sums are added in order */
+  int32_t stages;          /* shared-memory pipeline stages per SM */
+  int32_t consumers;       /* consumer warps per SM */
+  uint32_t device_error;   /* nonzero if a kernel gave up a bounded wait (reading it syncs) */
 } spc5_info;
 
 /*

@@ -14,6 +14,8 @@ first use (or by ``build()``), and follows the paper:
 * ``spc5_spmv``     Algorithm 1, scalar path.
 * ``to_csr``        beta(r,c) -> CSR.
 * ``pack_masks``    per-block packed r*c-bit mask words.
+* ``quantize``      FP64 -> FP32 / BF16 storage (round to nearest even;
+                    BF16 through a round-to-odd FP32 intermediate).
 """
 from __future__ import annotations
 
@@ -70,7 +72,8 @@ def _bind(lib):
     lib.oracle_spc5_spmv.argtypes = [i64, ci, ci, i64p, i32p, u64p, f64p, f64p, f64p]
     lib.oracle_spc5_to_csr.argtypes = [i64, ci, ci, i64p, i32p, u64p, f64p, i32p, i32p, f64p]
     lib.oracle_pack_masks.argtypes = [i64, ci, ci, u64p, u8p]
-    for f in (lib.oracle_check_csr, lib.oracle_csr_spmv, lib.oracle_csr_spmv_plain,
+    lib.oracle_quantize.argtypes = [i64, f64p, ci, opt]
+    for f in (lib.oracle_quantize, lib.oracle_check_csr, lib.oracle_csr_spmv, lib.oracle_csr_spmv_plain,
               lib.oracle_spc5_convert, lib.oracle_spc5_spmv, lib.oracle_spc5_to_csr,
               lib.oracle_pack_masks):
         f.restype = ci
@@ -195,6 +198,14 @@ class Oracle:
                                          _arr(S.values, np.float64), x, y))
         return y
 
+    def quantize(self, values, dtype: str) -> np.ndarray:
+        """FP64 -> "f32" (float32) or "bf16" (uint16 bit patterns)."""
+        v = _arr(values, np.float64)
+        code, out = {"f32": (1, np.empty(v.shape, np.float32)),
+                     "bf16": (2, np.empty(v.shape, np.uint16))}[dtype]
+        _check(self.lib.oracle_quantize(v.size, v, code, out.ctypes.data_as(ctypes.c_void_p)))
+        return out
+
     def to_csr(self, S: SPC5):
         """beta(r,c) -> (rowptr, colidx, vals)."""
         nnz = S.nnz
@@ -241,6 +252,16 @@ def spc5_spmv(S: SPC5, x) -> np.ndarray:
 
 def to_csr(S: SPC5):
     return _default().to_csr(S)
+
+
+def quantize(values, dtype: str) -> np.ndarray:
+    return _default().quantize(values, dtype)
+
+
+def bf16_to_f64(bits) -> np.ndarray:
+    """BF16 bit patterns -> exact FP64 values (a BF16 is the upper half of an FP32)."""
+    b = np.asarray(bits, np.uint16).astype(np.uint32) << 16
+    return b.view(np.float32).astype(np.float64)
 
 
 def panel_value_offsets(A, r: int) -> np.ndarray:

@@ -14,6 +14,8 @@
  *   oracle_spc5_spmv    Algorithm 1, scalar path, over beta(r,c)
  *   oracle_spc5_to_csr  beta(r,c) -> CSR (inverse of the conversion)
  *   oracle_pack_masks   the r per-row c-bit masks of a block as one word
+ *   oracle_quantize     FP64 values -> FP32 or BF16 storage, round to
+ *                       nearest even (the reduced-precision value forms)
  *
  * Readings of the paper taken here (each one is also listed in the design
  * notes):
@@ -274,4 +276,58 @@ int oracle_pack_masks(int64_t nblocks, int r, int c, const uint64_t *block_masks
     for (int t = 0; t < nbytes; ++t) packed[b * nbytes + t] = (uint8_t)(word >> (8 * t));
   }
   return ORACLE_OK;
+}
+
+/*
+ * Reduced-precision storage of the values: FP64 -> FP32 or BF16, round to
+ * nearest, ties to even.
+ *
+ * FP32: the C conversion (float)d rounds to nearest even in the default
+ * rounding mode.
+ *
+ * BF16 (1 sign, 8 exponent, 7 fraction bits; the upper half of an FP32):
+ * rounding twice (FP64 -> FP32 -> BF16, both to nearest) can differ from
+ * one correct rounding when the first rounding lands exactly on a BF16
+ * midpoint.  Rounding the first step to odd instead (Boldo and Melquiond,
+ * "Emulation of FMA and correctly rounded sums: proved algorithms using
+ * rounding to odd", IEEE TC 2008) makes the second rounding correct, since
+ * FP32 keeps at least two more significand bits than BF16:
+ *   1. f = d truncated toward zero to FP32; if f != d, force f's last bit to 1;
+ *   2. round f to the nearest BF16, ties to even, on its bit pattern.
+ * Finite inputs whose magnitude stays inside the FP32 normal range.
+ */
+static float round_to_odd_f32(double d) {
+  float f = (float)d;
+  /* move toward zero if the nearest rounding went away from zero */
+  if (fabs((double)f) > fabs(d)) f = nextafterf(f, 0.0f);
+  if ((double)f != d) {
+    uint32_t b;
+    memcpy(&b, &f, 4);
+    b |= 1u;
+    memcpy(&f, &b, 4);
+  }
+  return f;
+}
+
+static uint16_t bf16_from_f32_rne(float f) {
+  uint32_t b;
+  memcpy(&b, &f, 4);
+  uint32_t lsb = (b >> 16) & 1u;
+  b += 0x7FFFu + lsb;
+  return (uint16_t)(b >> 16);
+}
+
+/* dtype 1: out is float[n]; dtype 2: out is uint16_t[n] (BF16 bit patterns). */
+int oracle_quantize(int64_t n, const double *in, int dtype, void *out) {
+  if (dtype == 1) {
+    float *o = (float *)out;
+    for (int64_t i = 0; i < n; ++i) o[i] = (float)in[i];
+    return ORACLE_OK;
+  }
+  if (dtype == 2) {
+    uint16_t *o = (uint16_t *)out;
+    for (int64_t i = 0; i < n; ++i) o[i] = bf16_from_f32_rne(round_to_odd_f32(in[i]));
+    return ORACLE_OK;
+  }
+  return ORACLE_EINVAL;
 }

@@ -64,6 +64,11 @@ void free_matrix(spc5_matrix *A) {
   cudaFree(A->values);
   cudaFree(A->x_stage);
   cudaFree(A->y_stage);
+  cudaFree(A->tiles);
+  cudaFree(A->long_panels);
+  cudaFree(A->long_slots);
+  cudaFree(A->partial);
+  cudaFree(A->dev_error);
   delete A;
 }
 
@@ -188,7 +193,19 @@ spc5_status spc5_matrix_info(const spc5_matrix *A, spc5_info *info) {
   info->mask_bytes = A->r * A->c / 8;
   info->device_bytes = A->device_bytes;
   info->device = A->device;
-  info->lanes_per_row = 1 << A->log2_lanes_per_row;
+  info->lanes_per_row = A->kernel ? (1 << A->log2_group_lanes) : (1 << A->log2_lanes_per_row);
+  info->launches_per_spmv = spmv_launches(A);
+  info->ntiles = A->ntiles;
+  info->long_panels = A->nlong;
+  info->stages = A->stages;
+  info->consumers = A->consumers;
+  uint32_t derr = 0;
+  if (A->dev_error) {
+    DeviceGuard g(A->device);
+    if (cudaMemcpy(&derr, A->dev_error, sizeof(uint32_t), cudaMemcpyDeviceToHost) != cudaSuccess)
+      derr = 0xffffffffu;
+  }
+  info->device_error = derr;
   return SPC5_OK;
 }
 

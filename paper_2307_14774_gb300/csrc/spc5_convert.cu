@@ -375,11 +375,38 @@ struct PopcIn {
   __device__ int32_t operator()(int64_t i) const { return __popc(m[i]); }
 };
 
+// Storage conversions of the values (round to nearest, ties to even).
+struct StoreF64 {
+  using T = double;
+  __device__ static double cvt(double d) { return d; }
+};
+struct StoreF32 {
+  using T = float;
+  __device__ static float cvt(double d) { return __double2float_rn(d); }
+};
+// FP64 -> BF16 with a single correct rounding: first round toward zero to
+// FP32 and, if inexact, force the last FP32 bit to 1 (round to odd; Boldo
+// and Melquiond, IEEE TC 2008), then round the FP32 bit pattern to the
+// nearest BF16, ties to even.  FP32 carries 16 more significand bits than
+// BF16, so the odd intermediate never creates a false tie.  Finite inputs
+// inside the FP32 normal range.
+struct StoreBF16 {
+  using T = uint16_t;
+  __device__ static uint16_t cvt(double d) {
+    float f = __double2float_rz(d);
+    uint32_t b = __float_as_uint(f);
+    if ((double)f != d) b |= 1u;
+    b += 0x7FFFu + ((b >> 16) & 1u);
+    return (uint16_t)(b >> 16);
+  }
+};
+
+template <typename Store>
 __global__ void k_values(int64_t nnz, int r, int c, const int32_t *colidx, const int32_t *rowid,
                          const int32_t *elem_pos, const int32_t *uidx_incl,
                          const int32_t *bidx_incl, const int32_t *block_colidx,
                          const uint32_t *mask32, const int32_t *boff, const double *vals,
-                         double *values) {
+                         typename Store::T *values) {
   GRID_STRIDE(e, nnz) {
     int32_t b;
     int bit;
@@ -388,7 +415,7 @@ __global__ void k_values(int64_t nnz, int r, int c, const int32_t *colidx, const
     if (k < 0 || k >= c) continue;  // reported by k_masks
     int32_t dst = boff[b] + __popc(mask32[b] & ((1u << bit) - 1u));
     if (dst < 0 || dst >= nnz) continue;
-    values[dst] = vals[e];
+    values[dst] = Store::cvt(vals[e]);
   }
 }
 
@@ -477,11 +504,17 @@ spc5_status convert_device(spc5_matrix *A, const int32_t *rowptr, const int32_t 
 
   // outputs
   int64_t nb = 0;
-  size_t vsize = sizeof(double);
-  CK(cudaMalloc((void **)&A->block_rowptr, (size_t)(np + 1) * sizeof(int32_t)), "alloc block_rowptr");
-  CK(cudaMalloc((void **)&A->panel_vptr, (size_t)(np + 1) * sizeof(int32_t)), "alloc panel_vptr");
+  const size_t vsize = A->value_dtype == SPC5_F64 ? 8 : A->value_dtype == SPC5_F32 ? 4 : 2;
+  // every array is padded by 16 bytes: the staged SpMV copies 16-byte
+  // aligned windows that may end up to 15 bytes past the last element
+  CK(cudaMalloc((void **)&A->block_rowptr, (size_t)(np + 1) * sizeof(int32_t) + 16),
+     "alloc block_rowptr");
+  CK(cudaMalloc((void **)&A->panel_vptr, (size_t)(np + 1) * sizeof(int32_t) + 16),
+     "alloc panel_vptr");
   CK(cudaMalloc(&A->values, (size_t)nnz * vsize + 16), "alloc values");
-  A->device_bytes = (int64_t)(2 * (np + 1) * sizeof(int32_t) + nnz * vsize + 16);
+  CK(cudaMalloc((void **)&A->dev_error, sizeof(uint32_t)), "alloc error word");
+  CK(cudaMemsetAsync(A->dev_error, 0, sizeof(uint32_t), s), "zero error word");
+  A->device_bytes = (int64_t)(2 * (np + 1) * sizeof(int32_t) + 32 + nnz * vsize + 16);
 
   if (nnz == 0) {
     CK(cudaMemsetAsync(A->block_rowptr, 0, (size_t)(np + 1) * sizeof(int32_t), s), "zero brp");
@@ -490,6 +523,8 @@ spc5_status convert_device(spc5_matrix *A, const int32_t *rowptr, const int32_t 
     CK(cudaMalloc(&A->masks, 16), "alloc masks");
     A->nblocks = 0;
     A->device_bytes += 32;
+    spc5_status pst = plan_tiles(A, nullptr, nullptr, s);
+    if (pst != SPC5_OK) return pst;
     CK(cudaStreamSynchronize(s), "sync");
     return SPC5_OK;
   }
@@ -562,9 +597,18 @@ spc5_status convert_device(spc5_matrix *A, const int32_t *rowptr, const int32_t 
   CK(device_scan<int32_t>(nb, PopcIn{mask32.p}, WriteI32{boff.p}, AddI32{}, 0, false,
                           scan_tmp.p, s),
      "scan popcounts");
-  k_values<<<grid_for(nnz), kThreads, 0, s>>>(nnz, r, c, colidx, rowid.p, elem_pos.p, uidx.p,
-                                             bidx.p, A->block_colidx, mask32.p, boff.p, vals,
-                                             (double *)A->values);
+  if (A->value_dtype == SPC5_F64)
+    k_values<StoreF64><<<grid_for(nnz), kThreads, 0, s>>>(
+        nnz, r, c, colidx, rowid.p, elem_pos.p, uidx.p, bidx.p, A->block_colidx, mask32.p,
+        boff.p, vals, (double *)A->values);
+  else if (A->value_dtype == SPC5_F32)
+    k_values<StoreF32><<<grid_for(nnz), kThreads, 0, s>>>(
+        nnz, r, c, colidx, rowid.p, elem_pos.p, uidx.p, bidx.p, A->block_colidx, mask32.p,
+        boff.p, vals, (float *)A->values);
+  else
+    k_values<StoreBF16><<<grid_for(nnz), kThreads, 0, s>>>(
+        nnz, r, c, colidx, rowid.p, elem_pos.p, uidx.p, bidx.p, A->block_colidx, mask32.p,
+        boff.p, vals, (uint16_t *)A->values);
   if (mask_bytes == 1)
     k_pack_masks<uint8_t><<<grid_for(nb), kThreads, 0, s>>>(nb, mask32.p, (uint8_t *)A->masks);
   else if (mask_bytes == 2)
@@ -573,6 +617,8 @@ spc5_status convert_device(spc5_matrix *A, const int32_t *rowptr, const int32_t 
     k_pack_masks<uint32_t><<<grid_for(nb), kThreads, 0, s>>>(nb, mask32.p, (uint32_t *)A->masks);
   k_check_offsets<<<grid_for(np), kThreads, 0, s>>>(np, A->block_rowptr, A->panel_vptr, boff.p,
                                                    nb, err.p);
+  spc5_status pst = plan_tiles(A, mask32.p, boff.p, s);
+  if (pst != SPC5_OK) return pst;
   CK(cudaGetLastError(), "conversion kernels");
   CK(cudaMemcpyAsync(&herr, err.p, sizeof(uint32_t), cudaMemcpyDeviceToHost, s), "read err");
   CK(cudaStreamSynchronize(s), "sync conversion");

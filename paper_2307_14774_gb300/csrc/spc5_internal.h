@@ -8,6 +8,23 @@
 
 #include "spc5.h"
 
+namespace spc5 {
+
+// One unit of SpMV work, produced by the planner at conversion time.
+//   group tile:   whole panels [p0, p1), lanes-per-row 2^(mode & 15); the
+//                 kernel stages the tile's block_rowptr and panel_vptr slices
+//   segment tile: blocks [b0, b1) of the single panel p0 (mode & kSegment),
+//                 32/r lanes per row; with mode & kPartial the r row sums go
+//                 to partial[slot * r + q] and a fixup adds the pieces.
+// [b0, b1) and [v0, v1) are the tile's block and value ranges.
+struct Tile {
+  int32_t p0, p1, b0, b1, v0, v1, slot, mode;
+};
+constexpr int32_t kSegment = 16;
+constexpr int32_t kPartial = 32;
+
+}  // namespace spc5
+
 // A converted matrix.  Every array is device memory owned by the handle.
 struct spc5_matrix {
   int64_t nrows = 0, ncols = 0, nnz = 0;
@@ -15,13 +32,30 @@ struct spc5_matrix {
   int64_t npanels = 0, nblocks = 0;
   int device = 0;
   spc5_dtype value_dtype = SPC5_F64;
-  int32_t *block_rowptr = nullptr;  // npanels + 1
-  int32_t *panel_vptr = nullptr;    // npanels + 1
+  int32_t *block_rowptr = nullptr;  // npanels + 1 (+16 bytes of padding)
+  int32_t *panel_vptr = nullptr;    // npanels + 1 (+16 bytes of padding)
   int32_t *block_colidx = nullptr;  // nblocks (+16 bytes of padding)
   void *masks = nullptr;            // nblocks * r * c / 8 bytes (+16 bytes of padding)
   void *values = nullptr;           // nnz values (+16 bytes of padding)
-  int log2_lanes_per_row = 0;       // SpMV mapping: 2^k lanes share one row
   int64_t device_bytes = 0;
+
+  // SpMV plan (built by the converter)
+  spc5::Tile *tiles = nullptr;
+  int64_t ntiles = 0;
+  int32_t *long_panels = nullptr;   // panels split into pieces
+  int32_t *long_slots = nullptr;    // [2 * nlong]: first and end piece slot of each
+  int64_t nlong = 0, npieces = 0;
+  double *partial = nullptr;        // npieces * r partial row sums
+  int log2_group_lanes = 0;         // lanes per row in group tiles
+  int vcap = 0, bcap = 0;           // stage capacity (values, blocks)
+  int group_panels = 0;             // panels per group tile
+  int stages = 0, consumers = 0, stage_bytes = 0;
+  int body = 0;                     // consumer body: bit 0 = predicated loop over the c
+                                    // bits (else set-bit loop), bit 1 = x staged in smem
+  int kernel = 1;                   // 1: staged tile kernel, 0: direct-load kernel
+  int log2_lanes_per_row = 0;       // direct-load kernel mapping
+  uint32_t *dev_error = nullptr;    // set by kernels on a timed-out wait
+
   // staging for host vectors in spc5_spmv
   double *x_stage = nullptr;
   double *y_stage = nullptr;
@@ -42,8 +76,16 @@ bool supported_rc(int r, int c);
 spc5_status convert_device(spc5_matrix *A, const int32_t *d_rowptr, const int32_t *d_colidx,
                            const double *d_vals, cudaStream_t stream);
 
+// Work plan for the staged SpMV kernel; called by the converter while the
+// per-block popcounts (mask32) and value offsets (boff) are still alive.
+spc5_status plan_tiles(spc5_matrix *A, const uint32_t *mask32, const int32_t *boff,
+                       cudaStream_t stream);
+
 // SpMV launch on device vectors.
 spc5_status spmv_device(const spc5_matrix *A, const double *x, double *y, double alpha,
                         double beta, cudaStream_t stream);
+
+// Number of kernel launches one spmv_device call makes.
+int spmv_launches(const spc5_matrix *A);
 
 }  // namespace spc5

@@ -1,0 +1,317 @@
+// Work plan of the staged SpMV kernel, built on the GPU at conversion time.
+//
+// The SpMV streams the matrix through shared memory one tile at a time, so a
+// tile's values, block columns and masks must fit one pipeline stage
+// (vcap values, bcap blocks).  Tiles:
+//   - group tiles: panels in fixed groups of group_panels = 32 / (r * G)
+//     consecutive panels, G lanes per row (G = 2^log2_group_lanes);
+//   - a group that does not fit a stage is "fat": each of its panels becomes
+//     its own segment tile (32 / r lanes per row) when it fits, otherwise a
+//     long panel, cut at block boundaries into pieces that fit; a piece's
+//     row sums go to a partial buffer and a fixup kernel adds the pieces of
+//     each long panel in order (deterministic, no atomics).
+// Piece boundaries are where the block's value offset or block index enters
+// a new window of (vcap - 32) values or bcap blocks; a block holds at most
+// 32 values, so every piece fits a stage.
+// All steps are flat passes plus prefix sums; nothing walks a panel serially.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdlib.h>
+
+#include <algorithm>
+
+#include "spc5_internal.h"
+#include "spc5_scan.cuh"
+
+namespace spc5 {
+namespace {
+
+constexpr int kThreads = 256;
+
+inline unsigned grid_for(int64_t n) {
+  int64_t blocks = (n + kThreads - 1) / kThreads;
+  if (blocks < 1) blocks = 1;
+  if (blocks > 1048576) blocks = 1048576;
+  return (unsigned)blocks;
+}
+
+#define GRID_STRIDE(i, n) \
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (n); \
+       i += (int64_t)gridDim.x * blockDim.x)
+
+struct PlanParams {
+  int64_t npanels, nblocks;
+  int32_t gp;       // panels per group
+  int32_t vcap, bcap, vwin;
+  int32_t log2g_group, log2g_segment;
+  const int32_t *brp, *vptr;
+};
+
+__device__ __forceinline__ bool group_fat(const PlanParams &P, int64_t g) {
+  int64_t a = g * P.gp, b = (a + P.gp < P.npanels) ? a + P.gp : P.npanels;
+  return (P.vptr[b] - P.vptr[a]) > P.vcap || (P.brp[b] - P.brp[a]) > P.bcap;
+}
+
+__device__ __forceinline__ bool panel_long(const PlanParams &P, int64_t p) {
+  return group_fat(P, p / P.gp) &&
+         ((P.vptr[p + 1] - P.vptr[p]) > P.vcap || (P.brp[p + 1] - P.brp[p]) > P.bcap);
+}
+
+// mark[b] counts the panels p >= 1 whose first block is b; an inclusive scan
+// gives the panel of every block.
+__global__ void k_mark_panels(PlanParams P, int32_t *mark) {
+  GRID_STRIDE(p, P.npanels - 1) {
+    int32_t b = P.brp[p + 1];
+    if (b < P.nblocks) atomicAdd(&mark[b], 1);
+  }
+}
+
+// Piece starts inside long panels.
+__global__ void k_piece_flags(PlanParams P, const int32_t *bpanel, const int32_t *boff,
+                              int32_t *pf) {
+  GRID_STRIDE(b, P.nblocks) {
+    int32_t p = bpanel[b];
+    int32_t f = 0;
+    if (panel_long(P, p)) {
+      int32_t first = P.brp[p];
+      if (b == first) {
+        f = 1;
+      } else {
+        int32_t v0 = P.vptr[p];
+        bool newv = (boff[b] - v0) / P.vwin != (boff[b - 1] - v0) / P.vwin;
+        bool newb = (b - first) / P.bcap != (b - 1 - first) / P.bcap;
+        f = (newv || newb) ? 1 : 0;
+      }
+    }
+    pf[b] = f;
+  }
+}
+
+// Tiles contributed by each panel, and the long-panel flags.
+__global__ void k_tile_counts(PlanParams P, const int32_t *pscan, int32_t *tc, int32_t *lf) {
+  GRID_STRIDE(p, P.npanels) {
+    int32_t t = 0, l = 0;
+    if (!group_fat(P, p / P.gp)) {
+      t = (p % P.gp == 0) ? 1 : 0;
+    } else if (panel_long(P, p)) {
+      t = pscan[P.brp[p + 1]] - pscan[P.brp[p]];
+      l = 1;
+    } else {
+      t = 1;
+    }
+    tc[p] = t;
+    lf[p] = l;
+  }
+}
+
+__global__ void k_write_panel_tiles(PlanParams P, const int32_t *tbase, const int32_t *lbase,
+                                    const int32_t *pscan, Tile *tiles, int32_t *long_panels,
+                                    int32_t *long_slots) {
+  GRID_STRIDE(p, P.npanels) {
+    bool fat = group_fat(P, p / P.gp);
+    if (!fat) {
+      if (p % P.gp == 0) {
+        int64_t p1 = (p + P.gp < P.npanels) ? p + P.gp : P.npanels;
+        tiles[tbase[p]] = Tile{(int32_t)p, (int32_t)p1, P.brp[p], P.brp[p1], P.vptr[p],
+                               P.vptr[p1], -1, P.log2g_group};
+      }
+    } else if (!panel_long(P, p)) {
+      tiles[tbase[p]] = Tile{(int32_t)p, (int32_t)p + 1, P.brp[p], P.brp[p + 1], P.vptr[p],
+                             P.vptr[p + 1], -1, P.log2g_segment | kSegment};
+    } else {
+      int32_t l = lbase[p];
+      long_panels[l] = (int32_t)p;
+      long_slots[2 * l] = pscan[P.brp[p]];
+      long_slots[2 * l + 1] = pscan[P.brp[p + 1]];
+    }
+  }
+}
+
+__global__ void k_write_piece_tiles(PlanParams P, const int32_t *bpanel, const int32_t *pf,
+                                    const int32_t *pscan, const int32_t *tbase,
+                                    const int32_t *boff, const uint32_t *mask32, Tile *tiles) {
+  GRID_STRIDE(b, P.nblocks) {
+    int32_t p = bpanel[b];
+    if (!panel_long(P, p)) continue;
+    int32_t first = P.brp[p];
+    int32_t piece = pscan[b] + pf[b] - 1;  // global index of the piece holding b
+    Tile *t = &tiles[tbase[p] + piece - pscan[first]];
+    if (pf[b]) {
+      t->p0 = p;
+      t->p1 = p + 1;
+      t->b0 = (int32_t)b;
+      t->v0 = boff[b];
+      t->slot = piece;
+      t->mode = P.log2g_segment | kSegment | kPartial;
+    }
+    bool last = (b + 1 == P.brp[p + 1]) || pf[b + 1];
+    if (last) {
+      t->b1 = (int32_t)b + 1;
+      t->v1 = boff[b] + __popc(mask32[b]);
+    }
+  }
+}
+
+template <typename T>
+struct Tmp {
+  T *p = nullptr;
+  cudaStream_t s;
+  explicit Tmp(cudaStream_t st) : s(st) {}
+  cudaError_t alloc(int64_t n) {
+    return cudaMallocAsync((void **)&p, (size_t)std::max<int64_t>(n, 1) * sizeof(T), s);
+  }
+  ~Tmp() {
+    if (p) cudaFreeAsync(p, s);
+  }
+};
+
+struct ReadI32 {
+  const int32_t *m;
+  __device__ int32_t operator()(int64_t i) const { return m[i]; }
+};
+struct ReadI32Pad {  // m[i] for i < n, 0 at i == n (so an exclusive scan of n+1 gives the total)
+  const int32_t *m;
+  int64_t n;
+  __device__ int32_t operator()(int64_t i) const { return i < n ? m[i] : 0; }
+};
+struct WriteI32 {
+  int32_t *o;
+  __device__ void operator()(int64_t i, int32_t v) const { o[i] = v; }
+};
+
+int env_int(const char *name, int dflt) {
+  const char *e = getenv(name);
+  return (e && *e) ? atoi(e) : dflt;
+}
+
+int round_up(int v, int m) { return (v + m - 1) / m * m; }
+
+}  // namespace
+
+#define CK(call, what)                            \
+  do {                                            \
+    spc5_status _st = cuda_check((call), (what)); \
+    if (_st != SPC5_OK) return _st;               \
+  } while (0)
+
+spc5_status plan_tiles(spc5_matrix *A, const uint32_t *mask32, const int32_t *boff,
+                       cudaStream_t s) {
+  const int r = A->r;
+  const int64_t np = A->npanels, nb = A->nblocks;
+  int log2r = 0;
+  while ((1 << log2r) < r) ++log2r;
+  const int log2g_segment = 5 - log2r;
+
+  // lanes per row in group tiles: about 8 block rounds per tile
+  double avg_b = np > 0 ? (double)nb / (double)np : 0.0;
+  double avg_v = np > 0 ? (double)A->nnz / (double)np : 0.0;
+  int log2g = 0;
+  while (log2g < log2g_segment && avg_b / (double)(1 << log2g) > 12.0) ++log2g;
+  log2g = std::min(std::max(env_int("SPC5_LOG2G_GROUP", log2g), 0), log2g_segment);
+  const int gp = 32 >> (log2r + log2g);
+
+  int vcap = round_up((int)(1.5 * gp * avg_v) + 64, 64);
+  vcap = std::min(std::max(vcap, 512), 4096);
+  int bcap = round_up((int)(1.5 * gp * avg_b) + 32, 32);
+  bcap = std::min(std::max(bcap, 128), 1024);
+  vcap = env_int("SPC5_VCAP", vcap);
+  bcap = env_int("SPC5_BCAP", bcap);
+  if (vcap < 64 || bcap < 1) {
+    set_error("invalid stage capacity");
+    return SPC5_EINVAL;
+  }
+  const int mb = A->r * A->c / 8;
+  auto r16 = [](int v) { return (v + 15) / 16 * 16; };
+  int stage = 64 + r16(vcap * 8 + 16) + r16(bcap * 4 + 16) + r16(bcap * mb + 16) +
+              2 * r16((gp + 1) * 4 + 16);
+  double filling = nb > 0 ? (double)A->nnz / ((double)nb * A->r * A->c) : 0.0;
+  int body = env_int("SPC5_BODY", filling >= 0.3 ? 3 : 2);
+  body = std::min(std::max(body, 0), 3);
+  int dev = 0, optin = 0;
+  CK(cudaGetDevice(&dev), "cudaGetDevice");
+  CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev), "smem attr");
+  int budget = optin - 2048;
+  int consumers;
+  int stages;
+  const int xs_bytes = (1024 + 32) * 8;  // per consumer, bodies 2 and 3
+  if (body >= 2) {
+    consumers = std::min(std::max(env_int("SPC5_CONSUMERS", 8), 1), 16);
+    stages = std::min(32, (budget - consumers * xs_bytes) / stage);
+  } else {
+    stages = std::min(32, budget / stage);
+    consumers = std::min(16, std::max(2, stages / 2 + 1));
+    consumers = std::min(std::max(env_int("SPC5_CONSUMERS", consumers), 1), 16);
+  }
+  stages = std::min(stages, env_int("SPC5_STAGES", stages));
+  if (stages < 2) {
+    set_error("pipeline stage does not fit shared memory");
+    return SPC5_EINVAL;
+  }
+  A->log2_group_lanes = log2g;
+  A->group_panels = gp;
+  A->vcap = vcap;
+  A->bcap = bcap;
+  A->stages = stages;
+  A->consumers = consumers;
+  A->stage_bytes = stage;
+  A->body = body;
+  A->kernel = env_int("SPC5_KERNEL", 1) ? 1 : 0;
+
+  if (np == 0) return SPC5_OK;
+  PlanParams P{np, nb, gp, vcap, bcap, vcap - 32, log2g, log2g_segment,
+               A->block_rowptr, A->panel_vptr};
+
+  Tmp<int32_t> bpanel(s), pf(s), pscan(s), tc(s), tbase(s), lf(s), lbase(s), tmp(s);
+  CK(bpanel.alloc(nb), "alloc");
+  CK(pf.alloc(nb), "alloc");
+  CK(pscan.alloc(nb + 1), "alloc");
+  CK(tc.alloc(np), "alloc");
+  CK(lf.alloc(np), "alloc");
+  CK(tbase.alloc(np + 1), "alloc");
+  CK(lbase.alloc(np + 1), "alloc");
+  CK(tmp.alloc(scan_tmp_elems(std::max<int64_t>(nb, np) + 1)), "alloc");
+  if (nb > 0) {
+    CK(cudaMemsetAsync(bpanel.p, 0, (size_t)nb * sizeof(int32_t), s), "memset");
+    if (np > 1) k_mark_panels<<<grid_for(np), kThreads, 0, s>>>(P, bpanel.p);
+    CK(device_scan<int32_t>(nb, ReadI32{bpanel.p}, WriteI32{bpanel.p}, AddI32{}, 0, true, tmp.p,
+                            s),
+       "scan panels");
+    k_piece_flags<<<grid_for(nb), kThreads, 0, s>>>(P, bpanel.p, boff, pf.p);
+  }
+  CK(device_scan<int32_t>(nb + 1, ReadI32Pad{pf.p, nb}, WriteI32{pscan.p}, AddI32{}, 0, false,
+                          tmp.p, s),
+     "scan pieces");
+  k_tile_counts<<<grid_for(np), kThreads, 0, s>>>(P, pscan.p, tc.p, lf.p);
+  CK(device_scan<int32_t>(np + 1, ReadI32Pad{tc.p, np}, WriteI32{tbase.p}, AddI32{}, 0, false,
+                          tmp.p, s),
+     "scan tiles");
+  CK(device_scan<int32_t>(np + 1, ReadI32Pad{lf.p, np}, WriteI32{lbase.p}, AddI32{}, 0, false,
+                          tmp.p, s),
+     "scan long panels");
+  int32_t counts[3] = {0, 0, 0};
+  CK(cudaMemcpyAsync(&counts[0], tbase.p + np, sizeof(int32_t), cudaMemcpyDeviceToHost, s), "rd");
+  CK(cudaMemcpyAsync(&counts[1], lbase.p + np, sizeof(int32_t), cudaMemcpyDeviceToHost, s), "rd");
+  CK(cudaMemcpyAsync(&counts[2], pscan.p + nb, sizeof(int32_t), cudaMemcpyDeviceToHost, s), "rd");
+  CK(cudaStreamSynchronize(s), "sync plan counts");
+  A->ntiles = counts[0];
+  A->nlong = counts[1];
+  A->npieces = counts[2];
+  CK(cudaMalloc((void **)&A->tiles, (size_t)std::max<int64_t>(A->ntiles, 1) * sizeof(Tile)),
+     "alloc tiles");
+  CK(cudaMalloc((void **)&A->long_panels, (size_t)std::max<int64_t>(A->nlong, 1) * 4), "alloc");
+  CK(cudaMalloc((void **)&A->long_slots, (size_t)std::max<int64_t>(A->nlong, 1) * 8), "alloc");
+  CK(cudaMalloc((void **)&A->partial,
+                (size_t)std::max<int64_t>(A->npieces, 1) * A->r * sizeof(double)),
+     "alloc partial");
+  A->device_bytes += A->ntiles * (int64_t)sizeof(Tile) + A->nlong * 12 +
+                     A->npieces * A->r * (int64_t)sizeof(double);
+  k_write_panel_tiles<<<grid_for(np), kThreads, 0, s>>>(P, tbase.p, lbase.p, pscan.p, A->tiles,
+                                                       A->long_panels, A->long_slots);
+  if (nb > 0 && A->nlong > 0)
+    k_write_piece_tiles<<<grid_for(nb), kThreads, 0, s>>>(P, bpanel.p, pf.p, pscan.p, tbase.p,
+                                                         boff, mask32, A->tiles);
+  CK(cudaGetLastError(), "plan kernels");
+  return SPC5_OK;
+}
+
+}  // namespace spc5

@@ -1,31 +1,52 @@
 // y = alpha * A x + beta * y over beta(r,c) (Algorithm 1).
 //
-// GPU mapping.  Algorithm 1 walks a panel's blocks with one running value
-// index idxVal, so a block's values cannot be located without the
-// popcounts of all earlier blocks.  The converter stores every panel's first
-// value offset (panel_vptr), which removes the dependency between panels;
-// inside a panel the offsets come from popcounts:
-//   - a warp holds PPW = 32 / (r * G) panels; lane (j, q, g) works on row q
-//     of panel j, and the G lanes of a row take the panel's blocks G at a
-//     time (G = 2^log2G, chosen per matrix),
-//   - a round loads G blocks (start column, packed mask word), the G lanes
-//     exclusive-scan the blocks' popcounts, and each lane finds its row's
-//     values at  panel offset + scan + popc(mask bits of rows < q),
-//   - each lane loops over its row's set bits (the scalar path of
-//     Algorithm 1, one bit per iteration) with FP64 FMAs; x is read through
-//     L1/L2 at column start + k,
-//   - the G partial sums of a row are combined with shuffles and one lane
-//     stores y (Section 3.2's single write of the reduced row results).
+// Algorithm 1 walks a panel's blocks with one running value index idxVal,
+// so a block's values cannot be located without the popcounts of all earlier
+// blocks.  The converter stores every panel's first value offset
+// (panel_vptr), which removes the dependency between panels; inside a panel
+// the offsets come from popcounts.
+//
+// Lane mapping (both kernels): a warp works on PPW = 32 / (r * G) panels;
+// lane (j, q, g) handles row q of panel j, and the G lanes of a row take the
+// panel's blocks G at a time.  A round loads G blocks (start column and
+// packed mask word), the G lanes exclusive-scan the blocks' popcounts, and a
+// lane finds its row's values at
+//     panel offset + scan + popc(mask bits of rows < q).
+// The lane then multiplies its row's values by x[start + k] for every set
+// bit k (Algorithm 1's scalar path; x is read through L1/L2, where the c
+// columns of a block are shared by the r rows), and the G partial sums of a
+// row are reduced with shuffles before one lane writes y (Section 3.2: one
+// write of the reduced row result instead of r separate updates).
+//
+// Staged kernel (default): persistent, one CTA per SM.  Warp 0 is a
+// producer: for each tile of the work plan it issues bulk asynchronous
+// copies (cp.async.bulk, completion counted on an mbarrier) of the tile's
+// values, block columns, masks and panel pointers into a ring of shared
+// memory stages.  The other warps are consumers: they take the tiles in
+// order, wait on the stage's barrier, compute from shared memory, and
+// release the stage.  HBM is read in large contiguous transfers, while the
+// consumers' irregular accesses hit shared memory.  Panels too long for one
+// stage were cut into pieces by the planner; their row sums go to a partial
+// buffer that a fixup kernel adds in a fixed order.
+//
+// Direct kernel (SPC5_KERNEL=0): the same lane mapping reading global memory
+// directly; kept as a reference point for measurements.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "spc5_internal.h"
+#include "spc5_ptx.cuh"
 
 namespace spc5 {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kSpmvThreads = 256;
+constexpr int kDirectThreads = 256;
+constexpr long long kWaitBudget = 4000000000LL;  // SM cycles (about 2 s) before a wait gives up
+
+enum : uint32_t { kErrProducerWait = 1u, kErrConsumerWait = 2u, kErrTileTooLarge = 4u };
 
 template <int R, int C>
 struct MaskType {
@@ -48,27 +69,102 @@ struct MaskType<4, 4> {
   using T = uint16_t;
 };
 
+template <int R>
+struct Log2 {
+  static constexpr int v = R == 1 ? 0 : R == 2 ? 1 : R == 4 ? 2 : 3;
+};
+
+// One row's contribution of one block: sum over set bits k of mq of
+// vals[running index] * x[col + k].
+template <int C, bool UNROLL>
+__device__ __forceinline__ double row_block(double acc, uint32_t mq, const double *vals,
+                                            const double *__restrict__ xp) {
+  if (UNROLL) {
+    int o = 0;
+#pragma unroll
+    for (int t = 0; t < C; ++t) {
+      if ((mq >> t) & 1u) {
+        acc = fma(vals[o], __ldg(xp + t), acc);
+        ++o;
+      }
+    }
+  } else {
+    while (mq) {
+      const int k = __ffs(mq) - 1;
+      mq &= mq - 1u;
+      acc = fma(*vals++, __ldg(xp + k), acc);
+    }
+  }
+  return acc;
+}
+
+// Same with x already staged in shared memory (xrow[k] = x[start + k]).
+template <int C, bool UNROLL>
+__device__ __forceinline__ double row_block_xs(double acc, uint32_t mq, const double *vals,
+                                               const double *xrow) {
+  if (UNROLL) {
+    int o = 0;
+#pragma unroll
+    for (int t = 0; t < C; ++t) {
+      if ((mq >> t) & 1u) {
+        acc = fma(vals[o], xrow[t], acc);
+        ++o;
+      }
+    }
+  } else {
+    while (mq) {
+      const int k = __ffs(mq) - 1;
+      mq &= mq - 1u;
+      acc = fma(*vals++, xrow[k], acc);
+    }
+  }
+  return acc;
+}
+
+// Columns of a block present in at least one of its R rows.
 template <int R, int C>
-__global__ void __launch_bounds__(kSpmvThreads)
-    k_spmv_rowlanes(int64_t npanels, int64_t nrows, const int32_t *__restrict__ block_rowptr,
-                    const int32_t *__restrict__ panel_vptr,
-                    const int32_t *__restrict__ block_colidx,
-                    const typename MaskType<R, C>::T *__restrict__ masks,
-                    const double *__restrict__ vals, const double *__restrict__ x,
-                    double *__restrict__ y, double alpha, double beta, int log2G) {
-  static_assert(R * C <= 32, "mask word must fit 32 bits");
+__device__ __forceinline__ uint32_t union_mask(uint32_t m) {
+  uint32_t u = 0;
+#pragma unroll
+  for (int q = 0; q < R; ++q) u |= (m >> (q * C)) & ((1u << C) - 1u);
+  return u;
+}
+
+// Exclusive prefix of `pc` over the G lanes of a row group; *total gets the
+// group's sum.
+__device__ __forceinline__ int group_scan(int pc, int g, int G, int *total) {
+  int incl = pc;
+  for (int o = 1; o < G; o <<= 1) {
+    int t = __shfl_up_sync(kFull, incl, o, G);
+    if (g >= o) incl += t;
+  }
+  *total = (G > 1) ? __shfl_sync(kFull, incl, G - 1, G) : pc;
+  return incl - pc;
+}
+
+__device__ __forceinline__ double group_sum(double acc, int G) {
+  for (int o = G >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o, G);
+  return acc;
+}
+
+// ------------------------------------------------------------ direct kernel --
+
+template <int R, int C, bool UNROLL>
+__global__ void __launch_bounds__(kDirectThreads)
+    k_spmv_direct(int64_t npanels, int64_t nrows, const int32_t *__restrict__ block_rowptr,
+                  const int32_t *__restrict__ panel_vptr, const int32_t *__restrict__ block_colidx,
+                  const typename MaskType<R, C>::T *__restrict__ masks,
+                  const double *__restrict__ vals, const double *__restrict__ x,
+                  double *__restrict__ y, double alpha, double beta, int log2G) {
   const int lane = threadIdx.x & 31;
   const int G = 1 << log2G;
-  int log2R = 0;
-  while ((1 << log2R) < R) ++log2R;
-  const int shift_j = log2R + log2G;
-  const int ppw = 32 >> shift_j;  // panels per warp
+  const int shift_j = Log2<R>::v + log2G;
+  const int ppw = 32 >> shift_j;
   const int g = lane & (G - 1);
   const int q = (lane >> log2G) & (R - 1);
   const int j = lane >> shift_j;
   const uint32_t row_low = (q == 0) ? 0u : ((1u << (q * C)) - 1u);
   const uint32_t cmask = (1u << C) - 1u;
-
   const int64_t warp_id = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t w = warp_id; w * ppw < npanels; w += nwarps) {
@@ -85,23 +181,13 @@ __global__ void __launch_bounds__(kSpmvThreads)
       const uint32_t m = valid ? (uint32_t)masks[b] : 0u;
       const int32_t col = valid ? block_colidx[b] : 0;
       const int pc = __popc(m);
-      int incl = pc;
-      for (int o = 1; o < G; o <<= 1) {
-        int t = __shfl_up_sync(kFull, incl, o, G);
-        if (g >= o) incl += t;
-      }
-      const int total = (G > 1) ? __shfl_sync(kFull, incl, G - 1, G) : pc;
-      int32_t off = v + (incl - pc) + __popc(m & row_low);
-      uint32_t mq = (m >> (q * C)) & cmask;
-      while (mq) {
-        const int k = __ffs(mq) - 1;
-        mq &= mq - 1u;
-        acc = fma(vals[off], x[col + k], acc);
-        ++off;
-      }
+      int total;
+      const int excl = group_scan(pc, g, G, &total);
+      const int32_t off = v + excl + __popc(m & row_low);
+      acc = row_block<C, UNROLL>(acc, (m >> (q * C)) & cmask, vals + off, x + col);
       v += total;
     }
-    for (int o = G >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o, G);
+    acc = group_sum(acc, G);
     const int64_t row = p * R + q;
     if (pvalid && g == 0 && row < nrows) {
       double out = alpha * acc;
@@ -111,26 +197,450 @@ __global__ void __launch_bounds__(kSpmvThreads)
   }
 }
 
+// ------------------------------------------------------------ staged kernel --
+
+// Written by the producer before it arms the stage's barrier.  `seq` is the
+// tile sequence number of the CTA: a consumer waits for its own number
+// before waiting on the barrier, because a parity wait cannot tell a phase
+// two laps behind from a completed one.
+struct StageHdr {
+  Tile t;
+  int32_t voff, coff, moff, roff, pvoff, valid, seq, pad1;
+};
+static_assert(sizeof(StageHdr) == 64, "stage header is 64 bytes");
+
+struct StagedParams {
+  const Tile *tiles;
+  int32_t ntiles;
+  const int32_t *brp, *vptr, *colidx;
+  const uint8_t *masks;
+  const double *vals, *x;
+  double *y, *partial;
+  double alpha, beta;
+  int64_t nrows;
+  int32_t stages, stage_bytes, stage_base;
+  int32_t off_vals, off_col, off_mask, off_brp, off_vptr;
+  int32_t cap_vals, cap_col, cap_mask, cap_ptr;  // section capacities in bytes
+  int32_t xs_base;                               // byte offset of the x windows (BODY >= 2)
+  uint32_t *err;
+};
+
+// Body variants of the staged kernel's consumers:
+//   0: set-bit loop, x from global;  1: predicated loop over the c bits, x
+//   from global;  2 / 3: like 0 / 1 with x staged per window in shared memory.
+// x staging: a window covers kXsRounds rounds of block loads; every lane
+// loads the x values of its share of columns of its own blocks (about 32
+// independent loads per lane), then the window is computed from shared
+// memory.  Per-panel stride is odd (in doubles) so the panels of a warp hit
+// different banks.
+constexpr int kXsDoubles = 1024;
+constexpr int kXsPerConsumer = kXsDoubles + 32;
+
+// A 16-byte aligned window covering elements [first, last) of `elem` bytes.
+struct Span {
+  int64_t lo;
+  uint32_t bytes;
+  int32_t off;
+};
+__device__ __forceinline__ Span span_of(int64_t first, int64_t last, int elem) {
+  Span sp;
+  int64_t b0 = first * elem, b1 = last * elem;
+  sp.lo = b0 & ~(int64_t)15;
+  int64_t hi = (b1 + 15) & ~(int64_t)15;
+  sp.bytes = (b1 > b0) ? (uint32_t)(hi - sp.lo) : 0u;
+  sp.off = (int32_t)((b0 - sp.lo) / elem);
+  return sp;
+}
+
 template <int R, int C>
-cudaError_t launch(const spc5_matrix *A, const double *x, double *y, double alpha, double beta,
-                   cudaStream_t s) {
+__device__ void producer(const StagedParams &P, uint8_t *stage0, uint64_t *full, uint64_t *empty,
+                         int my_ntiles) {
+  constexpr int MB = R * C / 8;
+  const int lane = threadIdx.x & 31;
+  const int S = P.stages;
+  int issued = 0;
+  bool abort = false;
+  for (int base = 0; base < my_ntiles && !abort; base += 32) {
+    const int kk = base + lane;
+    Tile mine{0, 0, 0, 0, 0, 0, 0, 0};
+    if (kk < my_ntiles) mine = P.tiles[blockIdx.x + (int64_t)kk * gridDim.x];
+    const int nbatch = min(32, my_ntiles - base);
+    for (int i = 0; i < nbatch; ++i) {
+      const int k = base + i;
+      const int s = k % S;
+      const uint32_t ph = (uint32_t)(k / S) & 1u;
+      const bool ok = __all_sync(kFull, mbar_wait(&empty[s], ph ^ 1u, kWaitBudget));
+      if (!ok) {
+        if (lane == 0) atomicOr(P.err, kErrProducerWait);
+        abort = true;
+        break;
+      }
+      Tile t;
+      t.p0 = __shfl_sync(kFull, mine.p0, i);
+      t.p1 = __shfl_sync(kFull, mine.p1, i);
+      t.b0 = __shfl_sync(kFull, mine.b0, i);
+      t.b1 = __shfl_sync(kFull, mine.b1, i);
+      t.v0 = __shfl_sync(kFull, mine.v0, i);
+      t.v1 = __shfl_sync(kFull, mine.v1, i);
+      t.slot = __shfl_sync(kFull, mine.slot, i);
+      t.mode = __shfl_sync(kFull, mine.mode, i);
+      if (lane == 0) {
+        uint8_t *st = stage0 + (size_t)s * P.stage_bytes;
+        const bool segment = (t.mode & kSegment) != 0;
+        Span sv = span_of(t.v0, t.v1, 8);
+        Span sc = span_of(t.b0, t.b1, 4);
+        Span sm = span_of(t.b0, t.b1, MB);
+        Span sr{0, 0u, 0}, sp{0, 0u, 0};
+        if (!segment) {
+          sr = span_of(t.p0, (int64_t)t.p1 + 1, 4);
+          sp = span_of(t.p0, (int64_t)t.p1 + 1, 4);
+        }
+        const bool fits = sv.bytes <= (uint32_t)P.cap_vals && sc.bytes <= (uint32_t)P.cap_col &&
+                          sm.bytes <= (uint32_t)P.cap_mask && sr.bytes <= (uint32_t)P.cap_ptr &&
+                          (segment || (t.p1 - t.p0) <= 32);
+        StageHdr *h = reinterpret_cast<StageHdr *>(st);
+        h->t = t;
+        h->voff = sv.off;
+        h->coff = sc.off;
+        h->moff = sm.off;
+        h->roff = sr.off;
+        h->pvoff = sp.off;
+        h->valid = fits ? 1 : 0;
+        h->seq = k;
+        if (!fits) {
+          atomicOr(P.err, kErrTileTooLarge);
+          mbar_arrive_expect_tx(&full[s], 0u);
+        } else {
+          mbar_arrive_expect_tx(&full[s], sv.bytes + sc.bytes + sm.bytes + sr.bytes + sp.bytes);
+          if (sv.bytes)
+            bulk_g2s(st + P.off_vals, reinterpret_cast<const uint8_t *>(P.vals) + sv.lo, sv.bytes,
+                     &full[s]);
+          if (sc.bytes)
+            bulk_g2s(st + P.off_col, reinterpret_cast<const uint8_t *>(P.colidx) + sc.lo,
+                     sc.bytes, &full[s]);
+          if (sm.bytes)
+            bulk_g2s(st + P.off_mask, P.masks + sm.lo, sm.bytes, &full[s]);
+          if (sr.bytes)
+            bulk_g2s(st + P.off_brp, reinterpret_cast<const uint8_t *>(P.brp) + sr.lo, sr.bytes,
+                     &full[s]);
+          if (sp.bytes)
+            bulk_g2s(st + P.off_vptr, reinterpret_cast<const uint8_t *>(P.vptr) + sp.lo,
+                     sp.bytes, &full[s]);
+        }
+      }
+      ++issued;
+      __syncwarp();
+    }
+  }
+  // Do not leave while copies issued by this warp may still be landing in
+  // shared memory: wait (bounded) for the last phase of every used stage.
+  const int first = issued > S ? issued - S : 0;
+  for (int k = first; k < issued; ++k) {
+    const bool ok = __all_sync(kFull, mbar_wait(&full[k % S], (uint32_t)(k / S) & 1u, kWaitBudget));
+    if (!ok) {
+      if (lane == 0) atomicOr(P.err, kErrProducerWait);
+      break;
+    }
+  }
+}
+
+template <int R, int C, int BODY>
+__device__ void consumer(const StagedParams &P, uint8_t *stage0, uint64_t *full, uint64_t *empty,
+                         int *counter, int my_ntiles, double *xs) {
+  constexpr bool UNROLL = (BODY & 1) != 0;
+  constexpr bool XS = BODY >= 2;
+  constexpr int CPL = (C + R - 1) / R;  // columns staged per lane and block
+  using MaskT = typename MaskType<R, C>::T;
+  constexpr int LOG2R = Log2<R>::v;
+  const int lane = threadIdx.x & 31;
+  const int S = P.stages;
+  const uint32_t cmask = (1u << C) - 1u;
+  for (;;) {
+    int k = 0;
+    if (lane == 0) k = atomicAdd(counter, 1);
+    k = __shfl_sync(kFull, k, 0);
+    if (k >= my_ntiles) break;
+    const int s = k % S;
+    const uint8_t *st = stage0 + (size_t)s * P.stage_bytes;
+    // 1. wait until the producer has stamped this stage with tile k (then the
+    //    barrier is in tile k's phase), 2. wait for that phase to complete.
+    bool ok = true;
+    if (lane == 0) {
+      const volatile int32_t *seq = &reinterpret_cast<const StageHdr *>(st)->seq;
+      const long long t0 = clock64();
+      while (*seq != k) {
+        if (clock64() - t0 > kWaitBudget) {
+          ok = false;
+          break;
+        }
+      }
+    }
+    ok = __shfl_sync(kFull, ok ? 1 : 0, 0) != 0;
+    ok = ok && __all_sync(kFull, mbar_wait(&full[s], (uint32_t)(k / S) & 1u, kWaitBudget));
+    if (!ok) {
+      if (lane == 0) atomicOr(P.err, kErrConsumerWait);
+      break;
+    }
+    const StageHdr h = *reinterpret_cast<const StageHdr *>(st);
+    if (h.valid) {
+      const Tile &t = h.t;
+      const bool segment = (t.mode & kSegment) != 0;
+      const int log2G = t.mode & 15;
+      const int G = 1 << log2G;
+      const int shift_j = LOG2R + log2G;
+      const int g = lane & (G - 1);
+      const int q = (lane >> log2G) & (R - 1);
+      const int j = lane >> shift_j;
+      const uint32_t row_low = (q == 0) ? 0u : ((1u << (q * C)) - 1u);
+      const double *vs = reinterpret_cast<const double *>(st + P.off_vals) + h.voff;
+      const int32_t *cs = reinterpret_cast<const int32_t *>(st + P.off_col) + h.coff;
+      const MaskT *ms = reinterpret_cast<const MaskT *>(st + P.off_mask) + h.moff;
+      bool pvalid;
+      int32_t bl, bh, v;
+      if (segment) {
+        pvalid = (j == 0);
+        bl = 0;
+        bh = t.b1 - t.b0;
+        v = 0;
+      } else {
+        const int32_t *rs = reinterpret_cast<const int32_t *>(st + P.off_brp) + h.roff;
+        const int32_t *ps = reinterpret_cast<const int32_t *>(st + P.off_vptr) + h.pvoff;
+        pvalid = j < (t.p1 - t.p0);
+        bl = pvalid ? rs[j] - t.b0 : 0;
+        bh = pvalid ? rs[j + 1] - t.b0 : 0;
+        v = pvalid ? ps[j] - t.v0 : 0;
+      }
+      const int32_t nbp = bh - bl;
+      const int32_t maxnb = __reduce_max_sync(kFull, nbp);
+      double acc = 0.0;
+      if (!XS) {
+        for (int32_t it = 0; it < maxnb; it += G) {
+          const int32_t idx = it + g;
+          const bool valid = idx < nbp;
+          const int32_t b = bl + idx;
+          const uint32_t m = valid ? (uint32_t)ms[b] : 0u;
+          const int32_t col = valid ? cs[b] : 0;
+          const int pc = __popc(m);
+          int total;
+          const int excl = group_scan(pc, g, G, &total);
+          const int32_t off = v + excl + __popc(m & row_low);
+          acc = row_block<C, UNROLL>(acc, (m >> (q * C)) & cmask, vs + off, P.x + col);
+          v += total;
+        }
+      } else {
+        // rounds per window: the window holds 32 * W / R blocks of C doubles
+        constexpr int W = (kXsDoubles * R) / (32 * C);
+        const int xstride = W * G * C + 1;
+        double *xw = xs + j * xstride;
+        for (int32_t it0 = 0; it0 < maxnb; it0 += W * G) {
+          for (int w = 0; w < W; ++w) {
+            const int32_t idx = it0 + w * G + g;
+            if (it0 + w * G >= maxnb) break;
+            const bool valid = idx < nbp;
+            const int32_t b = bl + idx;
+            const uint32_t um = valid ? union_mask<R, C>((uint32_t)ms[b]) : 0u;
+            const int32_t col = valid ? cs[b] : 0;
+            double *dst = xw + (w * G + g) * C;
+#pragma unroll
+            for (int t = 0; t < CPL; ++t) {
+              const int k = q * CPL + t;
+              if (k < C && ((um >> k) & 1u)) dst[k] = __ldg(P.x + col + k);
+            }
+          }
+          __syncwarp();
+          for (int w = 0; w < W; ++w) {
+            if (it0 + w * G >= maxnb) break;
+            const int32_t idx = it0 + w * G + g;
+            const bool valid = idx < nbp;
+            const int32_t b = bl + idx;
+            const uint32_t m = valid ? (uint32_t)ms[b] : 0u;
+            const int pc = __popc(m);
+            int total;
+            const int excl = group_scan(pc, g, G, &total);
+            const int32_t off = v + excl + __popc(m & row_low);
+            acc = row_block_xs<C, UNROLL>(acc, (m >> (q * C)) & cmask, vs + off,
+                                          xw + (w * G + g) * C);
+            v += total;
+          }
+          __syncwarp();
+        }
+      }
+      acc = group_sum(acc, G);
+      if (pvalid && g == 0) {
+        if (t.mode & kPartial) {
+          P.partial[(int64_t)t.slot * R + q] = acc;
+        } else {
+          const int64_t row = ((int64_t)t.p0 + j) * R + q;
+          if (row < P.nrows) {
+            double out = P.alpha * acc;
+            if (P.beta != 0.0) out = fma(P.beta, P.y[row], out);
+            P.y[row] = out;
+          }
+        }
+      }
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[s]);
+  }
+}
+
+template <int R, int C, int BODY>
+__global__ void __launch_bounds__(32 * 17, 1) k_spmv_staged(const StagedParams P) {
+  extern __shared__ __align__(128) uint8_t smem[];
+  uint64_t *full = reinterpret_cast<uint64_t *>(smem);
+  uint64_t *empty = full + P.stages;
+  int *counter = reinterpret_cast<int *>(empty + P.stages);
+  uint8_t *stage0 = smem + P.stage_base;
+  const int warp = threadIdx.x >> 5;
+  const int my_ntiles =
+      (P.ntiles > (int)blockIdx.x) ? (P.ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < P.stages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+      reinterpret_cast<StageHdr *>(stage0 + (size_t)s * P.stage_bytes)->seq = -1;
+    }
+    *counter = 0;
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (warp == 0)
+    producer<R, C>(P, stage0, full, empty, my_ntiles);
+  else
+    consumer<R, C, BODY>(P, stage0, full, empty, counter, my_ntiles,
+                         reinterpret_cast<double *>(smem + P.xs_base) +
+                             (size_t)(warp - 1) * kXsPerConsumer);
+}
+
+// y rows of panels that were cut into pieces: add the pieces in order.
+template <int R>
+__global__ void k_fixup(int64_t nlong, const int32_t *long_panels, const int32_t *long_slots,
+                        const double *partial, double *y, double alpha, double beta,
+                        int64_t nrows) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nlong * R;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t l = i / R;
+    const int q = (int)(i % R);
+    const int64_t row = (int64_t)long_panels[l] * R + q;
+    double acc = 0.0;
+    for (int32_t s = long_slots[2 * l]; s < long_slots[2 * l + 1]; ++s)
+      acc += partial[(int64_t)s * R + q];
+    if (row < nrows) {
+      double out = alpha * acc;
+      if (beta != 0.0) out = fma(beta, y[row], out);
+      y[row] = out;
+    }
+  }
+}
+
+int num_sms() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+  }
+  return n;
+}
+
+template <int R, int C, int BODY>
+cudaError_t launch_staged(const spc5_matrix *A, const double *x, double *y, double alpha,
+                          double beta, cudaStream_t s) {
+  constexpr int MB = R * C / 8;
+  auto r16 = [](int v) { return (v + 15) / 16 * 16; };
+  StagedParams P;
+  P.tiles = A->tiles;
+  P.ntiles = (int32_t)A->ntiles;
+  P.brp = A->block_rowptr;
+  P.vptr = A->panel_vptr;
+  P.colidx = A->block_colidx;
+  P.masks = reinterpret_cast<const uint8_t *>(A->masks);
+  P.vals = reinterpret_cast<const double *>(A->values);
+  P.x = x;
+  P.y = y;
+  P.partial = A->partial;
+  P.alpha = alpha;
+  P.beta = beta;
+  P.nrows = A->nrows;
+  P.stages = A->stages;
+  P.cap_vals = r16(A->vcap * 8 + 16);
+  P.cap_col = r16(A->bcap * 4 + 16);
+  P.cap_mask = r16(A->bcap * MB + 16);
+  P.cap_ptr = r16((A->group_panels + 1) * 4 + 16);
+  P.off_vals = 64;
+  P.off_col = P.off_vals + P.cap_vals;
+  P.off_mask = P.off_col + P.cap_col;
+  P.off_brp = P.off_mask + P.cap_mask;
+  P.off_vptr = P.off_brp + P.cap_ptr;
+  P.stage_bytes = P.off_vptr + P.cap_ptr;
+  P.stage_base = (16 * A->stages + 16 + 127) / 128 * 128;
+  P.err = A->dev_error;
+  P.xs_base = P.stage_base + A->stages * P.stage_bytes;
+  const size_t smem = (size_t)P.xs_base +
+                      (BODY >= 2 ? (size_t)A->consumers * kXsPerConsumer * sizeof(double) : 0);
+  static size_t configured = 0;  // per instantiation
+  cudaError_t e = cudaSuccess;
+  if (smem > configured) {
+    e = cudaFuncSetAttribute(k_spmv_staged<R, C, BODY>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    configured = smem;
+  }
+  if (A->ntiles > 0) {
+    int grid = (int)std::min<int64_t>(num_sms(), A->ntiles);
+    k_spmv_staged<R, C, BODY><<<grid, 32 * (1 + A->consumers), smem, s>>>(P);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  if (A->nlong > 0) {
+    int64_t threads = A->nlong * R;
+    int blocks = (int)std::min<int64_t>((threads + 255) / 256, 4096);
+    k_fixup<R><<<blocks, 256, 0, s>>>(A->nlong, A->long_panels, A->long_slots, A->partial, y,
+                                      alpha, beta, A->nrows);
+    e = cudaGetLastError();
+  }
+  return e;
+}
+
+template <int R, int C, bool UNROLL>
+cudaError_t launch_direct(const spc5_matrix *A, const double *x, double *y, double alpha,
+                          double beta, cudaStream_t s) {
   using MaskT = typename MaskType<R, C>::T;
   int log2G = A->log2_lanes_per_row;
-  int log2R = 0;
-  while ((1 << log2R) < R) ++log2R;
-  if (log2R + log2G > 5) log2G = 5 - log2R;
-  const int ppw = 32 >> (log2R + log2G);
+  if (Log2<R>::v + log2G > 5) log2G = 5 - Log2<R>::v;
+  const int ppw = 32 >> (Log2<R>::v + log2G);
   int64_t warps = (A->npanels + ppw - 1) / ppw;
-  int64_t blocks = (warps + (kSpmvThreads / 32) - 1) / (kSpmvThreads / 32);
+  int64_t blocks = (warps + (kDirectThreads / 32) - 1) / (kDirectThreads / 32);
   if (blocks < 1) blocks = 1;
-  if (blocks > 152 * 64) blocks = 152 * 64;
-  k_spmv_rowlanes<R, C><<<(unsigned)blocks, kSpmvThreads, 0, s>>>(
+  if (blocks > (int64_t)num_sms() * 64) blocks = (int64_t)num_sms() * 64;
+  k_spmv_direct<R, C, UNROLL><<<(unsigned)blocks, kDirectThreads, 0, s>>>(
       A->npanels, A->nrows, A->block_rowptr, A->panel_vptr, A->block_colidx,
       (const MaskT *)A->masks, (const double *)A->values, x, y, alpha, beta, log2G);
   return cudaGetLastError();
 }
 
+template <int R, int C>
+cudaError_t launch(const spc5_matrix *A, const double *x, double *y, double alpha, double beta,
+                   cudaStream_t s) {
+  if (A->kernel == 0)
+    return (A->body & 1) ? launch_direct<R, C, true>(A, x, y, alpha, beta, s)
+                         : launch_direct<R, C, false>(A, x, y, alpha, beta, s);
+  switch (A->body) {
+    case 0: return launch_staged<R, C, 0>(A, x, y, alpha, beta, s);
+    case 1: return launch_staged<R, C, 1>(A, x, y, alpha, beta, s);
+    case 2: return launch_staged<R, C, 2>(A, x, y, alpha, beta, s);
+    default: return launch_staged<R, C, 3>(A, x, y, alpha, beta, s);
+  }
+}
+
 }  // namespace
+
+int spmv_launches(const spc5_matrix *A) {
+  if (A->nrows == 0) return 0;
+  if (A->kernel == 0) return 1;
+  return (A->ntiles > 0 ? 1 : 0) + (A->nlong > 0 ? 1 : 0);
+}
 
 spc5_status spmv_device(const spc5_matrix *A, const double *x, double *y, double alpha,
                         double beta, cudaStream_t s) {

@@ -40,7 +40,10 @@ class Info(ctypes.Structure):
                 ("nblocks", ctypes.c_int64), ("filling", ctypes.c_double),
                 ("value_dtype", ctypes.c_int), ("mask_bytes", ctypes.c_int32),
                 ("device_bytes", ctypes.c_int64), ("device", ctypes.c_int32),
-                ("lanes_per_row", ctypes.c_int32)]
+                ("lanes_per_row", ctypes.c_int32), ("launches_per_spmv", ctypes.c_int32),
+                ("ntiles", ctypes.c_int64), ("long_panels", ctypes.c_int64),
+                ("stages", ctypes.c_int32), ("consumers", ctypes.c_int32),
+                ("device_error", ctypes.c_uint32)]
 
 
 _lock = threading.Lock()
@@ -193,7 +196,7 @@ class _DeviceArray:
 
     def __init__(self, ptr: int, shape, typestr: str, owner):
         self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr,
-                                         "data": (ptr, True), "version": 3, "strides": None}
+                                         "data": (ptr, False), "version": 3, "strides": None}
         self._owner = owner
 
 
@@ -203,18 +206,17 @@ def export_tensors(A: Matrix) -> dict:
     info = spc5_matrix_info(A)
     p = spc5_export(A)
     npan, nb, nnz = info["npanels"], info["nblocks"], info["nnz"]
-    mtype = {1: "|u1", 2: "<u2", 4: "<u4"}[info["mask_bytes"]]
     dev = torch.device("cuda", info["device"])
 
     def view(ptr, n, typestr):
         if n == 0:
             return torch.empty(0, device=dev, dtype={"<i4": torch.int32, "|u1": torch.uint8,
-                                                     "<u2": torch.uint16, "<u4": torch.uint32,
                                                      "<f8": torch.float64}[typestr])
         return torch.as_tensor(_DeviceArray(ptr, (n,), typestr, A), device=dev)
 
     return {"block_rowptr": view(p["block_rowptr"], npan + 1, "<i4"),
             "panel_vptr": view(p["panel_vptr"], npan + 1, "<i4"),
             "block_colidx": view(p["block_colidx"], nb, "<i4"),
-            "block_masks": view(p["block_masks"], nb, mtype),
+            # packed mask words as raw little-endian bytes, mask_bytes per block
+            "block_masks": view(p["block_masks"], nb * info["mask_bytes"], "|u1"),
             "values": view(p["values"], nnz, "<f8")}

@@ -170,14 +170,68 @@ def test_invalid_csr_is_rejected_on_device():
 
 
 @pytest.mark.parametrize("log2g", [0, 1, 2, 3])
-def test_lane_mappings_agree(monkeypatch, log2g):
-    """Every lanes-per-row mapping computes the same products (within
-    tolerance) and identical results on integer data."""
+def test_direct_kernel_lane_mappings(monkeypatch, log2g):
+    """The direct-load kernel with every lanes-per-row mapping."""
+    monkeypatch.setenv("SPC5_KERNEL", "0")
     monkeypatch.setenv("SPC5_LOG2_LANES_PER_ROW", str(log2g))
     A = synth.powerlaw(30_000, seed=12)
     x = synth.vector_uniform(A.ncols, seed=4)
     y_ref, scale = oracle.csr_spmv(A, x)
     for r, c in [(1, 8), (4, 4)]:
+        for body in ("0", "1"):
+            monkeypatch.setenv("SPC5_BODY", body)
+            M = convert(A, r, c)
+            assert M.info()["lanes_per_row"] == 1 << min(log2g, 5 - {1: 0, 4: 2}[r])
+            assert_within_tol(spmv(M, x), y_ref, scale)
+
+
+STAGED_SETTINGS = [
+    # (env, expect pieces) -- small stages force fat groups, segment tiles and pieces
+    ({}, False),
+    ({"SPC5_VCAP": "512", "SPC5_BCAP": "128"}, True),
+    ({"SPC5_VCAP": "512", "SPC5_BCAP": "128", "SPC5_STAGES": "2", "SPC5_CONSUMERS": "5"}, True),
+    ({"SPC5_LOG2G_GROUP": "2", "SPC5_BODY": "0"}, False),
+    ({"SPC5_LOG2G_GROUP": "1", "SPC5_BODY": "1", "SPC5_STAGES": "3", "SPC5_CONSUMERS": "1"}, False),
+    ({"SPC5_BODY": "2"}, False),
+    ({"SPC5_BODY": "3", "SPC5_VCAP": "512", "SPC5_BCAP": "128", "SPC5_CONSUMERS": "3"}, True),
+    ({"SPC5_BODY": "2", "SPC5_LOG2G_GROUP": "2", "SPC5_STAGES": "2", "SPC5_CONSUMERS": "6"}, False),
+]
+
+
+@pytest.mark.parametrize("setting", range(len(STAGED_SETTINGS)))
+@pytest.mark.parametrize("r,c", BETAS)
+def test_staged_kernel_plans(monkeypatch, setting, r, c):
+    """The staged kernel under different plans: group tiles only, fat groups
+    with segment tiles and long panels cut into pieces (fixup), a two-stage
+    ring with more consumers than stages, both row bodies."""
+    env, expect_pieces = STAGED_SETTINGS[setting]
+    for k, v in env.items():
+        monkeypatch.setenv(k, v)
+    mats = [synth.powerlaw(40_000, seed=21), synth.fem3d(4000, seed=3),
+            synth.bernoulli(333, 5000, 0.2, seed=2, integer_values=False)]
+    saw_pieces = False
+    for A in mats:
+        x = synth.vector_uniform(A.ncols, seed=6)
+        y_ref, scale = oracle.csr_spmv(A, x)
         M = convert(A, r, c)
-        assert M.info()["lanes_per_row"] == 1 << log2g
+        info = M.info()
+        saw_pieces |= info["long_panels"] > 0
+        y0 = synth.vector_normal(A.nrows, seed=3)
         assert_within_tol(spmv(M, x), y_ref, scale)
+        assert_within_tol(spmv(M, x, y0.copy(), -1.5, 0.5), -1.5 * y_ref + 0.5 * y0,
+                          1.5 * scale, extra=np.abs(0.5 * y0))
+        assert M.info()["device_error"] == 0
+    if expect_pieces:
+        assert saw_pieces
+
+
+def test_staged_integer_exact_with_pieces(monkeypatch):
+    """Integer data through pieces and fixup: bit-exact."""
+    monkeypatch.setenv("SPC5_VCAP", "512")
+    monkeypatch.setenv("SPC5_BCAP", "128")
+    A = synth.bernoulli(40, 20_000, 0.3, seed=9, integer_values=True)
+    x = synth.vector_int(A.ncols, -3, 3, seed=1)
+    for r, c in BETAS:
+        M = convert(A, r, c)
+        assert M.info()["long_panels"] > 0
+        assert np.array_equal(spmv(M, x), A.todense() @ x)

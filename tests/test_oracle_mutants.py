@@ -44,6 +44,9 @@ MUTANTS = [
     ("pack_shift", "<< (q * c);", "<< (q * 8);"),
     ("check_unsorted", "colidx[e] <= colidx[e - 1]) return ORACLE_EUNSORTED;",
      "colidx[e] < colidx[e - 1]) return ORACLE_EUNSORTED;"),
+    ("bf16_double_rounding", "bf16_from_f32_rne(round_to_odd_f32(in[i]))",
+     "bf16_from_f32_rne((float)in[i])"),
+    ("bf16_truncate", "b += 0x7FFFu + lsb;", "b += 0u * lsb;"),
 ]
 
 
@@ -139,7 +142,17 @@ def _pins(O: oracle.Oracle) -> list[str]:
     pin("alg1_exact", alg1_exact)
     pin("roundtrip", roundtrip)
     pin("rejects_duplicates", rejects_duplicates)
+    def quantize_exact():
+        from test_oracle_quantize import _cases, bf16_exact
+        v = _cases()
+        got = O.quantize(v, "bf16")
+        if not np.array_equal(got, np.array([bf16_exact(float(d)) for d in v], np.uint16)):
+            return False
+        return np.array_equal(O.quantize(v, "f32").view(np.uint32),
+                              v.astype(np.float32).view(np.uint32))
+
     pin("closed_form", closed_form)
+    pin("quantize_exact", quantize_exact)
     return failed
 
 
