@@ -72,15 +72,6 @@ void free_matrix(spc5_matrix *A) {
   delete A;
 }
 
-int default_log2_lanes(const spc5_matrix *A) {
-  const char *env = getenv("SPC5_LOG2_LANES_PER_ROW");
-  if (env && *env) {
-    int v = atoi(env);
-    if (v >= 0 && v <= 5) return v;
-  }
-  return 0;
-}
-
 }  // namespace
 }  // namespace spc5
 
@@ -128,8 +119,9 @@ spc5_status spc5_convert_csr(int64_t nrows, int64_t ncols, int64_t nnz, const in
             "block shape must be one of (1,8) (2,4) (2,8) (4,4) (4,8) (8,4)");
   RETURN_IF(nrows >= INT32_MAX || ncols >= INT32_MAX || nnz >= INT32_MAX, SPC5_EOVERFLOW,
             "sizes must stay below 2^31");
-  RETURN_IF(vals_dtype != SPC5_F64 || store_dtype != SPC5_F64, SPC5_EUNSUPPORTED,
-            "only FP64 values are implemented");
+  RETURN_IF(vals_dtype != SPC5_F64, SPC5_EUNSUPPORTED, "input values must be FP64");
+  RETURN_IF(store_dtype != SPC5_F64 && store_dtype != SPC5_F32 && store_dtype != SPC5_BF16,
+            SPC5_EINVAL, "unknown storage dtype");
   cudaStream_t s = (cudaStream_t)stream;
 
   spc5_matrix *A = new (std::nothrow) spc5_matrix();
@@ -173,7 +165,6 @@ spc5_status spc5_convert_csr(int64_t nrows, int64_t ncols, int64_t nnz, const in
     free_matrix(A);
     return st;
   }
-  A->log2_lanes_per_row = default_log2_lanes(A);
   *out = A;
   return SPC5_OK;
 }
@@ -193,7 +184,7 @@ spc5_status spc5_matrix_info(const spc5_matrix *A, spc5_info *info) {
   info->mask_bytes = A->r * A->c / 8;
   info->device_bytes = A->device_bytes;
   info->device = A->device;
-  info->lanes_per_row = A->kernel ? (1 << A->log2_group_lanes) : (1 << A->log2_lanes_per_row);
+  info->lanes_per_row = 1 << A->log2_group_lanes;
   info->launches_per_spmv = spmv_launches(A);
   info->ntiles = A->ntiles;
   info->long_panels = A->nlong;
@@ -221,8 +212,8 @@ spc5_status spc5_export(const spc5_matrix *A, const int32_t **block_rowptr,
   return SPC5_OK;
 }
 
-spc5_status spc5_spmv(const spc5_matrix *A, const double *x, double *y, double alpha,
-                      double beta, void *stream) {
+spc5_status spc5_spmv(const spc5_matrix *A, const void *x, void *y, double alpha, double beta,
+                      void *stream) {
   RETURN_IF(!A, SPC5_EINVAL, "NULL handle");
   RETURN_IF((A->ncols > 0 && !x) || (A->nrows > 0 && !y), SPC5_EINVAL, "NULL vector");
   cudaStream_t s = (cudaStream_t)stream;
@@ -231,27 +222,26 @@ spc5_status spc5_spmv(const spc5_matrix *A, const double *x, double *y, double a
   const bool host_y = A->nrows > 0 && is_host_pointer(y);
   if (!host_x && !host_y) return spmv_device(A, x, y, alpha, beta, s);
 
+  const size_t es = A->value_dtype == SPC5_F64 ? sizeof(double) : sizeof(float);
   spc5_matrix *M = const_cast<spc5_matrix *>(A);
   spc5_status st = SPC5_OK;
   if (host_x && !M->x_stage)
-    st = cuda_check(cudaMalloc((void **)&M->x_stage, (size_t)A->ncols * sizeof(double) + 16),
-                    "alloc x staging");
+    st = cuda_check(cudaMalloc(&M->x_stage, (size_t)A->ncols * es + 16), "alloc x staging");
   if (st == SPC5_OK && host_y && !M->y_stage)
-    st = cuda_check(cudaMalloc((void **)&M->y_stage, (size_t)A->nrows * sizeof(double) + 16),
-                    "alloc y staging");
+    st = cuda_check(cudaMalloc(&M->y_stage, (size_t)A->nrows * es + 16), "alloc y staging");
   if (st != SPC5_OK) return st;
-  const double *dx = x;
-  double *dy = y;
+  const void *dx = x;
+  void *dy = y;
   if (host_x) {
-    st = cuda_check(cudaMemcpyAsync(M->x_stage, x, (size_t)A->ncols * sizeof(double),
-                                    cudaMemcpyHostToDevice, s),
+    st = cuda_check(cudaMemcpyAsync(M->x_stage, x, (size_t)A->ncols * es, cudaMemcpyHostToDevice,
+                                    s),
                     "copy x");
     if (st != SPC5_OK) return st;
     dx = M->x_stage;
   }
   if (host_y) {
     if (beta != 0.0) {
-      st = cuda_check(cudaMemcpyAsync(M->y_stage, y, (size_t)A->nrows * sizeof(double),
+      st = cuda_check(cudaMemcpyAsync(M->y_stage, y, (size_t)A->nrows * es,
                                       cudaMemcpyHostToDevice, s),
                       "copy y");
       if (st != SPC5_OK) return st;
@@ -261,8 +251,7 @@ spc5_status spc5_spmv(const spc5_matrix *A, const double *x, double *y, double a
   st = spmv_device(A, dx, dy, alpha, beta, s);
   if (st != SPC5_OK) return st;
   if (host_y) {
-    st = cuda_check(cudaMemcpyAsync(y, dy, (size_t)A->nrows * sizeof(double),
-                                    cudaMemcpyDeviceToHost, s),
+    st = cuda_check(cudaMemcpyAsync(y, dy, (size_t)A->nrows * es, cudaMemcpyDeviceToHost, s),
                     "copy y back");
     if (st != SPC5_OK) return st;
   }

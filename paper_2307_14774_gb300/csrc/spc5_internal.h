@@ -45,20 +45,19 @@ struct spc5_matrix {
   int32_t *long_panels = nullptr;   // panels split into pieces
   int32_t *long_slots = nullptr;    // [2 * nlong]: first and end piece slot of each
   int64_t nlong = 0, npieces = 0;
-  double *partial = nullptr;        // npieces * r partial row sums
+  double *partial = nullptr;        // npieces * r partial row sums (FP64 or FP32 slots)
   int log2_group_lanes = 0;         // lanes per row in group tiles
   int vcap = 0, bcap = 0;           // stage capacity (values, blocks)
   int group_panels = 0;             // panels per group tile
   int stages = 0, consumers = 0, stage_bytes = 0;
   int body = 0;                     // consumer body: bit 0 = predicated loop over the c
                                     // bits (else set-bit loop), bit 1 = x staged in smem
-  int kernel = 1;                   // 1: staged tile kernel, 0: direct-load kernel
-  int log2_lanes_per_row = 0;       // direct-load kernel mapping
+  int kernel = 0;                   // 0: direct tile kernel, 1: staged tile kernel
   uint32_t *dev_error = nullptr;    // set by kernels on a timed-out wait
 
   // staging for host vectors in spc5_spmv
-  double *x_stage = nullptr;
-  double *y_stage = nullptr;
+  void *x_stage = nullptr;
+  void *y_stage = nullptr;
 };
 
 namespace spc5 {
@@ -82,8 +81,14 @@ spc5_status plan_tiles(spc5_matrix *A, const uint32_t *mask32, const int32_t *bo
                        cudaStream_t stream);
 
 // SpMV launch on device vectors.
-spc5_status spmv_device(const spc5_matrix *A, const double *x, double *y, double alpha,
-                        double beta, cudaStream_t stream);
+// x, y: FP64 for an FP64 matrix, FP32 for FP32 and BF16 matrices.
+spc5_status spmv_device(const spc5_matrix *A, const void *x, void *y, double alpha, double beta,
+                        cudaStream_t stream);
+
+// The same with the partial sums of split panels written to `partial`
+// (npieces * r doubles) instead of the handle's own buffer.
+spc5_status spmv_device_scratch(const spc5_matrix *A, const void *x, void *y, double alpha,
+                                double beta, cudaStream_t stream, void *partial);
 
 // Number of kernel launches one spmv_device call makes.
 int spmv_launches(const spc5_matrix *A);

@@ -202,18 +202,29 @@ spc5_status plan_tiles(spc5_matrix *A, const uint32_t *mask32, const int32_t *bo
   while ((1 << log2r) < r) ++log2r;
   const int log2g_segment = 5 - log2r;
 
-  // lanes per row in group tiles: about 8 block rounds per tile
+  // the staged kernel is built for FP64 values only
+  A->kernel = (A->value_dtype == SPC5_F64 && env_int("SPC5_KERNEL", 0)) ? 1 : 0;
+  const bool staged = A->kernel == 1;
+  // lanes per row in group tiles: a few block rounds per tile
   double avg_b = np > 0 ? (double)nb / (double)np : 0.0;
   double avg_v = np > 0 ? (double)A->nnz / (double)np : 0.0;
   int log2g = 0;
-  while (log2g < log2g_segment && avg_b / (double)(1 << log2g) > 12.0) ++log2g;
+  const double rounds = staged ? 12.0 : 8.0;
+  const int max_log2g = staged ? log2g_segment : std::min(2, log2g_segment);
+  while (log2g < max_log2g && avg_b / (double)(1 << log2g) > rounds) ++log2g;
   log2g = std::min(std::max(env_int("SPC5_LOG2G_GROUP", log2g), 0), log2g_segment);
   const int gp = 32 >> (log2r + log2g);
 
-  int vcap = round_up((int)(1.5 * gp * avg_v) + 64, 64);
-  vcap = std::min(std::max(vcap, 512), 4096);
-  int bcap = round_up((int)(1.5 * gp * avg_b) + 32, 32);
-  bcap = std::min(std::max(bcap, 128), 1024);
+  // Tile capacity.  Staged kernel: one shared-memory stage.  Direct kernel:
+  // only bounds the work of one warp (long panels are cut into pieces).
+  int vcap, bcap;
+  if (staged) {
+    vcap = std::min(std::max(round_up((int)(1.5 * gp * avg_v) + 64, 64), 512), 4096);
+    bcap = std::min(std::max(round_up((int)(1.5 * gp * avg_b) + 32, 32), 128), 1024);
+  } else {
+    vcap = std::min(std::max(round_up((int)(2.0 * gp * avg_v) + 64, 64), 2048), 8192);
+    bcap = std::min(std::max(round_up((int)(2.0 * gp * avg_b) + 32, 32), 256), 2048);
+  }
   vcap = env_int("SPC5_VCAP", vcap);
   bcap = env_int("SPC5_BCAP", bcap);
   if (vcap < 64 || bcap < 1) {
@@ -243,7 +254,7 @@ spc5_status plan_tiles(spc5_matrix *A, const uint32_t *mask32, const int32_t *bo
     consumers = std::min(std::max(env_int("SPC5_CONSUMERS", consumers), 1), 16);
   }
   stages = std::min(stages, env_int("SPC5_STAGES", stages));
-  if (stages < 2) {
+  if (staged && stages < 2) {
     set_error("pipeline stage does not fit shared memory");
     return SPC5_EINVAL;
   }
@@ -254,8 +265,7 @@ spc5_status plan_tiles(spc5_matrix *A, const uint32_t *mask32, const int32_t *bo
   A->stages = stages;
   A->consumers = consumers;
   A->stage_bytes = stage;
-  A->body = body;
-  A->kernel = env_int("SPC5_KERNEL", 1) ? 1 : 0;
+  A->body = staged ? body : (env_int("SPC5_BODY", 0) & 1);
 
   if (np == 0) return SPC5_OK;
   PlanParams P{np, nb, gp, vcap, bcap, vcap - 32, log2g, log2g_segment,

@@ -29,8 +29,11 @@
 // stage were cut into pieces by the planner; their row sums go to a partial
 // buffer that a fixup kernel adds in a fixed order.
 //
-// Direct kernel (SPC5_KERNEL=0): the same lane mapping reading global memory
-// directly; kept as a reference point for measurements.
+// Direct kernel (default, SPC5_KERNEL=0): the same tiles and lane mapping
+// reading global memory directly with many resident warps.  On GB300 the
+// FP64 path is bound by the FP64 pipe (2 FMA per cycle per SM), which needs
+// many warps in flight more than it needs shared-memory staging; the staged
+// kernel (SPC5_KERNEL=1) stays available for comparison.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -44,6 +47,7 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kDirectThreads = 256;
+constexpr int kDirectBlocksPerSM = 6;  // 48 warps per SM at <= 40 registers
 constexpr long long kWaitBudget = 4000000000LL;  // SM cycles (about 2 s) before a wait gives up
 
 enum : uint32_t { kErrProducerWait = 1u, kErrConsumerWait = 2u, kErrTileTooLarge = 4u };
@@ -74,17 +78,24 @@ struct Log2 {
   static constexpr int v = R == 1 ? 0 : R == 2 ? 1 : R == 4 ? 2 : 3;
 };
 
+// Stored value -> accumulation type.  FP64 and FP32 are used as they are;
+// a BF16 bit pattern is the upper half of an FP32, so widening is exact.
+__device__ __forceinline__ double widen(double v) { return v; }
+__device__ __forceinline__ float widen(float v) { return v; }
+__device__ __forceinline__ float widen(uint16_t v) { return __uint_as_float((uint32_t)v << 16); }
+
 // One row's contribution of one block: sum over set bits k of mq of
-// vals[running index] * x[col + k].
-template <int C, bool UNROLL>
-__device__ __forceinline__ double row_block(double acc, uint32_t mq, const double *vals,
-                                            const double *__restrict__ xp) {
+// vals[running index] * x[col + k], accumulated in AT (FP64 for FP64
+// values; FP32 for FP32 and BF16 values).
+template <int C, bool UNROLL, typename VT, typename AT>
+__device__ __forceinline__ AT row_block(AT acc, uint32_t mq, const VT *vals,
+                                        const AT *__restrict__ xp) {
   if (UNROLL) {
     int o = 0;
 #pragma unroll
     for (int t = 0; t < C; ++t) {
       if ((mq >> t) & 1u) {
-        acc = fma(vals[o], __ldg(xp + t), acc);
+        acc = fma((AT)widen(vals[o]), __ldg(xp + t), acc);
         ++o;
       }
     }
@@ -92,7 +103,7 @@ __device__ __forceinline__ double row_block(double acc, uint32_t mq, const doubl
     while (mq) {
       const int k = __ffs(mq) - 1;
       mq &= mq - 1u;
-      acc = fma(*vals++, __ldg(xp + k), acc);
+      acc = fma((AT)widen(*vals++), __ldg(xp + k), acc);
     }
   }
   return acc;
@@ -142,44 +153,80 @@ __device__ __forceinline__ int group_scan(int pc, int g, int G, int *total) {
   return incl - pc;
 }
 
-__device__ __forceinline__ double group_sum(double acc, int G) {
+template <typename AT>
+__device__ __forceinline__ AT group_sum(AT acc, int G) {
   for (int o = G >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o, G);
   return acc;
 }
 
 // ------------------------------------------------------------ direct kernel --
 
-template <int R, int C, bool UNROLL>
-__global__ void __launch_bounds__(kDirectThreads)
-    k_spmv_direct(int64_t npanels, int64_t nrows, const int32_t *__restrict__ block_rowptr,
-                  const int32_t *__restrict__ panel_vptr, const int32_t *__restrict__ block_colidx,
-                  const typename MaskType<R, C>::T *__restrict__ masks,
-                  const double *__restrict__ vals, const double *__restrict__ x,
-                  double *__restrict__ y, double alpha, double beta, int log2G) {
+// Tile-scheduled kernel reading global memory directly.  Each warp walks the
+// planner's tiles (warp w takes tiles w, w + nwarps, ...), prefetching the
+// next tile's descriptor, and pipelines each round's block metadata one
+// round ahead so that a round waits for one memory round trip (its values)
+// instead of two (metadata, then values).  Many resident warps (up to 64
+// per SM) keep the FP64 pipe and the memory system busy.
+template <int R, int C, bool UNROLL, typename VT, typename AT>
+__global__ void __launch_bounds__(kDirectThreads, kDirectBlocksPerSM)
+    k_spmv_tiles(const Tile *__restrict__ tiles, int64_t ntiles,
+                 const int32_t *__restrict__ block_rowptr, const int32_t *__restrict__ panel_vptr,
+                 const int32_t *__restrict__ block_colidx,
+                 const typename MaskType<R, C>::T *__restrict__ masks,
+                 const VT *__restrict__ vals, const AT *__restrict__ x, AT *__restrict__ y,
+                 AT *__restrict__ partial, AT alpha, AT beta, int64_t nrows) {
+  constexpr int LOG2R = Log2<R>::v;
   const int lane = threadIdx.x & 31;
-  const int G = 1 << log2G;
-  const int shift_j = Log2<R>::v + log2G;
-  const int ppw = 32 >> shift_j;
-  const int g = lane & (G - 1);
-  const int q = (lane >> log2G) & (R - 1);
-  const int j = lane >> shift_j;
-  const uint32_t row_low = (q == 0) ? 0u : ((1u << (q * C)) - 1u);
   const uint32_t cmask = (1u << C) - 1u;
-  const int64_t warp_id = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t w = warp_id; w * ppw < npanels; w += nwarps) {
-    const int64_t p = w * ppw + j;
-    const bool pvalid = p < npanels;
-    const int32_t b0 = pvalid ? block_rowptr[p] : 0;
-    const int32_t nbp = pvalid ? block_rowptr[p + 1] - b0 : 0;
-    int32_t v = pvalid ? panel_vptr[p] : 0;
+  int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  Tile cur{0, 0, 0, 0, 0, 0, 0, 0};
+  if (t < ntiles) cur = tiles[t];
+  while (t < ntiles) {
+    const int64_t tn = t + nwarps;
+    Tile nxt{0, 0, 0, 0, 0, 0, 0, 0};
+    if (tn < ntiles) nxt = tiles[tn];
+    const bool segment = (cur.mode & kSegment) != 0;
+    const int log2G = cur.mode & 15;
+    const int G = 1 << log2G;
+    const int shift_j = LOG2R + log2G;
+    const int g = lane & (G - 1);
+    const int q = (lane >> log2G) & (R - 1);
+    const int j = lane >> shift_j;
+    const uint32_t row_low = (q == 0) ? 0u : ((1u << (q * C)) - 1u);
+    bool pvalid;
+    int32_t bl, nbp, v;
+    if (segment) {
+      pvalid = (j == 0);
+      bl = cur.b0;
+      nbp = cur.b1 - cur.b0;
+      v = cur.v0;
+    } else {
+      const int64_t p = (int64_t)cur.p0 + j;
+      pvalid = p < cur.p1;
+      bl = pvalid ? block_rowptr[p] : 0;
+      nbp = pvalid ? block_rowptr[p + 1] - bl : 0;
+      v = pvalid ? panel_vptr[p] : 0;
+    }
     const int32_t maxnb = __reduce_max_sync(kFull, nbp);
-    double acc = 0.0;
+    uint32_t m_next = 0u;
+    int32_t c_next = 0;
+    if (g < nbp) {
+      m_next = (uint32_t)masks[bl + g];
+      c_next = block_colidx[bl + g];
+    }
+    AT acc = 0;
     for (int32_t it = 0; it < maxnb; it += G) {
-      const bool valid = (it + g) < nbp;
-      const int32_t b = b0 + it + g;
-      const uint32_t m = valid ? (uint32_t)masks[b] : 0u;
-      const int32_t col = valid ? block_colidx[b] : 0;
+      const uint32_t m = m_next;
+      const int32_t col = c_next;
+      const int32_t idx2 = it + G + g;
+      if (idx2 < nbp) {
+        m_next = (uint32_t)masks[bl + idx2];
+        c_next = block_colidx[bl + idx2];
+      } else {
+        m_next = 0u;
+        c_next = 0;
+      }
       const int pc = __popc(m);
       int total;
       const int excl = group_scan(pc, g, G, &total);
@@ -188,12 +235,20 @@ __global__ void __launch_bounds__(kDirectThreads)
       v += total;
     }
     acc = group_sum(acc, G);
-    const int64_t row = p * R + q;
-    if (pvalid && g == 0 && row < nrows) {
-      double out = alpha * acc;
-      if (beta != 0.0) out = fma(beta, y[row], out);
-      y[row] = out;
+    if (pvalid && g == 0) {
+      if (cur.mode & kPartial) {
+        partial[(int64_t)cur.slot * R + q] = acc;
+      } else {
+        const int64_t row = ((int64_t)cur.p0 + j) * R + q;
+        if (row < nrows) {
+          AT out = alpha * acc;
+          if (beta != (AT)0) out = fma(beta, y[row], out);
+          y[row] = out;
+        }
+      }
     }
+    cur = nxt;
+    t = tn;
   }
 }
 
@@ -424,7 +479,8 @@ __device__ void consumer(const StagedParams &P, uint8_t *stage0, uint64_t *full,
           int total;
           const int excl = group_scan(pc, g, G, &total);
           const int32_t off = v + excl + __popc(m & row_low);
-          acc = row_block<C, UNROLL>(acc, (m >> (q * C)) & cmask, vs + off, P.x + col);
+          acc = row_block<C, UNROLL, double, double>(acc, (m >> (q * C)) & cmask, vs + off,
+                                                     P.x + col);
           v += total;
         }
       } else {
@@ -513,21 +569,20 @@ __global__ void __launch_bounds__(32 * 17, 1) k_spmv_staged(const StagedParams P
 }
 
 // y rows of panels that were cut into pieces: add the pieces in order.
-template <int R>
+template <int R, typename AT>
 __global__ void k_fixup(int64_t nlong, const int32_t *long_panels, const int32_t *long_slots,
-                        const double *partial, double *y, double alpha, double beta,
-                        int64_t nrows) {
+                        const AT *partial, AT *y, AT alpha, AT beta, int64_t nrows) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nlong * R;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t l = i / R;
     const int q = (int)(i % R);
     const int64_t row = (int64_t)long_panels[l] * R + q;
-    double acc = 0.0;
+    AT acc = 0;
     for (int32_t s = long_slots[2 * l]; s < long_slots[2 * l + 1]; ++s)
       acc += partial[(int64_t)s * R + q];
     if (row < nrows) {
-      double out = alpha * acc;
-      if (beta != 0.0) out = fma(beta, y[row], out);
+      AT out = alpha * acc;
+      if (beta != (AT)0) out = fma(beta, y[row], out);
       y[row] = out;
     }
   }
@@ -546,7 +601,7 @@ int num_sms() {
 
 template <int R, int C, int BODY>
 cudaError_t launch_staged(const spc5_matrix *A, const double *x, double *y, double alpha,
-                          double beta, cudaStream_t s) {
+                          double beta, cudaStream_t s, double *partial) {
   constexpr int MB = R * C / 8;
   auto r16 = [](int v) { return (v + 15) / 16 * 16; };
   StagedParams P;
@@ -559,7 +614,7 @@ cudaError_t launch_staged(const spc5_matrix *A, const double *x, double *y, doub
   P.vals = reinterpret_cast<const double *>(A->values);
   P.x = x;
   P.y = y;
-  P.partial = A->partial;
+  P.partial = partial;
   P.alpha = alpha;
   P.beta = beta;
   P.nrows = A->nrows;
@@ -596,41 +651,66 @@ cudaError_t launch_staged(const spc5_matrix *A, const double *x, double *y, doub
   if (A->nlong > 0) {
     int64_t threads = A->nlong * R;
     int blocks = (int)std::min<int64_t>((threads + 255) / 256, 4096);
-    k_fixup<R><<<blocks, 256, 0, s>>>(A->nlong, A->long_panels, A->long_slots, A->partial, y,
-                                      alpha, beta, A->nrows);
+    k_fixup<R, double><<<blocks, 256, 0, s>>>(A->nlong, A->long_panels, A->long_slots, partial,
+                                              y, alpha, beta, A->nrows);
     e = cudaGetLastError();
   }
   return e;
 }
 
-template <int R, int C, bool UNROLL>
-cudaError_t launch_direct(const spc5_matrix *A, const double *x, double *y, double alpha,
-                          double beta, cudaStream_t s) {
+template <int R, int C, bool UNROLL, typename VT, typename AT>
+cudaError_t launch_direct(const spc5_matrix *A, const AT *x, AT *y, double alpha, double beta,
+                          cudaStream_t s, AT *partial) {
   using MaskT = typename MaskType<R, C>::T;
-  int log2G = A->log2_lanes_per_row;
-  if (Log2<R>::v + log2G > 5) log2G = 5 - Log2<R>::v;
-  const int ppw = 32 >> (Log2<R>::v + log2G);
-  int64_t warps = (A->npanels + ppw - 1) / ppw;
-  int64_t blocks = (warps + (kDirectThreads / 32) - 1) / (kDirectThreads / 32);
-  if (blocks < 1) blocks = 1;
-  if (blocks > (int64_t)num_sms() * 64) blocks = (int64_t)num_sms() * 64;
-  k_spmv_direct<R, C, UNROLL><<<(unsigned)blocks, kDirectThreads, 0, s>>>(
-      A->npanels, A->nrows, A->block_rowptr, A->panel_vptr, A->block_colidx,
-      (const MaskT *)A->masks, (const double *)A->values, x, y, alpha, beta, log2G);
-  return cudaGetLastError();
+  cudaError_t e = cudaSuccess;
+  if (A->ntiles > 0) {
+    const int warps_per_block = kDirectThreads / 32;
+    int64_t blocks = (A->ntiles + warps_per_block - 1) / warps_per_block;
+    const int64_t resident = (int64_t)num_sms() * kDirectBlocksPerSM;
+    if (blocks > resident) blocks = resident;
+    k_spmv_tiles<R, C, UNROLL, VT, AT><<<(unsigned)blocks, kDirectThreads, 0, s>>>(
+        A->tiles, A->ntiles, A->block_rowptr, A->panel_vptr, A->block_colidx,
+        (const MaskT *)A->masks, (const VT *)A->values, x, y, partial, (AT)alpha, (AT)beta,
+        A->nrows);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  if (A->nlong > 0) {
+    int64_t threads = A->nlong * R;
+    int fblocks = (int)std::min<int64_t>((threads + 255) / 256, 4096);
+    k_fixup<R, AT><<<fblocks, 256, 0, s>>>(A->nlong, A->long_panels, A->long_slots, partial, y,
+                                           (AT)alpha, (AT)beta, A->nrows);
+    e = cudaGetLastError();
+  }
+  return e;
+}
+
+template <int R, int C, typename VT, typename AT>
+cudaError_t launch_direct_body(const spc5_matrix *A, const void *x, void *y, double alpha,
+                               double beta, cudaStream_t s, void *partial) {
+  return (A->body & 1)
+             ? launch_direct<R, C, true, VT, AT>(A, (const AT *)x, (AT *)y, alpha, beta, s,
+                                                 (AT *)partial)
+             : launch_direct<R, C, false, VT, AT>(A, (const AT *)x, (AT *)y, alpha, beta, s,
+                                                  (AT *)partial);
 }
 
 template <int R, int C>
-cudaError_t launch(const spc5_matrix *A, const double *x, double *y, double alpha, double beta,
-                   cudaStream_t s) {
+cudaError_t launch(const spc5_matrix *A, const void *x, void *y, double alpha, double beta,
+                   cudaStream_t s, void *partial) {
+  if (A->value_dtype == SPC5_F32)
+    return launch_direct_body<R, C, float, float>(A, x, y, alpha, beta, s, partial);
+  if (A->value_dtype == SPC5_BF16)
+    return launch_direct_body<R, C, uint16_t, float>(A, x, y, alpha, beta, s, partial);
   if (A->kernel == 0)
-    return (A->body & 1) ? launch_direct<R, C, true>(A, x, y, alpha, beta, s)
-                         : launch_direct<R, C, false>(A, x, y, alpha, beta, s);
+    return launch_direct_body<R, C, double, double>(A, x, y, alpha, beta, s, partial);
+  const double *xd = (const double *)x;
+  double *yd = (double *)y, *pd = (double *)partial;
   switch (A->body) {
-    case 0: return launch_staged<R, C, 0>(A, x, y, alpha, beta, s);
-    case 1: return launch_staged<R, C, 1>(A, x, y, alpha, beta, s);
-    case 2: return launch_staged<R, C, 2>(A, x, y, alpha, beta, s);
-    default: return launch_staged<R, C, 3>(A, x, y, alpha, beta, s);
+    case 0: return launch_staged<R, C, 0>(A, xd, yd, alpha, beta, s, pd);
+    case 1: return launch_staged<R, C, 1>(A, xd, yd, alpha, beta, s, pd);
+    case 2: return launch_staged<R, C, 2>(A, xd, yd, alpha, beta, s, pd);
+    default: return launch_staged<R, C, 3>(A, xd, yd, alpha, beta, s, pd);
   }
 }
 
@@ -638,26 +718,30 @@ cudaError_t launch(const spc5_matrix *A, const double *x, double *y, double alph
 
 int spmv_launches(const spc5_matrix *A) {
   if (A->nrows == 0) return 0;
-  if (A->kernel == 0) return 1;
   return (A->ntiles > 0 ? 1 : 0) + (A->nlong > 0 ? 1 : 0);
 }
 
-spc5_status spmv_device(const spc5_matrix *A, const double *x, double *y, double alpha,
-                        double beta, cudaStream_t s) {
+spc5_status spmv_device_scratch(const spc5_matrix *A, const void *x, void *y, double alpha,
+                                double beta, cudaStream_t s, void *partial) {
   if (A->nrows == 0) return SPC5_OK;
   cudaError_t e;
   switch (A->r * 100 + A->c) {
-    case 108: e = launch<1, 8>(A, x, y, alpha, beta, s); break;
-    case 204: e = launch<2, 4>(A, x, y, alpha, beta, s); break;
-    case 208: e = launch<2, 8>(A, x, y, alpha, beta, s); break;
-    case 404: e = launch<4, 4>(A, x, y, alpha, beta, s); break;
-    case 408: e = launch<4, 8>(A, x, y, alpha, beta, s); break;
-    case 804: e = launch<8, 4>(A, x, y, alpha, beta, s); break;
+    case 108: e = launch<1, 8>(A, x, y, alpha, beta, s, partial); break;
+    case 204: e = launch<2, 4>(A, x, y, alpha, beta, s, partial); break;
+    case 208: e = launch<2, 8>(A, x, y, alpha, beta, s, partial); break;
+    case 404: e = launch<4, 4>(A, x, y, alpha, beta, s, partial); break;
+    case 408: e = launch<4, 8>(A, x, y, alpha, beta, s, partial); break;
+    case 804: e = launch<8, 4>(A, x, y, alpha, beta, s, partial); break;
     default:
       set_error("unsupported block shape");
       return SPC5_EUNSUPPORTED_RC;
   }
   return cuda_check(e, "spmv launch");
+}
+
+spc5_status spmv_device(const spc5_matrix *A, const void *x, void *y, double alpha, double beta,
+                        cudaStream_t s) {
+  return spmv_device_scratch(A, x, y, alpha, beta, s, A->partial);
 }
 
 }  // namespace spc5

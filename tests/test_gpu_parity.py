@@ -171,18 +171,26 @@ def test_invalid_csr_is_rejected_on_device():
 
 @pytest.mark.parametrize("log2g", [0, 1, 2, 3])
 def test_direct_kernel_lane_mappings(monkeypatch, log2g):
-    """The direct-load kernel with every lanes-per-row mapping."""
+    """The direct tile kernel with every lanes-per-row mapping and both row
+    bodies, with and without long-panel pieces."""
     monkeypatch.setenv("SPC5_KERNEL", "0")
-    monkeypatch.setenv("SPC5_LOG2_LANES_PER_ROW", str(log2g))
+    monkeypatch.setenv("SPC5_LOG2G_GROUP", str(log2g))
     A = synth.powerlaw(30_000, seed=12)
     x = synth.vector_uniform(A.ncols, seed=4)
     y_ref, scale = oracle.csr_spmv(A, x)
-    for r, c in [(1, 8), (4, 4)]:
+    for r, c in [(1, 8), (4, 4), (8, 4)]:
         for body in ("0", "1"):
-            monkeypatch.setenv("SPC5_BODY", body)
-            M = convert(A, r, c)
-            assert M.info()["lanes_per_row"] == 1 << min(log2g, 5 - {1: 0, 4: 2}[r])
-            assert_within_tol(spmv(M, x), y_ref, scale)
+            for vcap in ("", "2048"):
+                monkeypatch.setenv("SPC5_BODY", body)
+                if vcap:
+                    monkeypatch.setenv("SPC5_VCAP", vcap)
+                    monkeypatch.setenv("SPC5_BCAP", "256")
+                else:
+                    monkeypatch.delenv("SPC5_VCAP", raising=False)
+                    monkeypatch.delenv("SPC5_BCAP", raising=False)
+                M = convert(A, r, c)
+                assert M.info()["lanes_per_row"] == 1 << min(log2g, 5 - {1: 0, 4: 2, 8: 3}[r])
+                assert_within_tol(spmv(M, x), y_ref, scale)
 
 
 STAGED_SETTINGS = [
@@ -205,6 +213,7 @@ def test_staged_kernel_plans(monkeypatch, setting, r, c):
     with segment tiles and long panels cut into pieces (fixup), a two-stage
     ring with more consumers than stages, both row bodies."""
     env, expect_pieces = STAGED_SETTINGS[setting]
+    monkeypatch.setenv("SPC5_KERNEL", "1")
     for k, v in env.items():
         monkeypatch.setenv(k, v)
     mats = [synth.powerlaw(40_000, seed=21), synth.fem3d(4000, seed=3),
@@ -225,8 +234,10 @@ def test_staged_kernel_plans(monkeypatch, setting, r, c):
         assert saw_pieces
 
 
-def test_staged_integer_exact_with_pieces(monkeypatch):
-    """Integer data through pieces and fixup: bit-exact."""
+@pytest.mark.parametrize("kernel", ["0", "1"])
+def test_integer_exact_with_pieces(monkeypatch, kernel):
+    """Integer data through pieces and fixup: bit-exact, both kernels."""
+    monkeypatch.setenv("SPC5_KERNEL", kernel)
     monkeypatch.setenv("SPC5_VCAP", "512")
     monkeypatch.setenv("SPC5_BCAP", "128")
     A = synth.bernoulli(40, 20_000, 0.3, seed=9, integer_values=True)
