@@ -59,6 +59,7 @@ def parse_args():
     ap.add_argument("--matrices", default=",".join(MATRICES))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-precision", action="store_true")
     ap.add_argument("--cases-out", default=None, help="write the per-case table here")
     return ap.parse_args()
 
@@ -79,12 +80,21 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+VALUE_BYTES = {0: 8, 1: 4, 2: 2}  # FP64, FP32, BF16 storage
+# FP64 FMA rate of the GB300 SM: 2 per cycle (ncu: sm__sass_thread_inst_executed_op_dfma
+# peak_sustained = 304 per cycle over 152 SMs), at the 2070 MHz maximum SM clock.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+
+
 def algorithmic_bytes(info: dict) -> int:
-    """Bytes an FP64 SpMV must move: values + block column indices + masks +
-    panel pointers (block_rowptr and panel value offsets) + x + y."""
+    """Bytes an SpMV must move: values + block column indices + masks + panel
+    pointers (block_rowptr and panel value offsets) + x + y.  FP64 matrices
+    use FP64 vectors, FP32/BF16 matrices FP32 vectors."""
     nb, npan = info["nblocks"], info["npanels"]
-    return (8 * info["nnz"] + 4 * nb + info["mask_bytes"] * nb + 8 * (npan + 1)
-            + 8 * info["ncols"] + 8 * info["nrows"])
+    sv = VALUE_BYTES[info["value_dtype"]]
+    sx = 8 if info["value_dtype"] == 0 else 4
+    return (sv * info["nnz"] + 4 * nb + info["mask_bytes"] * nb + 8 * (npan + 1)
+            + sx * info["ncols"] + sx * info["nrows"])
 
 
 def kernel_source_hash() -> str:
@@ -174,6 +184,25 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def roofline_object(achieved_gbs, achieved_tflops, hbm, peak_kind, traffic, bytes_per_step,
+                    flops_per_step):
+    """The binding roofline of the FP64 SpMV kernel over a step: whichever of
+    HBM bytes and FP64 FMAs needs more time at its peak."""
+    t_hbm = bytes_per_step / (hbm * 1e9)
+    t_alu = flops_per_step / (FP64_PEAK_TFLOPS * 1e12)
+    hbm_part = {"achieved": round(achieved_gbs, 1), "peak": hbm, "unit": "GB/s",
+                "frac": round(achieved_gbs / hbm, 4), "peak_kind": peak_kind}
+    alu_part = {"achieved": round(achieved_tflops, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
+                "unit": "TFLOP/s", "frac": round(achieved_tflops / FP64_PEAK_TFLOPS, 4),
+                "peak_kind": "derived: 152 SMs x 2 FP64 FMA/cycle x 2 flop x 2070 MHz"}
+    main, other = (alu_part, hbm_part) if t_alu > t_hbm else (hbm_part, alu_part)
+    out = {"bound": "alu" if t_alu > t_hbm else "hbm", **main, "traffic": traffic,
+           "kernel": "spc5 SpMV (FP64), all 24 launches of a step",
+           "bytes_per_step": bytes_per_step, "flops_per_step": flops_per_step,
+           "other": other}
+    return out
+
+
 # ------------------------------------------------------------------ native --
 
 def build_cases(names, torch, spc5, synth, log):
@@ -201,6 +230,71 @@ def build_cases(names, torch, spc5, synth, log):
         del dev
         torch.cuda.synchronize()
     return cases, hosts
+
+
+PRECISION_TOL = {"f32": 2e-6, "bf16": 1e-2}  # |y - y_fp64| <= tol * sum_j |a_ij x_j|
+
+
+def precision_section(hosts, torch, spc5, stream, hbm, case_rows, log, reps=10):
+    """FP32 and BF16 value storage (FP32 x, y, accumulation) on the 27-point
+    and FEM matrices, every beta: time per SpMV, HBM fraction, speed-up over
+    the FP64 case of the main step, and the largest error relative to the
+    stated tolerance, measured against the FP64 product of the same matrix
+    with S_i = sum_j |a_ij x_j| computed as an FP64 product of |A| and |x|."""
+    import numpy as np
+    fp64_us = {(r["matrix"], r["beta"]): r["us"] for r in case_rows}
+    rows = []
+    for name in ("stencil27", "fem3d"):
+        if name not in hosts:
+            continue
+        A, x = hosts[name]
+        dev = [torch.from_numpy(a).cuda() for a in (A.rowptr, A.colidx, A.vals)]
+        dabs = torch.from_numpy(np.abs(A.vals)).cuda()
+        x64 = torch.from_numpy(x).cuda()
+        xabs = torch.from_numpy(np.abs(x)).cuda()
+        x32 = x64.float()
+        y64 = torch.empty(A.nrows, dtype=torch.float64, device="cuda")
+        sc = torch.empty(A.nrows, dtype=torch.float64, device="cuda")
+        M64 = spc5.spc5_convert_csr(A.nrows, A.ncols, A.nnz, *dev, r=4, c=8)
+        spc5.spc5_spmv(M64, x64, y64, 1.0, 0.0, stream)
+        Mabs = spc5.spc5_convert_csr(A.nrows, A.ncols, A.nnz, dev[0], dev[1], dabs, r=4, c=8)
+        spc5.spc5_spmv(Mabs, xabs, sc, 1.0, 0.0, stream)
+        del M64, Mabs
+        y32 = torch.empty(A.nrows, dtype=torch.float32, device="cuda")
+        for r, c in BETAS:
+            for dt, code in (("f32", spc5.SPC5_F32), ("bf16", spc5.SPC5_BF16)):
+                M = spc5.spc5_convert_csr(A.nrows, A.ncols, A.nnz, *dev, store_dtype=code, r=r,
+                                          c=c)
+                info = M.info()
+                for _ in range(3):
+                    spc5.spc5_spmv(M, x32, y32, 1.0, 0.0, stream)
+                evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                       for _ in range(reps)]
+                for e0, e1 in evs:
+                    e0.record(stream)
+                    spc5.spc5_spmv(M, x32, y32, 1.0, 0.0, stream)
+                    e1.record(stream)
+                torch.cuda.synchronize()
+                us = statistics.median(e0.elapsed_time(e1) for e0, e1 in evs) * 1e3
+                err = (y32.double() - y64).abs()
+                bound = PRECISION_TOL[dt] * sc
+                ratio = float(torch.where(bound > 0, err / bound,
+                                          torch.where(err > 0, torch.full_like(err, float("inf")),
+                                                      torch.zeros_like(err))).max())
+                b = algorithmic_bytes(info)
+                ref = fp64_us.get((name, f"{r}x{c}"))
+                rows.append({"matrix": name, "beta": f"{r}x{c}", "dtype": dt,
+                             "us": round(us, 2),
+                             "gflops": round(2.0 * A.nnz / (us * 1e-6) / 1e9, 1),
+                             "gbs": round(b / (us * 1e-6) / 1e9, 1),
+                             "frac": round(b / (us * 1e-6) / 1e9 / hbm, 3),
+                             "speedup_vs_fp64": round(ref / us, 2) if ref else None,
+                             "tol": PRECISION_TOL[dt], "max_err_over_tol": round(ratio, 4)})
+                del M
+        del dev, dabs
+        torch.cuda.synchronize()
+        log(f"precision rows for {name} done")
+    return rows
 
 
 def cpu_baseline_sample(hosts, oracle, log):
@@ -293,6 +387,7 @@ def run_native(args):
     bytes_per_step = sum(cs["bytes"] for cs in cases)
     hbm, peak_kind = measured_peaks()
     achieved = bytes_per_step * args.steps / (sum_launch_ms * 1e-3) / 1e9
+    achieved_tflops = flops_per_step * args.steps / (sum_launch_ms * 1e-3) / 1e12
     launches_per_spmv = max(cs["info"].get("launches_per_spmv", 1) for cs in cases)
     traffic_tab = ncu_traffic()
     traffic = None
@@ -303,12 +398,17 @@ def run_native(args):
     case_rows = []
     for cs, ms in zip(cases, per_case_ms):
         gbs = cs["bytes"] / (ms * 1e-3) / 1e9
+        gf = 2.0 * cs["nnz"] / (ms * 1e-3) / 1e9
+        t_hbm = cs["bytes"] / (hbm * 1e9) * 1e6
+        t_fp64 = 2.0 * cs["nnz"] / (FP64_PEAK_TFLOPS * 1e12) * 1e6
         case_rows.append({"matrix": cs["matrix"], "beta": f"{cs['r']}x{cs['c']}",
                           "nnz": cs["nnz"], "nblocks": cs["info"]["nblocks"],
                           "filling": round(cs["info"]["filling"], 4),
-                          "us": round(ms * 1e3, 2),
-                          "gflops": round(2.0 * cs["nnz"] / (ms * 1e-3) / 1e9, 1),
+                          "us": round(ms * 1e3, 2), "gflops": round(gf, 1),
                           "gbs": round(gbs, 1), "frac": round(gbs / hbm, 3),
+                          "fp64_frac": round(gf / (FP64_PEAK_TFLOPS * 1e3), 3),
+                          "bound": "alu" if t_fp64 > t_hbm else "hbm",
+                          "floor_us": round(max(t_hbm, t_fp64), 2),
                           "convert_ms": round(cs["convert_s"] * 1e3, 2)})
 
     result = {
@@ -323,11 +423,8 @@ def run_native(args):
                    "l2": "inputs larger than L2: every SpMV streams >= "
                          f"{min(cs['bytes'] for cs in cases) / 1e6:.0f} MB (L2 129 MB)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm,
-                     "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": traffic,
-                     "peak_kind": peak_kind,
-                     "kernel": "spc5 SpMV kernel, all 24 launches of a step",
-                     "bytes_per_step": bytes_per_step},
+        "roofline": roofline_object(achieved, achieved_tflops, hbm, peak_kind, traffic,
+                                    bytes_per_step, flops_per_step),
         "gpu_launches": nlaunch * launches_per_spmv * args.steps,
         "cases": case_rows,
         "convert": {"ms_total": round(sum(cs["convert_s"] for cs in cases) * 1e3, 1),
@@ -336,6 +433,19 @@ def run_native(args):
     clocks = clk.summary()
     if clocks:
         result["clocks"] = clocks
+
+    if not args.no_precision and rank == 0:
+        prec = precision_section(hosts, torch, spc5, stream, hbm, case_rows, log)
+        result["precision"] = {
+            "note": "FP32/BF16 value storage, FP32 x/y/accumulation; error vs the FP64 product "
+                    "of the same matrix, relative to tol * sum_j |a_ij x_j|",
+            "rows": prec,
+            "summary": {dt: {"gflops_total": round(
+                sum(2.0 * cs_nnz for cs_nnz in [hosts[rw["matrix"]][0].nnz for rw in prec
+                                                if rw["dtype"] == dt])
+                / (sum(rw["us"] for rw in prec if rw["dtype"] == dt) * 1e-6) / 1e9, 1),
+                "max_err_over_tol": max(rw["max_err_over_tol"] for rw in prec if rw["dtype"] == dt)}
+                for dt in ("f32", "bf16")} if prec else {}}
 
     # end to end through the C-ABI with host vectors: every step copies x from
     # pinned host memory and reads y back

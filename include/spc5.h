@@ -38,8 +38,10 @@ extern "C" {
 /* Opaque handle of a matrix converted to beta(r,c); owns its device arrays. */
 typedef struct spc5_matrix spc5_matrix;
 
-/* Element types.  Values may be stored in FP64 (the default); FP32 and BF16
- * storage are reserved and currently return SPC5_EUNSUPPORTED. */
+/* Element types.  Input values are FP64; the converted values are stored
+ * in FP64, FP32 or BF16 (rounded to nearest, ties to even).  An FP64 matrix
+ * multiplies FP64 vectors with FP64 accumulation; FP32 and BF16 matrices
+ * multiply FP32 vectors with FP32 accumulation. */
 typedef enum { SPC5_F64 = 0, SPC5_F32 = 1, SPC5_BF16 = 2 } spc5_dtype;
 
 typedef enum {
@@ -88,8 +90,9 @@ typedef struct {
  * nrows, ncols, nnz  matrix shape and number of stored entries
  * rowptr[nrows+1]    CSR row pointers, rowptr[0] = 0, rowptr[nrows] = nnz
  * colidx[nnz]        column of every entry, strictly ascending in each row
- * vals[nnz]          values of type vals_dtype (only SPC5_F64 is accepted)
- * store_dtype        storage type of the converted values (SPC5_F64)
+ * vals[nnz]          values of type vals_dtype (must be SPC5_F64)
+ * store_dtype        storage type of the converted values: SPC5_F64, or
+ *                    SPC5_F32 / SPC5_BF16 (round to nearest even from FP64)
  * r, c               block shape; (1,8) (2,4) (2,8) (4,4) (4,8) (8,4) are
  *                    supported, others give SPC5_EUNSUPPORTED_RC
  * stream             stream the conversion runs on; the call returns after
@@ -132,15 +135,17 @@ spc5_status spc5_export(const spc5_matrix *A, const int32_t **block_rowptr,
 /*
  * spc5_spmv -- y = alpha * A x + beta * y (Algorithm 1 computes y = A x).
  *
- * x[ncols], y[nrows] are FP64 vectors in device or host memory.  With
- * beta == 0, y is not read (no NaN or Inf from a previous y propagates).
+ * x[ncols], y[nrows] are vectors in device or host memory: FP64 for an
+ * FP64 matrix, FP32 for FP32 and BF16 matrices (accumulation in the vector
+ * type).  With beta == 0, y is not read (no NaN or Inf from a previous y
+ * propagates).
  * Device vectors: asynchronous on `stream`.  Host vectors: copied through
  * device buffers owned by A; the call returns when y is on the host.  x and y
  * must not overlap.  Concurrent calls on the same handle with host vectors
  * must be serialised by the caller.
  */
-spc5_status spc5_spmv(const spc5_matrix *A, const double *x, double *y, double alpha,
-                      double beta, void *stream);
+spc5_status spc5_spmv(const spc5_matrix *A, const void *x, void *y, double alpha, double beta,
+                      void *stream);
 
 /* Release the handle and every device array it owns (synchronising). */
 spc5_status spc5_destroy(spc5_matrix *A);

@@ -219,4 +219,7 @@ def export_tensors(A: Matrix) -> dict:
             "block_colidx": view(p["block_colidx"], nb, "<i4"),
             # packed mask words as raw little-endian bytes, mask_bytes per block
             "block_masks": view(p["block_masks"], nb * info["mask_bytes"], "|u1"),
-            "values": view(p["values"], nnz, "<f8")}
+            # raw value storage: FP64, FP32 or BF16 bit patterns, as bytes for non-FP64
+            "values": (view(p["values"], nnz, "<f8") if info["value_dtype"] == SPC5_F64 else
+                       view(p["values"], nnz * (4 if info["value_dtype"] == SPC5_F32 else 2),
+                            "|u1"))}
