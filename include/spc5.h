@@ -147,6 +147,34 @@ spc5_status spc5_export(const spc5_matrix *A, const int32_t **block_rowptr,
 spc5_status spc5_spmv(const spc5_matrix *A, const void *x, void *y, double alpha, double beta,
                       void *stream);
 
+/*
+ * spc5_spmv_noalloc -- the same product as spc5_spmv for callers that must
+ * not allocate device memory during the call (for example while a CUDA
+ * graph is being captured on `stream`, or in a loop that must never reach
+ * the allocator).  The paper has no counterpart: this is a deployment
+ * variant of Algorithm 1's product, not part of the method.
+ *
+ * x[ncols], y[nrows] must be in device (or managed) memory, typed as for
+ * spc5_spmv (FP64 for an FP64 matrix, FP32 otherwise);
+ * host vectors give SPC5_EINVAL, since copying them needs staging buffers.
+ * The partial sums of panels that the work plan splits into pieces go to a
+ * fixed array inside the library (1 MiB = 131072 doubles, kept on every
+ * GPU that loads the library until the process exits) instead of the
+ * handle's own buffer; a matrix needing more than 131072 partial sums
+ * (pieces * r) is rejected with SPC5_EOVERFLOW before any work is queued.
+ * The call makes no cudaMalloc, cudaFree or other allocating call.
+ *
+ * The array is shared by every call on a device: concurrent calls whose
+ * kernels overlap on the GPU (different streams, or different handles at
+ * once) race on it and must be serialised by the caller.  No state carries
+ * over between calls (each call writes every partial sum it reads).
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.
+ */
+spc5_status spc5_spmv_noalloc(const spc5_matrix *A, const void *x, void *y, double alpha,
+                              double beta, void *stream);
+
 /* Release the handle and every device array it owns (synchronising). */
 spc5_status spc5_destroy(spc5_matrix *A);
 

@@ -1,0 +1,112 @@
+// spc5_spmv_noalloc: the SpMV for callers that must not allocate.
+//
+// Some callers cannot call cudaMalloc at the moment they need a product: a
+// solver step running while a CUDA graph is being captured on its stream, a
+// real-time loop that must not hit the allocator (or its implicit device
+// synchronisation), or code running under a memory budget that was fixed at
+// start-up.  spc5_spmv itself allocates nothing for device vectors either,
+// but it writes the partial sums of panels split into pieces to a buffer
+// owned by the matrix handle.  This entry point writes them instead to a
+// fixed array compiled into the library (file-scope __device__ storage), so
+// the whole call allocates nothing and touches no per-matrix scratch.
+//
+// The array holds kNoallocScratchDoubles doubles (1 MiB); every GPU that
+// loads the library keeps it until the process exits.  A matrix whose split
+// panels need more partial sums is rejected with SPC5_EOVERFLOW.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <mutex>
+#include <string>
+
+#include "spc5_internal.h"
+
+namespace spc5 {
+namespace {
+
+constexpr int64_t kNoallocScratchDoubles = 131072;  // 1 MiB
+constexpr int kMaxDevices = 64;
+
+// Shared by every call on a device.  Every slot a call reads is written
+// earlier in the same call (each piece writes its own r sums before the
+// fixup adds them), so nothing needs clearing; calls that overlap on the
+// GPU race on it.
+static __device__ __align__(256) double g_noalloc_scratch[kNoallocScratchDoubles];
+
+std::mutex g_mutex;
+double *g_scratch_addr[kMaxDevices] = {};
+
+// Device address of the array on `dev`, looked up once per device with that
+// device current.  (In host code the array's name is only a host-side
+// stand-in, not a device address.)
+spc5_status scratch_address(int dev, double **out) {
+  if (dev < 0 || dev >= kMaxDevices) {
+    set_error("device ordinal out of range for spc5_spmv_noalloc");
+    return SPC5_EINVAL;
+  }
+  std::lock_guard<std::mutex> lock(g_mutex);
+  if (!g_scratch_addr[dev]) {
+    int cur = -1;
+    spc5_status st = cuda_check(cudaGetDevice(&cur), "cudaGetDevice");
+    if (st != SPC5_OK) return st;
+    if (cur != dev) {
+      st = cuda_check(cudaSetDevice(dev), "cudaSetDevice");
+      if (st != SPC5_OK) return st;
+    }
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (cur != dev) cudaSetDevice(cur);
+    st = cuda_check(e, "cudaGetSymbolAddress(noalloc scratch)");
+    if (st != SPC5_OK) return st;
+    g_scratch_addr[dev] = static_cast<double *>(p);
+  }
+  *out = g_scratch_addr[dev];
+  return SPC5_OK;
+}
+
+bool device_readable(const void *p) {
+  cudaPointerAttributes attr;
+  if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+}  // namespace spc5
+
+using namespace spc5;
+
+extern "C" spc5_status spc5_spmv_noalloc(const spc5_matrix *A, const void *x, void *y,
+                                         double alpha, double beta, void *stream) {
+  if (!A) {
+    set_error("NULL handle");
+    return SPC5_EINVAL;
+  }
+  if (A->nrows == 0) return SPC5_OK;
+  if ((A->ncols > 0 && (!x || !device_readable(x))) || !y || !device_readable(y)) {
+    set_error("spc5_spmv_noalloc takes device vectors only (host vectors need staging buffers)");
+    return SPC5_EINVAL;
+  }
+  const int64_t need = A->npieces * A->r;
+  if (need > kNoallocScratchDoubles) {
+    set_error("the matrix's split panels need " + std::to_string(need) +
+              " partial sums; spc5_spmv_noalloc holds at most " +
+              std::to_string(kNoallocScratchDoubles));
+    return SPC5_EOVERFLOW;
+  }
+  double *scratch = nullptr;
+  spc5_status st = scratch_address(A->device, &scratch);
+  if (st != SPC5_OK) return st;
+  int cur = -1;
+  st = cuda_check(cudaGetDevice(&cur), "cudaGetDevice");
+  if (st != SPC5_OK) return st;
+  if (cur != A->device) {
+    st = cuda_check(cudaSetDevice(A->device), "cudaSetDevice");
+    if (st != SPC5_OK) return st;
+  }
+  st = spmv_device_scratch(A, x, y, alpha, beta, (cudaStream_t)stream, scratch);
+  if (cur != A->device) cudaSetDevice(cur);
+  return st;
+}

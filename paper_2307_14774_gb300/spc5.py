@@ -24,7 +24,7 @@ SUPPORTED_RC = ((1, 8), (2, 4), (2, 8), (4, 4), (4, 8), (8, 4))
 
 # Exported symbols declared in include/spc5.h.
 EXPORTS = ("spc5_convert_csr", "spc5_matrix_info", "spc5_export", "spc5_spmv", "spc5_destroy",
-           "spc5_status_str", "spc5_last_error")
+           "spc5_status_str", "spc5_last_error", "spc5_spmv_noalloc")
 
 
 class SPC5Error(RuntimeError):
@@ -71,6 +71,8 @@ def load(path: str | None = None):
         lib.spc5_matrix_info.argtypes = [vp, ctypes.POINTER(Info)]
         lib.spc5_export.argtypes = [vp] + [ctypes.POINTER(vp)] * 5
         lib.spc5_spmv.argtypes = [vp, vp, vp, dbl, dbl, vp]
+        lib.spc5_spmv_noalloc.argtypes = [vp, vp, vp, dbl, dbl, vp]
+        lib.spc5_spmv_noalloc.restype = ci
         lib.spc5_destroy.argtypes = [vp]
         for f in (lib.spc5_convert_csr, lib.spc5_matrix_info, lib.spc5_export, lib.spc5_spmv,
                   lib.spc5_destroy):
@@ -172,6 +174,14 @@ def spc5_spmv(A: Matrix, x, y, alpha: float = 1.0, beta: float = 0.0, stream=Non
     """y = alpha * A x + beta * y (FP64 vectors, device or host)."""
     _check(load().spc5_spmv(A.handle, _ptr(x), _ptr(y), float(alpha), float(beta),
                             _stream_ptr(stream)))
+
+
+def spc5_spmv_noalloc(A: Matrix, x, y, alpha: float = 1.0, beta: float = 0.0,
+                      stream=None) -> None:
+    """y = alpha * A x + beta * y without any device allocation (device
+    vectors only; partial sums in the library's fixed scratch array)."""
+    _check(load().spc5_spmv_noalloc(A.handle, _ptr(x), _ptr(y), float(alpha), float(beta),
+                                    _stream_ptr(stream)))
 
 
 def spc5_destroy(A: Matrix) -> None:
