@@ -38,6 +38,7 @@ extern "C" {
 /* Opaque handle of a matrix converted to beta(r,c); owns its device arrays. */
 typedef struct spc5_matrix spc5_matrix;
 
+
 /* Element types.  Input values are FP64; the converted values are stored
  * in FP64, FP32 or BF16 (rounded to nearest, ties to even).  An FP64 matrix
  * multiplies FP64 vectors with FP64 accumulation; FP32 and BF16 matrices
@@ -146,6 +147,38 @@ spc5_status spc5_export(const spc5_matrix *A, const int32_t **block_rowptr,
  */
 spc5_status spc5_spmv(const spc5_matrix *A, const void *x, void *y, double alpha, double beta,
                       void *stream);
+
+/*
+ * spc5_spmv_t -- dx = alpha * A^T g + beta * dx, the product with the
+ * transposed matrix (the input gradient of y = A x: dx = A^T dy).  Walks
+ * the stored blocks of Algorithm 1's layout and scatters
+ * values[idxVal] * g[row] into dx[idxCol + k] with atomic additions, so the
+ * summation order (and the last bits of the result) may differ from run to
+ * run.  g[nrows] and dx[ncols] are device vectors typed as for spc5_spmv.
+ * With beta == 0, dx is not read.  Asynchronous on `stream`.
+ */
+spc5_status spc5_spmv_t(const spc5_matrix *A, const void *g, void *dx, double alpha, double beta,
+                        void *stream);
+
+/*
+ * spc5_values_grad -- dvals[e] = alpha * g[row(e)] * x[col(e)] for every
+ * stored entry e (the gradient of <g, A x> with respect to the matrix
+ * values), computed over the stored mask bits and written in CSR order
+ * (dvals[e] belongs to the e-th entry of the CSR given to spc5_convert_csr).
+ * g[nrows], x[ncols], dvals[nnz]: device arrays, FP64 for an FP64 matrix,
+ * FP32 otherwise.  Asynchronous on `stream`.
+ */
+spc5_status spc5_values_grad(const spc5_matrix *A, const void *g, const void *x, void *dvals,
+                             double alpha, void *stream);
+
+/*
+ * spc5_set_values -- replace the stored values with vals[nnz] (FP64, device
+ * memory, CSR order of the conversion), keeping the pattern, the blocks and
+ * the work plan; values are rounded to the matrix's storage type.  For
+ * matrices whose values change while the pattern does not (training,
+ * Newton iterations).  Asynchronous on `stream`.
+ */
+spc5_status spc5_set_values(spc5_matrix *A, const double *vals, void *stream);
 
 /*
  * spc5_spmv_noalloc -- the same product as spc5_spmv for callers that must

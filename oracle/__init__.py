@@ -73,7 +73,9 @@ def _bind(lib):
     lib.oracle_spc5_to_csr.argtypes = [i64, ci, ci, i64p, i32p, u64p, f64p, i32p, i32p, f64p]
     lib.oracle_pack_masks.argtypes = [i64, ci, ci, u64p, u8p]
     lib.oracle_quantize.argtypes = [i64, f64p, ci, opt]
-    for f in (lib.oracle_quantize, lib.oracle_check_csr, lib.oracle_csr_spmv, lib.oracle_csr_spmv_plain,
+    lib.oracle_csr_transpose.argtypes = [i64, i64, i32p, i32p, f64p, i32p, i32p, f64p]
+    lib.oracle_values_grad.argtypes = [i64, i32p, i32p, f64p, f64p, f64p]
+    for f in (lib.oracle_quantize, lib.oracle_csr_transpose, lib.oracle_values_grad, lib.oracle_check_csr, lib.oracle_csr_spmv, lib.oracle_csr_spmv_plain,
               lib.oracle_spc5_convert, lib.oracle_spc5_spmv, lib.oracle_spc5_to_csr,
               lib.oracle_pack_masks):
         f.restype = ci
@@ -206,6 +208,31 @@ class Oracle:
         _check(self.lib.oracle_quantize(v.size, v, code, out.ctypes.data_as(ctypes.c_void_p)))
         return out
 
+    def transpose(self, A):
+        """A^T as a CSR with the same attribute names (nrows, ncols, rowptr, colidx, vals)."""
+        from types import SimpleNamespace
+        nnz = int(A.rowptr[-1])
+        rp = np.zeros(A.ncols + 1, np.int32)
+        ci = np.zeros(max(nnz, 1), np.int32)
+        vv = np.zeros(max(nnz, 1), np.float64)
+        _check(self.lib.oracle_csr_transpose(A.nrows, A.ncols, _arr(A.rowptr, np.int32),
+                                             _arr(A.colidx, np.int32), _arr(A.vals, np.float64),
+                                             rp, ci, vv))
+        return SimpleNamespace(nrows=A.ncols, ncols=A.nrows, rowptr=rp, colidx=ci[:nnz],
+                               vals=vv[:nnz])
+
+    def csr_spmv_t(self, A, g):
+        """dx = A^T g (compensated FP64) and S_j = sum_i |a_ij g_i|."""
+        return self.csr_spmv(self.transpose(A), g)
+
+    def values_grad(self, A, g, x) -> np.ndarray:
+        """dvals[e] = g[row(e)] * x[col(e)] in CSR order."""
+        out = np.empty(int(A.rowptr[-1]), np.float64)
+        _check(self.lib.oracle_values_grad(A.nrows, _arr(A.rowptr, np.int32),
+                                           _arr(A.colidx, np.int32), _arr(g, np.float64),
+                                           _arr(x, np.float64), out))
+        return out
+
     def to_csr(self, S: SPC5):
         """beta(r,c) -> (rowptr, colidx, vals)."""
         nnz = S.nnz
@@ -256,6 +283,18 @@ def to_csr(S: SPC5):
 
 def quantize(values, dtype: str) -> np.ndarray:
     return _default().quantize(values, dtype)
+
+
+def transpose(A):
+    return _default().transpose(A)
+
+
+def csr_spmv_t(A, g):
+    return _default().csr_spmv_t(A, g)
+
+
+def values_grad(A, g, x) -> np.ndarray:
+    return _default().values_grad(A, g, x)
 
 
 def bf16_to_f64(bits) -> np.ndarray:

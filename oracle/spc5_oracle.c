@@ -16,6 +16,8 @@
  *   oracle_pack_masks   the r per-row c-bit masks of a block as one word
  *   oracle_quantize     FP64 values -> FP32 or BF16 storage, round to
  *                       nearest even (the reduced-precision value forms)
+ *   oracle_csr_transpose  A^T in CSR (for dx = A^T g, the input gradient)
+ *   oracle_values_grad  dvals[e] = g[row(e)] * x[col(e)] (value gradient)
  *
  * Readings of the paper taken here (each one is also listed in the design
  * notes):
@@ -330,4 +332,39 @@ int oracle_quantize(int64_t n, const double *in, int dtype, void *out) {
     return ORACLE_OK;
   }
   return ORACLE_EINVAL;
+}
+
+/*
+ * Transpose of a CSR matrix (nrows x ncols -> ncols x nrows): entries are
+ * counted per column, the counts prefix-summed, and the entries dealt out
+ * row by row, so every row of the transpose lists its columns (the
+ * original rows) in ascending order.  dx = A^T g is then oracle_csr_spmv on
+ * the transpose.  rowptr_t[ncols+1], colidx_t[nnz], vals_t[nnz].
+ */
+int oracle_csr_transpose(int64_t nrows, int64_t ncols, const int32_t *rowptr,
+                         const int32_t *colidx, const double *vals, int32_t *rowptr_t,
+                         int32_t *colidx_t, double *vals_t) {
+  for (int64_t j = 0; j <= ncols; ++j) rowptr_t[j] = 0;
+  for (int64_t e = 0; e < rowptr[nrows]; ++e) rowptr_t[colidx[e] + 1]++;
+  for (int64_t j = 0; j < ncols; ++j) rowptr_t[j + 1] += rowptr_t[j];
+  int32_t *next = (int32_t *)malloc(sizeof(int32_t) * (size_t)(ncols > 0 ? ncols : 1));
+  if (!next) return ORACLE_EINVAL;
+  for (int64_t j = 0; j < ncols; ++j) next[j] = rowptr_t[j];
+  for (int64_t i = 0; i < nrows; ++i)
+    for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+      int32_t t = next[colidx[e]]++;
+      colidx_t[t] = (int32_t)i;
+      vals_t[t] = vals[e];
+    }
+  free(next);
+  return ORACLE_OK;
+}
+
+/* Gradient of <g, A x> with respect to the stored values: one product per
+ * entry, in CSR order. */
+int oracle_values_grad(int64_t nrows, const int32_t *rowptr, const int32_t *colidx,
+                       const double *g, const double *x, double *dvals) {
+  for (int64_t i = 0; i < nrows; ++i)
+    for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) dvals[e] = g[i] * x[colidx[e]];
+  return ORACLE_OK;
 }

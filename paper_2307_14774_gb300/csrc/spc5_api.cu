@@ -62,6 +62,7 @@ void free_matrix(spc5_matrix *A) {
   cudaFree(A->block_colidx);
   cudaFree(A->masks);
   cudaFree(A->values);
+  cudaFree(A->value_src);
   cudaFree(A->x_stage);
   cudaFree(A->y_stage);
   cudaFree(A->tiles);

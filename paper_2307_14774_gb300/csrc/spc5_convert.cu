@@ -406,7 +406,7 @@ __global__ void k_values(int64_t nnz, int r, int c, const int32_t *colidx, const
                          const int32_t *elem_pos, const int32_t *uidx_incl,
                          const int32_t *bidx_incl, const int32_t *block_colidx,
                          const uint32_t *mask32, const int32_t *boff, const double *vals,
-                         typename Store::T *values) {
+                         typename Store::T *values, int32_t *value_src) {
   GRID_STRIDE(e, nnz) {
     int32_t b;
     int bit;
@@ -416,6 +416,7 @@ __global__ void k_values(int64_t nnz, int r, int c, const int32_t *colidx, const
     int32_t dst = boff[b] + __popc(mask32[b] & ((1u << bit) - 1u));
     if (dst < 0 || dst >= nnz) continue;
     values[dst] = Store::cvt(vals[e]);
+    value_src[dst] = (int32_t)e;
   }
 }
 
@@ -512,9 +513,11 @@ spc5_status convert_device(spc5_matrix *A, const int32_t *rowptr, const int32_t 
   CK(cudaMalloc((void **)&A->panel_vptr, (size_t)(np + 1) * sizeof(int32_t) + 16),
      "alloc panel_vptr");
   CK(cudaMalloc(&A->values, (size_t)nnz * vsize + 16), "alloc values");
+  CK(cudaMalloc((void **)&A->value_src, (size_t)nnz * sizeof(int32_t) + 16), "alloc value_src");
   CK(cudaMalloc((void **)&A->dev_error, sizeof(uint32_t)), "alloc error word");
   CK(cudaMemsetAsync(A->dev_error, 0, sizeof(uint32_t), s), "zero error word");
-  A->device_bytes = (int64_t)(2 * (np + 1) * sizeof(int32_t) + 32 + nnz * vsize + 16);
+  A->device_bytes = (int64_t)(2 * (np + 1) * sizeof(int32_t) + 32 + nnz * vsize + 16 +
+                             nnz * sizeof(int32_t) + 16);
 
   if (nnz == 0) {
     CK(cudaMemsetAsync(A->block_rowptr, 0, (size_t)(np + 1) * sizeof(int32_t), s), "zero brp");
@@ -600,15 +603,15 @@ spc5_status convert_device(spc5_matrix *A, const int32_t *rowptr, const int32_t 
   if (A->value_dtype == SPC5_F64)
     k_values<StoreF64><<<grid_for(nnz), kThreads, 0, s>>>(
         nnz, r, c, colidx, rowid.p, elem_pos.p, uidx.p, bidx.p, A->block_colidx, mask32.p,
-        boff.p, vals, (double *)A->values);
+        boff.p, vals, (double *)A->values, A->value_src);
   else if (A->value_dtype == SPC5_F32)
     k_values<StoreF32><<<grid_for(nnz), kThreads, 0, s>>>(
         nnz, r, c, colidx, rowid.p, elem_pos.p, uidx.p, bidx.p, A->block_colidx, mask32.p,
-        boff.p, vals, (float *)A->values);
+        boff.p, vals, (float *)A->values, A->value_src);
   else
     k_values<StoreBF16><<<grid_for(nnz), kThreads, 0, s>>>(
         nnz, r, c, colidx, rowid.p, elem_pos.p, uidx.p, bidx.p, A->block_colidx, mask32.p,
-        boff.p, vals, (uint16_t *)A->values);
+        boff.p, vals, (uint16_t *)A->values, A->value_src);
   if (mask_bytes == 1)
     k_pack_masks<uint8_t><<<grid_for(nb), kThreads, 0, s>>>(nb, mask32.p, (uint8_t *)A->masks);
   else if (mask_bytes == 2)

@@ -37,6 +37,7 @@ struct spc5_matrix {
   int32_t *block_colidx = nullptr;  // nblocks (+16 bytes of padding)
   void *masks = nullptr;            // nblocks * r * c / 8 bytes (+16 bytes of padding)
   void *values = nullptr;           // nnz values (+16 bytes of padding)
+  int32_t *value_src = nullptr;     // CSR index of every stored value (nnz)
   int64_t device_bytes = 0;
 
   // SpMV plan (built by the converter)

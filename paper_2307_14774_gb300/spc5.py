@@ -24,7 +24,8 @@ SUPPORTED_RC = ((1, 8), (2, 4), (2, 8), (4, 4), (4, 8), (8, 4))
 
 # Exported symbols declared in include/spc5.h.
 EXPORTS = ("spc5_convert_csr", "spc5_matrix_info", "spc5_export", "spc5_spmv", "spc5_destroy",
-           "spc5_status_str", "spc5_last_error", "spc5_spmv_noalloc")
+           "spc5_status_str", "spc5_last_error", "spc5_spmv_t", "spc5_values_grad",
+           "spc5_set_values", "spc5_spmv_noalloc")
 
 
 class SPC5Error(RuntimeError):
@@ -71,6 +72,11 @@ def load(path: str | None = None):
         lib.spc5_matrix_info.argtypes = [vp, ctypes.POINTER(Info)]
         lib.spc5_export.argtypes = [vp] + [ctypes.POINTER(vp)] * 5
         lib.spc5_spmv.argtypes = [vp, vp, vp, dbl, dbl, vp]
+        lib.spc5_spmv_t.argtypes = [vp, vp, vp, dbl, dbl, vp]
+        lib.spc5_values_grad.argtypes = [vp, vp, vp, vp, dbl, vp]
+        lib.spc5_set_values.argtypes = [vp, vp, vp]
+        for f in (lib.spc5_spmv_t, lib.spc5_values_grad, lib.spc5_set_values):
+            f.restype = ci
         lib.spc5_spmv_noalloc.argtypes = [vp, vp, vp, dbl, dbl, vp]
         lib.spc5_spmv_noalloc.restype = ci
         lib.spc5_destroy.argtypes = [vp]
@@ -174,6 +180,23 @@ def spc5_spmv(A: Matrix, x, y, alpha: float = 1.0, beta: float = 0.0, stream=Non
     """y = alpha * A x + beta * y (FP64 vectors, device or host)."""
     _check(load().spc5_spmv(A.handle, _ptr(x), _ptr(y), float(alpha), float(beta),
                             _stream_ptr(stream)))
+
+
+def spc5_spmv_t(A: Matrix, g, dx, alpha: float = 1.0, beta: float = 0.0, stream=None) -> None:
+    """dx = alpha * A^T g + beta * dx (device vectors)."""
+    _check(load().spc5_spmv_t(A.handle, _ptr(g), _ptr(dx), float(alpha), float(beta),
+                              _stream_ptr(stream)))
+
+
+def spc5_values_grad(A: Matrix, g, x, dvals, alpha: float = 1.0, stream=None) -> None:
+    """dvals[e] = alpha * g[row(e)] * x[col(e)] in CSR order (device arrays)."""
+    _check(load().spc5_values_grad(A.handle, _ptr(g), _ptr(x), _ptr(dvals), float(alpha),
+                                   _stream_ptr(stream)))
+
+
+def spc5_set_values(A: Matrix, vals, stream=None) -> None:
+    """Replace the stored values with CSR-ordered FP64 device values."""
+    _check(load().spc5_set_values(A.handle, _ptr(vals), _stream_ptr(stream)))
 
 
 def spc5_spmv_noalloc(A: Matrix, x, y, alpha: float = 1.0, beta: float = 0.0,

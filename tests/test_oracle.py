@@ -283,3 +283,29 @@ def test_rejects_invalid_csr():
     assert oracle.check_csr(6, 6, bad, good.colidx) in (2, 3, 4)
     with pytest.raises(oracle.OracleError):
         oracle.convert(synth.CSR(6, 6, good.rowptr, unsorted, good.vals), 2, 4)
+
+
+# ------------------------------------------------------------- gradients --
+
+def test_transpose_pins():
+    for seed, (nr, nc, d) in enumerate([(31, 23, 0.3), (5, 80, 0.7), (64, 1, 0.5), (9, 9, 0.0)]):
+        A = synth.bernoulli(nr, nc, d, seed=seed, integer_values=True)
+        T = oracle.transpose(A)
+        assert np.array_equal(synth.CSR(T.nrows, T.ncols, T.rowptr, T.colidx, T.vals).todense(),
+                              A.todense().T)
+        TT = oracle.transpose(T)
+        assert np.array_equal(TT.rowptr, A.rowptr) and np.array_equal(TT.colidx, A.colidx)
+        assert np.array_equal(TT.vals, A.vals)
+        g = synth.vector_int(nr, -4, 4, seed=seed)
+        dx, _ = oracle.csr_spmv_t(A, g)
+        assert np.array_equal(dx, A.todense().T @ g)
+
+
+def test_values_grad_pin():
+    A = synth.bernoulli(40, 30, 0.4, seed=2, integer_values=True)
+    g = synth.vector_normal(40, seed=1)
+    x = synth.vector_normal(30, seed=2)
+    dv = oracle.values_grad(A, g, x)
+    dense = np.outer(g, x)
+    rows = np.repeat(np.arange(A.nrows), np.diff(A.rowptr))
+    assert np.array_equal(dv, dense[rows, A.colidx])
