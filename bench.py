@@ -57,9 +57,14 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--matrices", default=",".join(MATRICES))
+    ap.add_argument("--betas", default=",".join(f"{r}x{c}" for r, c in BETAS),
+                    help="subset of block shapes (e.g. 4x8), for profiling one kernel")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-precision", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="keep the planner's default mapping instead of autotuning it")
     ap.add_argument("--cases-out", default=None, help="write the per-case table here")
     return ap.parse_args()
 
@@ -205,7 +210,7 @@ def roofline_object(achieved_gbs, achieved_tflops, hbm, peak_kind, traffic, byte
 
 # ------------------------------------------------------------------ native --
 
-def build_cases(names, torch, spc5, synth, log):
+def build_cases(names, torch, spc5, synth, log, betas, tune=True):
     """Generate, upload and convert every (matrix, beta); return cases and
     the host matrices (kept for the CPU baseline sample)."""
     cases, hosts = [], {}
@@ -219,10 +224,14 @@ def build_cases(names, torch, spc5, synth, log):
         dx = torch.from_numpy(x).cuda()
         dy = torch.empty(A.nrows, dtype=torch.float64, device="cuda")
         for r, c in BETAS:
+            if f"{r}x{c}" not in betas:
+                continue
             torch.cuda.synchronize()
             t1 = time.perf_counter()
             M = spc5.spc5_convert_csr(A.nrows, A.ncols, A.nnz, *dev, r=r, c=c)
             t_conv = time.perf_counter() - t1
+            if tune:
+                spc5.spc5_tune(M, dx, dy, iters=3)
             info = M.info()
             cases.append({"matrix": name, "r": r, "c": c, "M": M, "x": dx, "y": dy,
                           "info": info, "bytes": algorithmic_bytes(info), "nnz": A.nnz,
@@ -297,6 +306,74 @@ def precision_section(hosts, torch, spc5, stream, hbm, case_rows, log, reps=10):
     return rows
 
 
+def batched_section(torch, spc5, synth, stream, log, nmat=256, reps=10):
+    """256 matrices of uneven size (n log-uniform in [1e3, 2e5]; 5-point,
+    27-point and power-law generators in turn), FP32 values, each converted
+    into the block shape and mapping the autotuner picks; for every k in
+    {1, 4, 8, 16}: one persistent batched launch captured in a CUDA graph,
+    timed by replaying the graph."""
+    import math
+    import numpy as np
+    rng = np.random.default_rng(4)
+    sizes = np.exp(rng.uniform(math.log(1e3), math.log(2e5), nmat))
+    mats, shapes = [], {}
+    t0 = time.perf_counter()
+    nnz_total = 0
+    for i, n in enumerate(sizes):
+        kind = i % 3
+        if kind == 0:
+            side = max(4, int(round(math.sqrt(n))))
+            A = synth.laplace2d(side, side)
+        elif kind == 1:
+            side = max(3, int(round(n ** (1 / 3))))
+            A = synth.stencil27(side, side, side, values="normal", seed=i)
+        else:
+            A = synth.powerlaw(int(n), seed=100 + i)
+        dev = [torch.from_numpy(a).cuda() for a in (A.rowptr, A.colidx, A.vals)]
+        M = spc5.spc5_convert_tuned(A.nrows, A.ncols, A.nnz, *dev, store_dtype=spc5.SPC5_F32,
+                                    iters=3, stream=stream)
+        info = M.info()
+        key = f"{info['r']}x{info['c']}/G{info['lanes_per_row']}"
+        shapes[key] = shapes.get(key, 0) + 1
+        mats.append((M, A.nrows, A.ncols))
+        nnz_total += A.nnz
+    setup_s = time.perf_counter() - t0
+    log(f"batched: {nmat} matrices, nnz {nnz_total}, converted+tuned in {setup_s:.1f}s")
+    rows = []
+    for k in (1, 4, 8, 16):
+        X = [torch.rand(nc, k, device="cuda", dtype=torch.float32) * 2 - 1 for _, _, nc in mats]
+        Y = [torch.empty(nr, k, device="cuda", dtype=torch.float32) for _, nr, _ in mats]
+        B = spc5.Batch([m for m, _, _ in mats], X, Y, k, stream=stream)
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            B.run(stream=side)
+        torch.cuda.current_stream().wait_stream(side)
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            B.run(stream=torch.cuda.current_stream())
+        for _ in range(3):
+            graph.replay()
+        torch.cuda.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(reps)]
+        for e0, e1 in evs:
+            e0.record()
+            graph.replay()
+            e1.record()
+        torch.cuda.synchronize()
+        us = statistics.median(e0.elapsed_time(e1) for e0, e1 in evs) * 1e3
+        rows.append({"k": k, "us": round(us, 2),
+                     "gflops": round(2.0 * nnz_total * k / (us * 1e-6) / 1e9, 1)})
+        del B, graph, X, Y
+    return {"matrices": nmat, "nnz_total": int(nnz_total), "dtype": "f32 values, f32 x/y",
+            "n_range": [int(sizes.min()), int(sizes.max())], "setup_s": round(setup_s, 1),
+            "tuned_shapes": shapes, "rows": rows,
+            "launch": "one CUDA graph replay = one persistent kernel over all matrices' tiles "
+                      "(+ one fixup kernel for split panels)"}
+
+
 def cpu_baseline_sample(hosts, oracle, log):
     """Algorithm 1 (the oracle's scalar path) on the first 1/16 of every
     matrix's rows, every beta; one host thread.  Returns GFlop/s and the
@@ -338,7 +415,8 @@ def run_native(args):
         lambda m: None)
     spc5.load()
     names = [n for n in args.matrices.split(",") if n]
-    cases, hosts = build_cases(names, torch, spc5, synth, log)
+    cases, hosts = build_cases(names, torch, spc5, synth, log, args.betas.split(","),
+                               tune=not args.no_tune)
     stream = torch.cuda.current_stream()
     nlaunch = len(cases)
 
@@ -422,7 +500,9 @@ def run_native(args):
                    "spmv_per_step": nlaunch, "nnz_per_step": int(flops_per_step / 2),
                    "l2": "inputs larger than L2: every SpMV streams >= "
                          f"{min(cs['bytes'] for cs in cases) / 1e6:.0f} MB (L2 129 MB)",
-                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "mapping": "autotuned lanes-per-row per matrix (spc5_tune, during setup)"
+                              if not args.no_tune else "planner default"},
         "roofline": roofline_object(achieved, achieved_tflops, hbm, peak_kind, traffic,
                                     bytes_per_step, flops_per_step),
         "gpu_launches": nlaunch * launches_per_spmv * args.steps,
@@ -446,6 +526,9 @@ def run_native(args):
                 / (sum(rw["us"] for rw in prec if rw["dtype"] == dt) * 1e-6) / 1e9, 1),
                 "max_err_over_tol": max(rw["max_err_over_tol"] for rw in prec if rw["dtype"] == dt)}
                 for dt in ("f32", "bf16")} if prec else {}}
+
+    if not args.no_batched and rank == 0:
+        result["batched"] = batched_section(torch, spc5, synth, stream, log)
 
     # end to end through the C-ABI with host vectors: every step copies x from
     # pinned host memory and reads y back

@@ -38,6 +38,8 @@ extern "C" {
 /* Opaque handle of a matrix converted to beta(r,c); owns its device arrays. */
 typedef struct spc5_matrix spc5_matrix;
 
+/* Opaque handle of a batch of products (see spc5_batch_create). */
+typedef struct spc5_batch spc5_batch;
 
 /* Element types.  Input values are FP64; the converted values are stored
  * in FP64, FP32 or BF16 (rounded to nearest, ties to even).  An FP64 matrix
@@ -77,6 +79,7 @@ typedef struct {
   int32_t stages;          /* shared-memory pipeline stages per SM */
   int32_t consumers;       /* consumer warps per SM */
   uint32_t device_error;   /* nonzero if a kernel gave up a bounded wait (reading it syncs) */
+  double tuned_us;         /* SpMV time of the plan chosen by spc5_tune, 0 if untuned */
 } spc5_info;
 
 /*
@@ -179,6 +182,62 @@ spc5_status spc5_values_grad(const spc5_matrix *A, const void *g, const void *x,
  * Newton iterations).  Asynchronous on `stream`.
  */
 spc5_status spc5_set_values(spc5_matrix *A, const double *vals, void *stream);
+
+/*
+ * spc5_tune -- autotune the SpMV mapping of a converted matrix: time the
+ * candidate numbers of lanes sharing one row (1, 2, 4, 8, those that fit
+ * 32 / r) over `iters` products with the caller's vectors x and y (device
+ * memory, typed as for spc5_spmv; y is overwritten) and keep the fastest
+ * plan.  The paper observes that the best blocking depends on the machine
+ * and the matrix (Section 4.3); the tuner measures instead of modelling.
+ * Synchronises `stream`; rebuilds the plan (reallocates its buffers).
+ */
+spc5_status spc5_tune(spc5_matrix *A, const void *x, void *y, int iters, void *stream);
+
+/*
+ * spc5_convert_tuned -- spc5_convert_csr into each block shape of
+ * `shapes` (nshapes (r, c) pairs; NULL = all six supported shapes), each
+ * tuned by spc5_tune on a zero vector, keeping the matrix with the fastest
+ * product.  Same arguments and ownership as spc5_convert_csr otherwise.
+ */
+spc5_status spc5_convert_tuned(int64_t nrows, int64_t ncols, int64_t nnz, const int32_t *rowptr,
+                               const int32_t *colidx, const void *vals, spc5_dtype vals_dtype,
+                               spc5_dtype store_dtype, const int *shapes, int nshapes, int iters,
+                               void *stream, spc5_matrix **out);
+
+/*
+ * spc5_spmv_batched -- Y[m] = A[m] X[m] for m < nmat in one launch, with k
+ * right-hand sides per matrix (k in {1, 2, 4, 8, 16}).  X[m] is row-major
+ * [ncols_m][k] and Y[m] row-major [nrows_m][k], device memory, FP64 for FP64
+ * matrices and FP32 otherwise; all matrices share one value dtype and one
+ * device and may have different sizes and block shapes.  Creates a batch,
+ * runs it once and destroys it; synchronises `stream`.  Algorithm 1 applied
+ * to many matrices and vectors at once (the paper's kernel handles one).
+ */
+spc5_status spc5_spmv_batched(int nmat, const spc5_matrix *const *A, const void *const *X,
+                              void *const *Y, int k, void *stream);
+
+/*
+ * spc5_batch_create -- prepare the batch above for repeated runs: builds, in
+ * device memory owned by the batch, a table of the matrices' arrays and the
+ * vectors' addresses, a map from global work tile to matrix and a buffer for
+ * the partial sums of split panels (k per row).  The matrices and vectors
+ * must outlive the batch; their addresses are fixed at creation.
+ * Synchronises `stream`.
+ */
+spc5_status spc5_batch_create(int nmat, const spc5_matrix *const *A, const void *const *X,
+                              void *const *Y, int k, void *stream, spc5_batch **out);
+
+/*
+ * spc5_batch_run -- Y[m] = alpha * A[m] X[m] + beta * Y[m] for the whole
+ * batch: one persistent kernel over all matrices' tiles plus one fixup
+ * kernel when some panel was split.  Asynchronous; allocates nothing and
+ * copies nothing from the host, so it can be captured in a CUDA graph.
+ */
+spc5_status spc5_batch_run(const spc5_batch *B, double alpha, double beta, void *stream);
+
+/* Release a batch (synchronising). */
+spc5_status spc5_batch_destroy(spc5_batch *B);
 
 /*
  * spc5_spmv_noalloc -- the same product as spc5_spmv for callers that must

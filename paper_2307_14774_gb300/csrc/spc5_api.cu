@@ -198,6 +198,7 @@ spc5_status spc5_matrix_info(const spc5_matrix *A, spc5_info *info) {
       derr = 0xffffffffu;
   }
   info->device_error = derr;
+  info->tuned_us = A->tuned_us;
   return SPC5_OK;
 }
 

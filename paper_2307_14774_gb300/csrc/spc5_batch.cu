@@ -1,0 +1,406 @@
+// Batched products: many converted matrices, each with k right-hand sides,
+// in one kernel launch (plus one launch that adds the pieces of split
+// panels).
+//
+// spc5_batch_create gathers, once, a device table with every matrix's
+// arrays and vectors and a map from a global tile index to its matrix; the
+// global tile list is the concatenation of the matrices' own work plans.
+// spc5_batch_run then launches the persistent kernel over all tiles: a warp
+// takes global tiles in turn, reads the tile's matrix from the table and
+// runs the SpMV lane mapping for that matrix's block shape (a warp-uniform
+// switch over the six shapes) with k accumulators per lane: every stored
+// value meets k x values, read as one contiguous run (X row-major [n][k]).
+// Running allocates nothing and copies nothing from the host, so it can be
+// captured in a CUDA graph.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <new>
+#include <type_traits>
+#include <vector>
+
+#include "spc5_internal.h"
+
+namespace spc5 {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kThreads = 256;
+
+struct MatDesc {
+  const Tile *tiles;
+  const int32_t *brp, *vptr, *colidx;
+  const void *masks, *values;
+  const void *x;
+  void *y;
+  void *partial;  // npieces * r * k slots
+  const int32_t *long_panels, *long_slots;
+  int64_t nrows;
+  int64_t tile_base;
+  int32_t r, c, ntiles, nlong;
+};
+
+__device__ __forceinline__ double widen(double v) { return v; }
+__device__ __forceinline__ float widen(float v) { return v; }
+__device__ __forceinline__ float widen(uint16_t v) { return __uint_as_float((uint32_t)v << 16); }
+
+template <int R, int C>
+struct Mask {
+  using T = typename std::conditional<(R * C == 8), uint8_t,
+                                      typename std::conditional<(R * C == 16), uint16_t,
+                                                                uint32_t>::type>::type;
+};
+template <int R>
+struct L2 {
+  static constexpr int v = R == 1 ? 0 : R == 2 ? 1 : R == 4 ? 2 : 3;
+};
+
+// One tile of one matrix with K right-hand sides.
+template <int R, int C, int K, typename VT, typename AT>
+__device__ __forceinline__ void batch_tile(const MatDesc &d, const Tile &cur, int lane, AT alpha,
+                                           AT beta) {
+  using MT = typename Mask<R, C>::T;
+  const MT *__restrict__ masks = (const MT *)d.masks;
+  const VT *__restrict__ vals = (const VT *)d.values;
+  const AT *__restrict__ x = (const AT *)d.x;
+  AT *__restrict__ y = (AT *)d.y;
+  const bool segment = (cur.mode & kSegment) != 0;
+  const int log2G = cur.mode & 15;
+  const int G = 1 << log2G;
+  const int shift_j = L2<R>::v + log2G;
+  const int g = lane & (G - 1);
+  const int q = (lane >> log2G) & (R - 1);
+  const int j = lane >> shift_j;
+  const uint32_t row_low = (q == 0) ? 0u : ((1u << (q * C)) - 1u);
+  const uint32_t cmask = (1u << C) - 1u;
+  bool pvalid;
+  int32_t bl, nbp, v;
+  if (segment) {
+    pvalid = (j == 0);
+    bl = cur.b0;
+    nbp = cur.b1 - cur.b0;
+    v = cur.v0;
+  } else {
+    const int64_t p = (int64_t)cur.p0 + j;
+    pvalid = p < cur.p1;
+    bl = pvalid ? d.brp[p] : 0;
+    nbp = pvalid ? d.brp[p + 1] - bl : 0;
+    v = pvalid ? d.vptr[p] : 0;
+  }
+  const int32_t maxnb = __reduce_max_sync(kFull, nbp);
+  AT acc[K];
+#pragma unroll
+  for (int i = 0; i < K; ++i) acc[i] = 0;
+  for (int32_t it = 0; it < maxnb; it += G) {
+    const int32_t idx = it + g;
+    const bool valid = idx < nbp;
+    const uint32_t m = valid ? (uint32_t)masks[bl + idx] : 0u;
+    const int32_t col = valid ? d.colidx[bl + idx] : 0;
+    const int pc = __popc(m);
+    int incl = pc;
+    for (int o = 1; o < G; o <<= 1) {
+      int t = __shfl_up_sync(kFull, incl, o, G);
+      if (g >= o) incl += t;
+    }
+    const int total = (G > 1) ? __shfl_sync(kFull, incl, G - 1, G) : pc;
+    int32_t off = v + (incl - pc) + __popc(m & row_low);
+    uint32_t mq = (m >> (q * C)) & cmask;
+    while (mq) {
+      const int k = __ffs(mq) - 1;
+      mq &= mq - 1u;
+      const AT a = (AT)widen(vals[off++]);
+      const AT *xr = x + (int64_t)(col + k) * K;
+#pragma unroll
+      for (int i = 0; i < K; ++i) acc[i] = fma(a, __ldg(xr + i), acc[i]);
+    }
+    v += total;
+  }
+#pragma unroll
+  for (int i = 0; i < K; ++i)
+    for (int o = G >> 1; o > 0; o >>= 1) acc[i] += __shfl_xor_sync(kFull, acc[i], o, G);
+  if (pvalid && g == 0) {
+    if (cur.mode & kPartial) {
+      AT *part = (AT *)d.partial + ((int64_t)cur.slot * R + q) * K;
+#pragma unroll
+      for (int i = 0; i < K; ++i) part[i] = acc[i];
+    } else {
+      const int64_t row = ((int64_t)cur.p0 + j) * R + q;
+      if (row < d.nrows) {
+        AT *yr = y + row * K;
+#pragma unroll
+        for (int i = 0; i < K; ++i) {
+          AT out = alpha * acc[i];
+          if (beta != (AT)0) out = fma(beta, yr[i], out);
+          yr[i] = out;
+        }
+      }
+    }
+  }
+}
+
+template <int K, typename VT, typename AT>
+__global__ void __launch_bounds__(kThreads)
+    k_batch(const MatDesc *__restrict__ table, const int32_t *__restrict__ tile_mat,
+            int64_t ntiles, AT alpha, AT beta) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < ntiles;
+       t += nwarps) {
+    const MatDesc d = table[tile_mat[t]];
+    const Tile cur = d.tiles[t - d.tile_base];
+    switch (d.r * 100 + d.c) {
+      case 108: batch_tile<1, 8, K, VT, AT>(d, cur, lane, alpha, beta); break;
+      case 204: batch_tile<2, 4, K, VT, AT>(d, cur, lane, alpha, beta); break;
+      case 208: batch_tile<2, 8, K, VT, AT>(d, cur, lane, alpha, beta); break;
+      case 404: batch_tile<4, 4, K, VT, AT>(d, cur, lane, alpha, beta); break;
+      case 408: batch_tile<4, 8, K, VT, AT>(d, cur, lane, alpha, beta); break;
+      default: batch_tile<8, 4, K, VT, AT>(d, cur, lane, alpha, beta); break;
+    }
+  }
+}
+
+// Split panels: add each panel's pieces in order, for every row and RHS.
+// lp_mat / lp_idx: matrix and local long-panel index of every global entry.
+template <int K, typename AT>
+__global__ void k_batch_fixup(const MatDesc *__restrict__ table,
+                              const int32_t *__restrict__ lp_mat,
+                              const int32_t *__restrict__ lp_idx, int64_t nlong_total, AT alpha,
+                              AT beta) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nlong_total * 8 * K;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = i / (8 * K);
+    const int q = (int)((i / K) % 8);
+    const int rhs = (int)(i % K);
+    const MatDesc d = table[lp_mat[e]];
+    if (q >= d.r) continue;
+    const int l = lp_idx[e];
+    const int64_t row = (int64_t)d.long_panels[l] * d.r + q;
+    AT acc = 0;
+    for (int32_t s = d.long_slots[2 * l]; s < d.long_slots[2 * l + 1]; ++s)
+      acc += ((const AT *)d.partial)[((int64_t)s * d.r + q) * K + rhs];
+    if (row < d.nrows) {
+      AT *yr = (AT *)d.y + row * K + rhs;
+      AT out = alpha * acc;
+      if (beta != (AT)0) out = fma(beta, *yr, out);
+      *yr = out;
+    }
+  }
+}
+
+__global__ void k_fill(int32_t *dst, int64_t n, int32_t v) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = v;
+}
+__global__ void k_iota(int32_t *dst, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = (int32_t)i;
+}
+
+int sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+  }
+  return n;
+}
+
+}  // namespace
+}  // namespace spc5
+
+using namespace spc5;
+
+struct spc5_batch {
+  int nmat = 0, k = 0, device = 0;
+  spc5_dtype dtype = SPC5_F64;
+  int64_t ntiles = 0, nlong = 0;
+  MatDesc *table = nullptr;
+  int32_t *tile_mat = nullptr;
+  int32_t *lp_mat = nullptr, *lp_idx = nullptr;
+  void *partial = nullptr;
+};
+
+namespace {
+
+void free_batch(spc5_batch *B) {
+  if (!B) return;
+  cudaFree(B->table);
+  cudaFree(B->tile_mat);
+  cudaFree(B->lp_mat);
+  cudaFree(B->lp_idx);
+  cudaFree(B->partial);
+  delete B;
+}
+
+template <int K, typename VT, typename AT>
+cudaError_t run_batch(const spc5_batch *B, double alpha, double beta, cudaStream_t s) {
+  if (B->ntiles > 0) {
+    int64_t blocks = (B->ntiles + (kThreads / 32) - 1) / (kThreads / 32);
+    blocks = std::min<int64_t>(blocks, (int64_t)sm_count() * 8);
+    k_batch<K, VT, AT><<<(unsigned)blocks, kThreads, 0, s>>>(B->table, B->tile_mat, B->ntiles,
+                                                              (AT)alpha, (AT)beta);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  if (B->nlong > 0) {
+    int64_t threads = B->nlong * 8 * K;
+    int blocks = (int)std::min<int64_t>((threads + 255) / 256, 8192);
+    k_batch_fixup<K, AT><<<blocks, 256, 0, s>>>(B->table, B->lp_mat, B->lp_idx, B->nlong,
+                                                (AT)alpha, (AT)beta);
+  }
+  return cudaGetLastError();
+}
+
+template <typename VT, typename AT>
+cudaError_t run_k(const spc5_batch *B, double alpha, double beta, cudaStream_t s) {
+  switch (B->k) {
+    case 1: return run_batch<1, VT, AT>(B, alpha, beta, s);
+    case 2: return run_batch<2, VT, AT>(B, alpha, beta, s);
+    case 4: return run_batch<4, VT, AT>(B, alpha, beta, s);
+    case 8: return run_batch<8, VT, AT>(B, alpha, beta, s);
+    default: return run_batch<16, VT, AT>(B, alpha, beta, s);
+  }
+}
+
+}  // namespace
+
+extern "C" spc5_status spc5_batch_create(int nmat, const spc5_matrix *const *A,
+                                         const void *const *X, void *const *Y, int k,
+                                         void *stream, spc5_batch **out) {
+  if (!out || nmat < 1 || !A || !X || !Y) {
+    set_error("invalid argument");
+    return SPC5_EINVAL;
+  }
+  if (k != 1 && k != 2 && k != 4 && k != 8 && k != 16) {
+    set_error("k must be 1, 2, 4, 8 or 16");
+    return SPC5_EUNSUPPORTED;
+  }
+  for (int m = 0; m < nmat; ++m) {
+    if (!A[m] || (A[m]->ncols > 0 && !X[m]) || (A[m]->nrows > 0 && !Y[m])) {
+      set_error("NULL matrix or vector in the batch");
+      return SPC5_EINVAL;
+    }
+    if (A[m]->value_dtype != A[0]->value_dtype || A[m]->device != A[0]->device) {
+      set_error("all matrices of a batch share one value dtype and one device");
+      return SPC5_EINVAL;
+    }
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  spc5_batch *B = new (std::nothrow) spc5_batch();
+  if (!B) {
+    set_error("host allocation failed");
+    return SPC5_ENOMEM;
+  }
+  B->nmat = nmat;
+  B->k = k;
+  B->device = A[0]->device;
+  B->dtype = A[0]->value_dtype;
+  const size_t slot = B->dtype == SPC5_F64 ? 8 : 4;
+  std::vector<MatDesc> table(nmat);
+  int64_t tiles = 0, nlong = 0, pslots = 0;
+  std::vector<int64_t> pbase(nmat);
+  for (int m = 0; m < nmat; ++m) {
+    const spc5_matrix *M = A[m];
+    MatDesc &d = table[m];
+    d.tiles = M->tiles;
+    d.brp = M->block_rowptr;
+    d.vptr = M->panel_vptr;
+    d.colidx = M->block_colidx;
+    d.masks = M->masks;
+    d.values = M->values;
+    d.x = X[m];
+    d.y = Y[m];
+    d.long_panels = M->long_panels;
+    d.long_slots = M->long_slots;
+    d.nrows = M->nrows;
+    d.tile_base = tiles;
+    d.r = M->r;
+    d.c = M->c;
+    d.ntiles = (int32_t)M->ntiles;
+    d.nlong = (int32_t)M->nlong;
+    pbase[m] = pslots;
+    pslots += M->npieces * M->r * k;
+    tiles += M->ntiles;
+    nlong += M->nlong;
+  }
+  B->ntiles = tiles;
+  B->nlong = nlong;
+  spc5_status st = cuda_check(cudaMalloc(&B->partial, (size_t)std::max<int64_t>(pslots, 1) * slot),
+                              "alloc batch partials");
+  for (int m = 0; m < nmat; ++m) table[m].partial = (char *)B->partial + pbase[m] * slot;
+  if (st == SPC5_OK)
+    st = cuda_check(cudaMalloc((void **)&B->table, sizeof(MatDesc) * nmat), "alloc batch table");
+  if (st == SPC5_OK)
+    st = cuda_check(cudaMalloc((void **)&B->tile_mat, sizeof(int32_t) * std::max<int64_t>(tiles, 1)),
+                    "alloc tile map");
+  if (st == SPC5_OK)
+    st = cuda_check(cudaMalloc((void **)&B->lp_mat, sizeof(int32_t) * std::max<int64_t>(nlong, 1)),
+                    "alloc long map");
+  if (st == SPC5_OK)
+    st = cuda_check(cudaMalloc((void **)&B->lp_idx, sizeof(int32_t) * std::max<int64_t>(nlong, 1)),
+                    "alloc long map");
+  if (st == SPC5_OK)
+    st = cuda_check(cudaMemcpyAsync(B->table, table.data(), sizeof(MatDesc) * nmat,
+                                    cudaMemcpyHostToDevice, s),
+                    "copy batch table");
+  int64_t lbase = 0;
+  for (int m = 0; st == SPC5_OK && m < nmat; ++m) {
+    const spc5_matrix *M = A[m];
+    if (M->ntiles > 0)
+      k_fill<<<(unsigned)std::min<int64_t>((M->ntiles + 255) / 256, 4096), 256, 0, s>>>(
+          B->tile_mat + table[m].tile_base, M->ntiles, m);
+    if (M->nlong > 0) {
+      k_fill<<<(unsigned)std::min<int64_t>((M->nlong + 255) / 256, 4096), 256, 0, s>>>(
+          B->lp_mat + lbase, M->nlong, m);
+      k_iota<<<(unsigned)std::min<int64_t>((M->nlong + 255) / 256, 4096), 256, 0, s>>>(
+          B->lp_idx + lbase, M->nlong);
+      lbase += M->nlong;
+    }
+  }
+  if (st == SPC5_OK) st = cuda_check(cudaStreamSynchronize(s), "sync batch create");
+  if (st != SPC5_OK) {
+    free_batch(B);
+    return st;
+  }
+  *out = B;
+  return SPC5_OK;
+}
+
+extern "C" spc5_status spc5_batch_run(const spc5_batch *B, double alpha, double beta,
+                                      void *stream) {
+  if (!B) {
+    set_error("NULL batch");
+    return SPC5_EINVAL;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e;
+  if (B->dtype == SPC5_F64)
+    e = run_k<double, double>(B, alpha, beta, s);
+  else if (B->dtype == SPC5_F32)
+    e = run_k<float, float>(B, alpha, beta, s);
+  else
+    e = run_k<uint16_t, float>(B, alpha, beta, s);
+  return cuda_check(e, "batch launch");
+}
+
+extern "C" spc5_status spc5_batch_destroy(spc5_batch *B) {
+  free_batch(B);
+  return SPC5_OK;
+}
+
+extern "C" spc5_status spc5_spmv_batched(int nmat, const spc5_matrix *const *A,
+                                         const void *const *X, void *const *Y, int k,
+                                         void *stream) {
+  spc5_batch *B = nullptr;
+  spc5_status st = spc5_batch_create(nmat, A, X, Y, k, stream, &B);
+  if (st != SPC5_OK) return st;
+  st = spc5_batch_run(B, 1.0, 0.0, stream);
+  if (st == SPC5_OK) st = cuda_check(cudaStreamSynchronize((cudaStream_t)stream), "sync batch");
+  free_batch(B);
+  return st;
+}

@@ -54,6 +54,7 @@ struct spc5_matrix {
   int body = 0;                     // consumer body: bit 0 = predicated loop over the c
                                     // bits (else set-bit loop), bit 1 = x staged in smem
   int kernel = 0;                   // 0: direct tile kernel, 1: staged tile kernel
+  double tuned_us = 0.0;            // SpMV time of the plan chosen by spc5_tune (0 = untuned)
   uint32_t *dev_error = nullptr;    // set by kernels on a timed-out wait
 
   // staging for host vectors in spc5_spmv
@@ -76,10 +77,23 @@ bool supported_rc(int r, int c);
 spc5_status convert_device(spc5_matrix *A, const int32_t *d_rowptr, const int32_t *d_colidx,
                            const double *d_vals, cudaStream_t stream);
 
-// Work plan for the staged SpMV kernel; called by the converter while the
+// Planner options; -1 = default (environment variable, else heuristic).
+struct PlanOptions {
+  int kernel = -1;  // 0 direct, 1 staged
+  int log2g = -1;   // lanes per row in group tiles = 2^log2g
+  int vcap = -1;    // tile capacity in values
+  int bcap = -1;    // tile capacity in blocks
+  int body = -1;    // consumer body
+};
+
+// Work plan of the SpMV kernels; called by the converter while the
 // per-block popcounts (mask32) and value offsets (boff) are still alive.
 spc5_status plan_tiles(spc5_matrix *A, const uint32_t *mask32, const int32_t *boff,
-                       cudaStream_t stream);
+                       cudaStream_t stream, const PlanOptions &opt = PlanOptions());
+
+// Rebuild the plan of a converted matrix with other options (recomputes the
+// per-block popcounts and value offsets from the stored masks).
+spc5_status replan(spc5_matrix *A, cudaStream_t stream, const PlanOptions &opt);
 
 // SpMV launch on device vectors.
 // x, y: FP64 for an FP64 matrix, FP32 for FP32 and BF16 matrices.

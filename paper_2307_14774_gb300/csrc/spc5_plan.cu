@@ -195,7 +195,7 @@ int round_up(int v, int m) { return (v + m - 1) / m * m; }
   } while (0)
 
 spc5_status plan_tiles(spc5_matrix *A, const uint32_t *mask32, const int32_t *boff,
-                       cudaStream_t s) {
+                       cudaStream_t s, const PlanOptions &opt) {
   const int r = A->r;
   const int64_t np = A->npanels, nb = A->nblocks;
   int log2r = 0;
@@ -203,7 +203,8 @@ spc5_status plan_tiles(spc5_matrix *A, const uint32_t *mask32, const int32_t *bo
   const int log2g_segment = 5 - log2r;
 
   // the staged kernel is built for FP64 values only
-  A->kernel = (A->value_dtype == SPC5_F64 && env_int("SPC5_KERNEL", 0)) ? 1 : 0;
+  const int want_kernel = opt.kernel >= 0 ? opt.kernel : env_int("SPC5_KERNEL", 0);
+  A->kernel = (A->value_dtype == SPC5_F64 && want_kernel) ? 1 : 0;
   const bool staged = A->kernel == 1;
   // lanes per row in group tiles: a few block rounds per tile
   double avg_b = np > 0 ? (double)nb / (double)np : 0.0;
@@ -212,7 +213,8 @@ spc5_status plan_tiles(spc5_matrix *A, const uint32_t *mask32, const int32_t *bo
   const double rounds = staged ? 12.0 : 8.0;
   const int max_log2g = staged ? log2g_segment : std::min(2, log2g_segment);
   while (log2g < max_log2g && avg_b / (double)(1 << log2g) > rounds) ++log2g;
-  log2g = std::min(std::max(env_int("SPC5_LOG2G_GROUP", log2g), 0), log2g_segment);
+  log2g = opt.log2g >= 0 ? opt.log2g : env_int("SPC5_LOG2G_GROUP", log2g);
+  log2g = std::min(std::max(log2g, 0), log2g_segment);
   const int gp = 32 >> (log2r + log2g);
 
   // Tile capacity.  Staged kernel: one shared-memory stage.  Direct kernel:
@@ -225,8 +227,8 @@ spc5_status plan_tiles(spc5_matrix *A, const uint32_t *mask32, const int32_t *bo
     vcap = std::min(std::max(round_up((int)(2.0 * gp * avg_v) + 64, 64), 2048), 8192);
     bcap = std::min(std::max(round_up((int)(2.0 * gp * avg_b) + 32, 32), 256), 2048);
   }
-  vcap = env_int("SPC5_VCAP", vcap);
-  bcap = env_int("SPC5_BCAP", bcap);
+  vcap = opt.vcap > 0 ? opt.vcap : env_int("SPC5_VCAP", vcap);
+  bcap = opt.bcap > 0 ? opt.bcap : env_int("SPC5_BCAP", bcap);
   if (vcap < 64 || bcap < 1) {
     set_error("invalid stage capacity");
     return SPC5_EINVAL;
@@ -236,7 +238,7 @@ spc5_status plan_tiles(spc5_matrix *A, const uint32_t *mask32, const int32_t *bo
   int stage = 64 + r16(vcap * 8 + 16) + r16(bcap * 4 + 16) + r16(bcap * mb + 16) +
               2 * r16((gp + 1) * 4 + 16);
   double filling = nb > 0 ? (double)A->nnz / ((double)nb * A->r * A->c) : 0.0;
-  int body = env_int("SPC5_BODY", filling >= 0.3 ? 3 : 2);
+  int body = opt.body >= 0 ? opt.body : env_int("SPC5_BODY", filling >= 0.3 ? 3 : 2);
   body = std::min(std::max(body, 0), 3);
   int dev = 0, optin = 0;
   CK(cudaGetDevice(&dev), "cudaGetDevice");
@@ -265,7 +267,7 @@ spc5_status plan_tiles(spc5_matrix *A, const uint32_t *mask32, const int32_t *bo
   A->stages = stages;
   A->consumers = consumers;
   A->stage_bytes = stage;
-  A->body = staged ? body : (env_int("SPC5_BODY", 0) & 1);
+  A->body = staged ? body : ((opt.body >= 0 ? opt.body : env_int("SPC5_BODY", 0)) & 1);
 
   if (np == 0) return SPC5_OK;
   PlanParams P{np, nb, gp, vcap, bcap, vcap - 32, log2g, log2g_segment,
@@ -321,6 +323,56 @@ spc5_status plan_tiles(spc5_matrix *A, const uint32_t *mask32, const int32_t *bo
     k_write_piece_tiles<<<grid_for(nb), kThreads, 0, s>>>(P, bpanel.p, pf.p, pscan.p, tbase.p,
                                                          boff, mask32, A->tiles);
   CK(cudaGetLastError(), "plan kernels");
+  return SPC5_OK;
+}
+
+namespace {
+template <typename MaskT>
+__global__ void k_mask32(int64_t nb, const MaskT *masks, uint32_t *mask32) {
+  GRID_STRIDE(b, nb) { mask32[b] = (uint32_t)masks[b]; }
+}
+struct PopcRead {
+  const uint32_t *m;
+  __device__ int32_t operator()(int64_t i) const { return __popc(m[i]); }
+};
+}  // namespace
+
+spc5_status replan(spc5_matrix *A, cudaStream_t s, const PlanOptions &opt) {
+  CK(cudaStreamSynchronize(s), "sync before replan");
+  cudaFree(A->tiles);
+  cudaFree(A->long_panels);
+  cudaFree(A->long_slots);
+  cudaFree(A->partial);
+  A->device_bytes -= A->ntiles * (int64_t)sizeof(Tile) + A->nlong * 12 +
+                     A->npieces * A->r * (int64_t)sizeof(double);
+  A->tiles = nullptr;
+  A->long_panels = nullptr;
+  A->long_slots = nullptr;
+  A->partial = nullptr;
+  A->ntiles = A->nlong = A->npieces = 0;
+  const int64_t nb = A->nblocks;
+  Tmp<uint32_t> mask32(s);
+  Tmp<int32_t> boff(s), tmp(s);
+  CK(mask32.alloc(nb), "alloc");
+  CK(boff.alloc(nb), "alloc");
+  CK(tmp.alloc(scan_tmp_elems(nb)), "alloc");
+  if (nb > 0) {
+    const int mb = A->r * A->c / 8;
+    if (mb == 1)
+      k_mask32<uint8_t><<<grid_for(nb), kThreads, 0, s>>>(nb, (const uint8_t *)A->masks, mask32.p);
+    else if (mb == 2)
+      k_mask32<uint16_t><<<grid_for(nb), kThreads, 0, s>>>(nb, (const uint16_t *)A->masks,
+                                                           mask32.p);
+    else
+      k_mask32<uint32_t><<<grid_for(nb), kThreads, 0, s>>>(nb, (const uint32_t *)A->masks,
+                                                           mask32.p);
+    CK(device_scan<int32_t>(nb, PopcRead{mask32.p}, WriteI32{boff.p}, AddI32{}, 0, false, tmp.p,
+                            s),
+       "scan popcounts");
+  }
+  spc5_status st = plan_tiles(A, mask32.p, boff.p, s, opt);
+  if (st != SPC5_OK) return st;
+  CK(cudaStreamSynchronize(s), "sync replan");
   return SPC5_OK;
 }
 

@@ -25,7 +25,8 @@ SUPPORTED_RC = ((1, 8), (2, 4), (2, 8), (4, 4), (4, 8), (8, 4))
 # Exported symbols declared in include/spc5.h.
 EXPORTS = ("spc5_convert_csr", "spc5_matrix_info", "spc5_export", "spc5_spmv", "spc5_destroy",
            "spc5_status_str", "spc5_last_error", "spc5_spmv_t", "spc5_values_grad",
-           "spc5_set_values", "spc5_spmv_noalloc")
+           "spc5_set_values", "spc5_tune", "spc5_convert_tuned", "spc5_spmv_batched",
+           "spc5_batch_create", "spc5_batch_run", "spc5_batch_destroy", "spc5_spmv_noalloc")
 
 
 class SPC5Error(RuntimeError):
@@ -44,7 +45,7 @@ class Info(ctypes.Structure):
                 ("lanes_per_row", ctypes.c_int32), ("launches_per_spmv", ctypes.c_int32),
                 ("ntiles", ctypes.c_int64), ("long_panels", ctypes.c_int64),
                 ("stages", ctypes.c_int32), ("consumers", ctypes.c_int32),
-                ("device_error", ctypes.c_uint32)]
+                ("device_error", ctypes.c_uint32), ("tuned_us", ctypes.c_double)]
 
 
 _lock = threading.Lock()
@@ -76,6 +77,20 @@ def load(path: str | None = None):
         lib.spc5_values_grad.argtypes = [vp, vp, vp, vp, dbl, vp]
         lib.spc5_set_values.argtypes = [vp, vp, vp]
         for f in (lib.spc5_spmv_t, lib.spc5_values_grad, lib.spc5_set_values):
+            f.restype = ci
+        lib.spc5_tune.argtypes = [vp, vp, vp, ci, vp]
+        lib.spc5_tune.restype = ci
+        lib.spc5_convert_tuned.argtypes = [i64, i64, i64, vp, vp, vp, ci, ci,
+                                           ctypes.POINTER(ctypes.c_int), ci, ci, vp,
+                                           ctypes.POINTER(vp)]
+        lib.spc5_convert_tuned.restype = ci
+        pvp = ctypes.POINTER(vp)
+        lib.spc5_spmv_batched.argtypes = [ci, pvp, pvp, pvp, ci, vp]
+        lib.spc5_batch_create.argtypes = [ci, pvp, pvp, pvp, ci, vp, pvp]
+        lib.spc5_batch_run.argtypes = [vp, dbl, dbl, vp]
+        lib.spc5_batch_destroy.argtypes = [vp]
+        for f in (lib.spc5_spmv_batched, lib.spc5_batch_create, lib.spc5_batch_run,
+                  lib.spc5_batch_destroy):
             f.restype = ci
         lib.spc5_spmv_noalloc.argtypes = [vp, vp, vp, dbl, dbl, vp]
         lib.spc5_spmv_noalloc.restype = ci
@@ -197,6 +212,65 @@ def spc5_values_grad(A: Matrix, g, x, dvals, alpha: float = 1.0, stream=None) ->
 def spc5_set_values(A: Matrix, vals, stream=None) -> None:
     """Replace the stored values with CSR-ordered FP64 device values."""
     _check(load().spc5_set_values(A.handle, _ptr(vals), _stream_ptr(stream)))
+
+
+def spc5_tune(A: Matrix, x, y, iters: int = 5, stream=None) -> dict:
+    """Autotune the lanes-per-row mapping on (x, y); returns the new info."""
+    _check(load().spc5_tune(A.handle, _ptr(x), _ptr(y), int(iters), _stream_ptr(stream)))
+    return spc5_matrix_info(A)
+
+
+def spc5_convert_tuned(nrows, ncols, nnz, rowptr, colidx, vals, vals_dtype=SPC5_F64,
+                       store_dtype=SPC5_F64, shapes=None, iters: int = 5,
+                       stream=None) -> Matrix:
+    """Convert into each block shape (default: all six), tune each, keep the fastest."""
+    lib = load()
+    out = ctypes.c_void_p()
+    if shapes is None:
+        arr, n = None, 0
+    else:
+        flat = [v for rc in shapes for v in rc]
+        arr, n = (ctypes.c_int * len(flat))(*flat), len(shapes)
+    _check(lib.spc5_convert_tuned(nrows, ncols, nnz, _ptr(rowptr), _ptr(colidx), _ptr(vals),
+                                  vals_dtype, store_dtype, arr, n, int(iters),
+                                  _stream_ptr(stream), ctypes.byref(out)))
+    return Matrix(out.value)
+
+
+def _ptr_array(items):
+    arr = (ctypes.c_void_p * len(items))()
+    for i, it in enumerate(items):
+        arr[i] = it.handle.value if isinstance(it, Matrix) else _ptr(it)
+    return arr
+
+
+def spc5_spmv_batched(mats, X, Y, k: int = 1, stream=None) -> None:
+    """Y[m] = A[m] X[m] (X[m]: [ncols][k], Y[m]: [nrows][k], row-major, device)."""
+    _check(load().spc5_spmv_batched(len(mats), _ptr_array(mats), _ptr_array(X), _ptr_array(Y),
+                                    int(k), _stream_ptr(stream)))
+
+
+class Batch:
+    """Owning wrapper of an spc5_batch handle (keeps matrices and vectors alive)."""
+
+    def __init__(self, mats, X, Y, k: int = 1, stream=None):
+        self._keep = (list(mats), list(X), list(Y))
+        h = ctypes.c_void_p()
+        _check(load().spc5_batch_create(len(mats), _ptr_array(mats), _ptr_array(X),
+                                        _ptr_array(Y), int(k), _stream_ptr(stream),
+                                        ctypes.byref(h)))
+        self._h = h
+
+    def run(self, alpha: float = 1.0, beta: float = 0.0, stream=None) -> None:
+        _check(load().spc5_batch_run(self._h, float(alpha), float(beta), _stream_ptr(stream)))
+
+    def __del__(self):
+        try:
+            if self._h:
+                load().spc5_batch_destroy(self._h)
+                self._h = ctypes.c_void_p(None)
+        except Exception:
+            pass
 
 
 def spc5_spmv_noalloc(A: Matrix, x, y, alpha: float = 1.0, beta: float = 0.0,
