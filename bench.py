@@ -63,6 +63,7 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-precision", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-cg", action="store_true")
     ap.add_argument("--no-tune", action="store_true",
                     help="keep the planner's default mapping instead of autotuning it")
     ap.add_argument("--cases-out", default=None, help="write the per-case table here")
@@ -306,6 +307,41 @@ def precision_section(hosts, torch, spc5, stream, hbm, case_rows, log, reps=10):
     return rows
 
 
+def cg_section(torch, spc5, synth, stream, log):
+    """Mixed-precision iterative-refinement CG on the SPD 27-point Poisson
+    matrix on 128^3 (26 on the diagonal, -1 off it), b ~ U[-1,1), to
+    ||b - A x|| / ||b|| <= 1e-10, with the inner solve in FP32, BF16 and (as
+    the all-FP64 reference) FP64 storage; the outer residual is FP64."""
+    A = synth.workload("poisson27_128")
+    b = synth.vector_uniform(A.nrows, seed=8)
+    dev = [torch.from_numpy(a).cuda() for a in (A.rowptr, A.colidx, A.vals)]
+    db = torch.from_numpy(b).cuda()
+    A64 = spc5.spc5_convert_csr(A.nrows, A.ncols, A.nnz, *dev, r=4, c=8, stream=stream)
+    out = {"matrix": "27-point Poisson 128^3", "n": A.nrows, "nnz": A.nnz, "tol": 1e-10,
+           "rows": []}
+    for name, code in (("f32", spc5.SPC5_F32), ("bf16", spc5.SPC5_BF16), ("f64", spc5.SPC5_F64)):
+        Alo = spc5.spc5_convert_csr(A.nrows, A.ncols, A.nnz, *dev, store_dtype=code, r=4, c=8,
+                                    stream=stream)
+        for _ in range(2):  # first run warms up; second is timed
+            dx = torch.zeros(A.nrows, dtype=torch.float64, device="cuda")
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rep = spc5.spc5_ircg(A64, Alo, db, dx, tol=1e-10, max_outer=40, inner_tol=1e-3,
+                                 max_inner=2000, stream=stream)
+            torch.cuda.synchronize()
+            secs = time.perf_counter() - t0
+        # independent FP64 check of the final residual with the FP64 SpMV
+        r = db.clone()
+        spc5.spc5_spmv(A64, dx, r, -1.0, 1.0, stream)
+        torch.cuda.synchronize()
+        relres = float(r.norm() / db.norm())
+        out["rows"].append({"inner": name, "seconds": round(secs, 4), **rep,
+                            "relres_check": relres})
+        log(f"ircg inner={name}: {secs:.3f}s {rep}")
+        del Alo
+    return out
+
+
 def batched_section(torch, spc5, synth, stream, log, nmat=256, reps=10):
     """256 matrices of uneven size (n log-uniform in [1e3, 2e5]; 5-point,
     27-point and power-law generators in turn), FP32 values, each converted
@@ -529,6 +565,8 @@ def run_native(args):
 
     if not args.no_batched and rank == 0:
         result["batched"] = batched_section(torch, spc5, synth, stream, log)
+    if not args.no_cg and rank == 0:
+        result["ircg"] = cg_section(torch, spc5, synth, stream, log)
 
     # end to end through the C-ABI with host vectors: every step copies x from
     # pinned host memory and reads y back

@@ -239,6 +239,37 @@ spc5_status spc5_batch_run(const spc5_batch *B, double alpha, double beta, void 
 /* Release a batch (synchronising). */
 spc5_status spc5_batch_destroy(spc5_batch *B);
 
+/* Outcome of spc5_ircg. */
+typedef struct {
+  int32_t outer_iters; /* refinement steps taken (FP64 residuals computed = outer_iters + 1) */
+  int32_t inner_iters; /* inner CG iterations, summed over the refinement steps */
+  double relres;       /* ||b - A64 x|| / ||b|| at the last FP64 residual */
+} spc5_cg_report;
+
+/*
+ * spc5_ircg -- solve A x = b for a symmetric positive definite A by
+ * mixed-precision iterative refinement: FP64 outer residual r = b - A64 x
+ * (spc5_spmv on the FP64 matrix), FP64 norms and updates x += ||r|| d, and
+ * an inner conjugate-gradient solve of Alo d = r / ||r|| with FP32 vectors
+ * (FP64 dot-product accumulation) on Alo, the same matrix stored in FP32
+ * or BF16 (or FP64: then the inner solve runs in FP64).  The iterative
+ * solvers that motivate a fast SpMV (Section 1) are the use case; the
+ * solver itself is not part of the paper.
+ *   A64, Alo   the matrix in FP64 and in the inner precision (same pattern
+ *              and size, square); b[n], x[n] FP64 device vectors, x holds
+ *              the initial guess on entry and the solution on return
+ *   tol        stop when ||b - A64 x|| <= tol ||b||
+ *   max_outer  maximum refinement steps
+ *   inner_tol  relative residual at which an inner solve stops (0 < . < 1)
+ *   max_inner  maximum CG iterations per inner solve
+ * One inner iteration is captured once as a CUDA graph and replayed; the
+ * host reads the inner r.r every 8 iterations and ||r|| once per step.
+ * Synchronises `stream`; allocates work vectors (5 n) for the call.
+ */
+spc5_status spc5_ircg(const spc5_matrix *A64, const spc5_matrix *Alo, const double *b, double *x,
+                      double tol, int max_outer, double inner_tol, int max_inner, void *stream,
+                      spc5_cg_report *report);
+
 /*
  * spc5_spmv_noalloc -- the same product as spc5_spmv for callers that must
  * not allocate device memory during the call (for example while a CUDA

@@ -267,7 +267,11 @@ spc5_status plan_tiles(spc5_matrix *A, const uint32_t *mask32, const int32_t *bo
   A->stages = stages;
   A->consumers = consumers;
   A->stage_bytes = stage;
-  A->body = staged ? body : ((opt.body >= 0 ? opt.body : env_int("SPC5_BODY", 0)) & 1);
+  // direct kernel bodies: 0 per-block set-bit loop, 1 per-block predicated
+  // loop over the c bits, 2 row stream across blocks (row-group tiles with one
+  // lane per row; other tiles use body 0)
+  A->body = staged ? body
+                   : std::min(std::max(opt.body >= 0 ? opt.body : env_int("SPC5_BODY", 0), 0), 2);
 
   if (np == 0) return SPC5_OK;
   PlanParams P{np, nb, gp, vcap, bcap, vcap - 32, log2g, log2g_segment,

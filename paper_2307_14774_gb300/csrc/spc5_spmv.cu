@@ -167,7 +167,54 @@ __device__ __forceinline__ AT group_sum(AT acc, int G) {
 // round ahead so that a round waits for one memory round trip (its values)
 // instead of two (metadata, then values).  Many resident warps (up to 64
 // per SM) keep the FP64 pipe and the memory system busy.
-template <int R, int C, bool UNROLL, typename VT, typename AT>
+// Row-stream body for row-group tiles with one lane per row: the lane walks
+// its row's values across the panel's blocks (moving to the next block when
+// the current row mask is used up, with the next block's metadata loaded one
+// block ahead), one FMA per loop trip.  A warp then issues as many FP64 FMAs
+// as its longest row has values in the tile, instead of the sum over blocks
+// of the largest per-block bit count, which keeps the FP64 pipe's lanes busy
+// when rows have uneven bit counts per block.
+template <int R, int C, typename VT, typename AT, typename MaskT>
+__device__ __forceinline__ AT row_stream(const MaskT *__restrict__ masks,
+                                         const int32_t *__restrict__ block_colidx,
+                                         const VT *__restrict__ vals, const AT *__restrict__ x,
+                                         int32_t bl, int32_t nbp, int32_t v, int q) {
+  const uint32_t row_low = (q == 0) ? 0u : ((1u << (q * C)) - 1u);
+  const uint32_t cmask = (1u << C) - 1u;
+  uint32_t m_next = 0u;
+  int32_t c_next = 0;
+  if (nbp > 0) {
+    m_next = (uint32_t)masks[bl];
+    c_next = block_colidx[bl];
+  }
+  int32_t b = 0, off = 0, col = 0;
+  uint32_t mq = 0u;
+  AT acc = 0;
+  for (;;) {
+    while (mq == 0u && b < nbp) {
+      const uint32_t m = m_next;
+      col = c_next;
+      ++b;
+      if (b < nbp) {
+        m_next = (uint32_t)masks[bl + b];
+        c_next = block_colidx[bl + b];
+      }
+      off = v + __popc(m & row_low);
+      v += __popc(m);
+      mq = (m >> (q * C)) & cmask;
+    }
+    if (!__any_sync(kFull, mq != 0u)) break;
+    if (mq) {
+      const int k = __ffs(mq) - 1;
+      mq &= mq - 1u;
+      acc = fma((AT)widen(vals[off]), __ldg(x + col + k), acc);
+      ++off;
+    }
+  }
+  return acc;
+}
+
+template <int R, int C, int BODY, typename VT, typename AT>
 __global__ void __launch_bounds__(kDirectThreads, kDirectBlocksPerSM)
     k_spmv_tiles(const Tile *__restrict__ tiles, int64_t ntiles,
                  const int32_t *__restrict__ block_rowptr, const int32_t *__restrict__ panel_vptr,
@@ -208,6 +255,11 @@ __global__ void __launch_bounds__(kDirectThreads, kDirectBlocksPerSM)
       nbp = pvalid ? block_rowptr[p + 1] - bl : 0;
       v = pvalid ? panel_vptr[p] : 0;
     }
+    AT acc = 0;
+    if (BODY == 2 && G == 1) {
+      acc = row_stream<R, C>(masks, block_colidx, vals, x, bl, nbp, v, q);
+    } else {
+    constexpr bool UNROLL = BODY == 1;
     const int32_t maxnb = __reduce_max_sync(kFull, nbp);
     uint32_t m_next = 0u;
     int32_t c_next = 0;
@@ -215,7 +267,6 @@ __global__ void __launch_bounds__(kDirectThreads, kDirectBlocksPerSM)
       m_next = (uint32_t)masks[bl + g];
       c_next = block_colidx[bl + g];
     }
-    AT acc = 0;
     for (int32_t it = 0; it < maxnb; it += G) {
       const uint32_t m = m_next;
       const int32_t col = c_next;
@@ -233,6 +284,7 @@ __global__ void __launch_bounds__(kDirectThreads, kDirectBlocksPerSM)
       const int32_t off = v + excl + __popc(m & row_low);
       acc = row_block<C, UNROLL>(acc, (m >> (q * C)) & cmask, vals + off, x + col);
       v += total;
+    }
     }
     acc = group_sum(acc, G);
     if (pvalid && g == 0) {
@@ -658,7 +710,7 @@ cudaError_t launch_staged(const spc5_matrix *A, const double *x, double *y, doub
   return e;
 }
 
-template <int R, int C, bool UNROLL, typename VT, typename AT>
+template <int R, int C, int BODY, typename VT, typename AT>
 cudaError_t launch_direct(const spc5_matrix *A, const AT *x, AT *y, double alpha, double beta,
                           cudaStream_t s, AT *partial) {
   using MaskT = typename MaskType<R, C>::T;
@@ -668,7 +720,7 @@ cudaError_t launch_direct(const spc5_matrix *A, const AT *x, AT *y, double alpha
     int64_t blocks = (A->ntiles + warps_per_block - 1) / warps_per_block;
     const int64_t resident = (int64_t)num_sms() * kDirectBlocksPerSM;
     if (blocks > resident) blocks = resident;
-    k_spmv_tiles<R, C, UNROLL, VT, AT><<<(unsigned)blocks, kDirectThreads, 0, s>>>(
+    k_spmv_tiles<R, C, BODY, VT, AT><<<(unsigned)blocks, kDirectThreads, 0, s>>>(
         A->tiles, A->ntiles, A->block_rowptr, A->panel_vptr, A->block_colidx,
         (const MaskT *)A->masks, (const VT *)A->values, x, y, partial, (AT)alpha, (AT)beta,
         A->nrows);
@@ -688,11 +740,17 @@ cudaError_t launch_direct(const spc5_matrix *A, const AT *x, AT *y, double alpha
 template <int R, int C, typename VT, typename AT>
 cudaError_t launch_direct_body(const spc5_matrix *A, const void *x, void *y, double alpha,
                                double beta, cudaStream_t s, void *partial) {
-  return (A->body & 1)
-             ? launch_direct<R, C, true, VT, AT>(A, (const AT *)x, (AT *)y, alpha, beta, s,
-                                                 (AT *)partial)
-             : launch_direct<R, C, false, VT, AT>(A, (const AT *)x, (AT *)y, alpha, beta, s,
-                                                  (AT *)partial);
+  switch (A->body) {
+    case 1:
+      return launch_direct<R, C, 1, VT, AT>(A, (const AT *)x, (AT *)y, alpha, beta, s,
+                                            (AT *)partial);
+    case 2:
+      return launch_direct<R, C, 2, VT, AT>(A, (const AT *)x, (AT *)y, alpha, beta, s,
+                                            (AT *)partial);
+    default:
+      return launch_direct<R, C, 0, VT, AT>(A, (const AT *)x, (AT *)y, alpha, beta, s,
+                                            (AT *)partial);
+  }
 }
 
 template <int R, int C>

@@ -56,12 +56,16 @@ spc5_status tune(spc5_matrix *A, const void *x, void *y, int iters, cudaStream_t
   while ((1 << log2r) < A->r) ++log2r;
   const int max_log2g = std::min(3, 5 - log2r);
   double best = -1.0;
-  int best_g = 0;
-  for (int lg = 0; lg <= max_log2g; ++lg) {
+  int best_g = 0, best_body = 0;
+  // candidates: (lanes per row, body); the row-stream body needs one lane per row
+  std::vector<std::pair<int, int>> cands;
+  cands.push_back({0, 2});
+  for (int lg = 0; lg <= max_log2g; ++lg) cands.push_back({lg, 0});
+  for (size_t i = 0; i < cands.size(); ++i) {
     PlanOptions o;
     o.kernel = 0;
-    o.log2g = lg;
-    o.body = 0;
+    o.log2g = cands[i].first;
+    o.body = cands[i].second;
     spc5_status st = replan(A, s, o);
     if (st != SPC5_OK) return st;
     double us = time_spmv(A, x, y, iters, s);
@@ -71,14 +75,15 @@ spc5_status tune(spc5_matrix *A, const void *x, void *y, int iters, cudaStream_t
     }
     if (best < 0 || us < best) {
       best = us;
-      best_g = lg;
+      best_g = cands[i].first;
+      best_body = cands[i].second;
     }
   }
-  if (best_g != max_log2g) {
+  if (best_g != cands.back().first || best_body != cands.back().second) {
     PlanOptions o;
     o.kernel = 0;
     o.log2g = best_g;
-    o.body = 0;
+    o.body = best_body;
     spc5_status st = replan(A, s, o);
     if (st != SPC5_OK) return st;
   }

@@ -26,7 +26,8 @@ SUPPORTED_RC = ((1, 8), (2, 4), (2, 8), (4, 4), (4, 8), (8, 4))
 EXPORTS = ("spc5_convert_csr", "spc5_matrix_info", "spc5_export", "spc5_spmv", "spc5_destroy",
            "spc5_status_str", "spc5_last_error", "spc5_spmv_t", "spc5_values_grad",
            "spc5_set_values", "spc5_tune", "spc5_convert_tuned", "spc5_spmv_batched",
-           "spc5_batch_create", "spc5_batch_run", "spc5_batch_destroy", "spc5_spmv_noalloc")
+           "spc5_batch_create", "spc5_batch_run", "spc5_batch_destroy", "spc5_ircg",
+           "spc5_spmv_noalloc")
 
 
 class SPC5Error(RuntimeError):
@@ -46,6 +47,11 @@ class Info(ctypes.Structure):
                 ("ntiles", ctypes.c_int64), ("long_panels", ctypes.c_int64),
                 ("stages", ctypes.c_int32), ("consumers", ctypes.c_int32),
                 ("device_error", ctypes.c_uint32), ("tuned_us", ctypes.c_double)]
+
+
+class CGReport(ctypes.Structure):
+    _fields_ = [("outer_iters", ctypes.c_int32), ("inner_iters", ctypes.c_int32),
+                ("relres", ctypes.c_double)]
 
 
 _lock = threading.Lock()
@@ -92,6 +98,8 @@ def load(path: str | None = None):
         for f in (lib.spc5_spmv_batched, lib.spc5_batch_create, lib.spc5_batch_run,
                   lib.spc5_batch_destroy):
             f.restype = ci
+        lib.spc5_ircg.argtypes = [vp, vp, vp, vp, dbl, ci, dbl, ci, vp, ctypes.POINTER(CGReport)]
+        lib.spc5_ircg.restype = ci
         lib.spc5_spmv_noalloc.argtypes = [vp, vp, vp, dbl, dbl, vp]
         lib.spc5_spmv_noalloc.restype = ci
         lib.spc5_destroy.argtypes = [vp]
@@ -271,6 +279,17 @@ class Batch:
                 self._h = ctypes.c_void_p(None)
         except Exception:
             pass
+
+
+def spc5_ircg(A64: Matrix, Alo: Matrix, b, x, tol: float = 1e-10, max_outer: int = 50,
+              inner_tol: float = 1e-3, max_inner: int = 1000, stream=None) -> dict:
+    """Mixed-precision iterative-refinement CG; x (FP64, device) is updated in place."""
+    rep = CGReport()
+    _check(load().spc5_ircg(A64.handle, Alo.handle, _ptr(b), _ptr(x), float(tol), int(max_outer),
+                            float(inner_tol), int(max_inner), _stream_ptr(stream),
+                            ctypes.byref(rep)))
+    return {"outer_iters": rep.outer_iters, "inner_iters": rep.inner_iters,
+            "relres": rep.relres}
 
 
 def spc5_spmv_noalloc(A: Matrix, x, y, alpha: float = 1.0, beta: float = 0.0,

@@ -179,7 +179,7 @@ def test_direct_kernel_lane_mappings(monkeypatch, log2g):
     x = synth.vector_uniform(A.ncols, seed=4)
     y_ref, scale = oracle.csr_spmv(A, x)
     for r, c in [(1, 8), (4, 4), (8, 4)]:
-        for body in ("0", "1"):
+        for body in ("0", "1", "2"):
             for vcap in ("", "2048"):
                 monkeypatch.setenv("SPC5_BODY", body)
                 if vcap:

@@ -90,8 +90,10 @@ def test_reduced_precision_spmv_error(mats, dtype, r, c):
         assert np.all(np.abs(y - y_dq) <= (k + 2) * 2.0 ** -24 * scale_dq)
 
 
+@pytest.mark.parametrize("body", ["0", "2"])
 @pytest.mark.parametrize("dtype", list(DTYPES))
-def test_reduced_precision_integer_exact(dtype):
+def test_reduced_precision_integer_exact(monkeypatch, dtype, body):
+    monkeypatch.setenv("SPC5_BODY", body)
     for seed in range(3):
         A = synth.bernoulli(77, 300, 0.4, seed=seed, integer_values=True)
         x = synth.vector_int(A.ncols, -3, 3, seed=seed).astype(np.float32)
