@@ -74,12 +74,16 @@ typedef struct {
   int32_t device;          /* CUDA device ordinal the matrix lives on */
   int32_t lanes_per_row;   /* lanes sharing one row in the SpMV's row groups (1, 2, 4, ...) */
   int32_t launches_per_spmv; /* kernel launches one spc5_spmv call makes (1, or 2 with pieces) */
-  int64_t ntiles;          /* SpMV work tiles (shared-memory stages of work) */
+  int64_t ntiles;          /* work tiles of the plan the SpMV uses */
   int64_t long_panels;     /* panels split into pieces whose partial sums are added in order */
   int32_t stages;          /* shared-memory pipeline stages per SM */
   int32_t consumers;       /* consumer warps per SM */
   uint32_t device_error;   /* nonzero if a kernel gave up a bounded wait (reading it syncs) */
   double tuned_us;         /* SpMV time of the plan chosen by spc5_tune, 0 if untuned */
+  int32_t flat;            /* 1: the SpMV deals blocks to lanes evenly (block-balanced plan);
+                              0: lanes own rows (row-group plan) */
+  double group_efficiency; /* busy share of the row-group plan's block slots; the converter
+                              picks the block-balanced plan below 0.7 */
 } spc5_info;
 
 /*
@@ -145,8 +149,16 @@ spc5_status spc5_export(const spc5_matrix *A, const int32_t **block_rowptr,
  * propagates).
  * Device vectors: asynchronous on `stream`.  Host vectors: copied through
  * device buffers owned by A; the call returns when y is on the host.  x and y
- * must not overlap.  Concurrent calls on the same handle with host vectors
- * must be serialised by the caller.
+ * must not overlap.  Products on the same handle whose kernels could overlap
+ * on the GPU (different streams) must be serialised by the caller: they
+ * share the handle's buffer of partial sums and its tile counter.
+ *
+ * Work mapping (chosen at conversion, see spc5_info.flat): lanes own rows
+ * of groups of panels (row-group plan), or the blocks of runs of whole
+ * panels are dealt to the lanes evenly and the row sums are assembled by a
+ * segmented warp scan (block-balanced plan, for matrices whose panels hold
+ * very different numbers of blocks).  Both give y within the same error
+ * bound; the summation order differs.
  */
 spc5_status spc5_spmv(const spc5_matrix *A, const void *x, void *y, double alpha, double beta,
                       void *stream);
@@ -287,10 +299,14 @@ spc5_status spc5_ircg(const spc5_matrix *A64, const spc5_matrix *Alo, const doub
  * (pieces * r) is rejected with SPC5_EOVERFLOW before any work is queued.
  * The call makes no cudaMalloc, cudaFree or other allocating call.
  *
- * The array is shared by every call on a device: concurrent calls whose
- * kernels overlap on the GPU (different streams, or different handles at
- * once) race on it and must be serialised by the caller.  No state carries
- * over between calls (each call writes every partial sum it reads).
+ * The block-balanced plan's tile counter is likewise a fixed pair of
+ * 32-bit words inside the library; every launch leaves it at zero.
+ *
+ * The array and the counter are shared by every call on a device:
+ * concurrent calls whose kernels overlap on the GPU (different streams, or
+ * different handles at once) race on them and must be serialised by the
+ * caller.  No state carries over between calls (each call writes every
+ * partial sum it reads).
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress, with that device current); make that first call
  * before any stream capture.

@@ -69,6 +69,11 @@ void free_matrix(spc5_matrix *A) {
   cudaFree(A->long_panels);
   cudaFree(A->long_slots);
   cudaFree(A->partial);
+  cudaFree(A->ftiles);
+  cudaFree(A->flong_panels);
+  cudaFree(A->flong_slots);
+  cudaFree(A->fpartial);
+  cudaFree(A->fsched);
   cudaFree(A->dev_error);
   delete A;
 }
@@ -187,8 +192,8 @@ spc5_status spc5_matrix_info(const spc5_matrix *A, spc5_info *info) {
   info->device = A->device;
   info->lanes_per_row = 1 << A->log2_group_lanes;
   info->launches_per_spmv = spmv_launches(A);
-  info->ntiles = A->ntiles;
-  info->long_panels = A->nlong;
+  info->ntiles = A->flat ? A->fntiles : A->ntiles;
+  info->long_panels = A->flat ? A->fnlong : A->nlong;
   info->stages = A->stages;
   info->consumers = A->consumers;
   uint32_t derr = 0;
@@ -199,6 +204,8 @@ spc5_status spc5_matrix_info(const spc5_matrix *A, spc5_info *info) {
   }
   info->device_error = derr;
   info->tuned_us = A->tuned_us;
+  info->flat = A->flat;
+  info->group_efficiency = A->group_efficiency;
   return SPC5_OK;
 }
 

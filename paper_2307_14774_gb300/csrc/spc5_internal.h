@@ -16,12 +16,17 @@ namespace spc5 {
 //   segment tile: blocks [b0, b1) of the single panel p0 (mode & kSegment),
 //                 32/r lanes per row; with mode & kPartial the r row sums go
 //                 to partial[slot * r + q] and a fixup adds the pieces.
+//   flat tile:    (mode & kFlat) whole panels [p0, p1) whose blocks
+//                 [b0, b1) are dealt to the lanes one block per lane; with
+//                 mode & kPartial the blocks [b0, b1) of the single long
+//                 panel p0, whose r row sums go to partial[slot * r + q].
 // [b0, b1) and [v0, v1) are the tile's block and value ranges.
 struct Tile {
   int32_t p0, p1, b0, b1, v0, v1, slot, mode;
 };
 constexpr int32_t kSegment = 16;
 constexpr int32_t kPartial = 32;
+constexpr int32_t kFlat = 64;
 
 }  // namespace spc5
 
@@ -57,6 +62,20 @@ struct spc5_matrix {
   double tuned_us = 0.0;            // SpMV time of the plan chosen by spc5_tune (0 = untuned)
   uint32_t *dev_error = nullptr;    // set by kernels on a timed-out wait
 
+  // Block-balanced plan (flat tiles), used by the SpMV instead of the row
+  // groups above when `flat` is set; the transposed product, the gradient
+  // and the batched kernel always use the row-group plan.
+  int flat = 0;
+  int flat_bcap = 0;                // blocks per flat tile (and per piece of a long panel)
+  double group_efficiency = 0.0;    // busy share of the row-group plan's block slots
+  spc5::Tile *ftiles = nullptr;
+  int64_t fntiles = 0;
+  int32_t *flong_panels = nullptr;
+  int32_t *flong_slots = nullptr;
+  int64_t fnlong = 0, fnpieces = 0;
+  double *fpartial = nullptr;       // fnpieces * r partial row sums
+  uint32_t *fsched = nullptr;       // [2]: next tile, finished warps (reset by the kernel)
+
   // staging for host vectors in spc5_spmv
   void *x_stage = nullptr;
   void *y_stage = nullptr;
@@ -84,6 +103,8 @@ struct PlanOptions {
   int vcap = -1;    // tile capacity in values
   int bcap = -1;    // tile capacity in blocks
   int body = -1;    // consumer body
+  int flat = -1;    // 1: block-balanced SpMV plan, 0: row groups
+  int fbcap = -1;   // blocks per flat tile
 };
 
 // Work plan of the SpMV kernels; called by the converter while the
@@ -101,9 +122,15 @@ spc5_status spmv_device(const spc5_matrix *A, const void *x, void *y, double alp
                         cudaStream_t stream);
 
 // The same with the partial sums of split panels written to `partial`
-// (npieces * r doubles) instead of the handle's own buffer.
+// (spmv_pieces(A) * r doubles) instead of the handle's own buffer, and the
+// flat plan's two tile-scheduling counters at `sched` (zero before the
+// first call; every launch leaves them zero again) instead of the handle's.
 spc5_status spmv_device_scratch(const spc5_matrix *A, const void *x, void *y, double alpha,
-                                double beta, cudaStream_t stream, void *partial);
+                                double beta, cudaStream_t stream, void *partial,
+                                uint32_t *sched);
+
+// Pieces of split panels in the plan the SpMV uses.
+int64_t spmv_pieces(const spc5_matrix *A);
 
 // Number of kernel launches one spmv_device call makes.
 int spmv_launches(const spc5_matrix *A);

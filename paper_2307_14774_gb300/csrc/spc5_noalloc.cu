@@ -6,13 +6,16 @@
 // synchronisation), or code running under a memory budget that was fixed at
 // start-up.  spc5_spmv itself allocates nothing for device vectors either,
 // but it writes the partial sums of panels split into pieces to a buffer
-// owned by the matrix handle.  This entry point writes them instead to a
-// fixed array compiled into the library (file-scope __device__ storage), so
-// the whole call allocates nothing and touches no per-matrix scratch.
+// owned by the matrix handle, and the block-balanced plan schedules its
+// tiles through a counter owned by the handle.  This entry point uses
+// instead a fixed array and a fixed counter pair compiled into the library
+// (file-scope __device__ storage), so the whole call allocates nothing and
+// touches no per-matrix scratch.
 //
 // The array holds kNoallocScratchDoubles doubles (1 MiB); every GPU that
 // loads the library keeps it until the process exits.  A matrix whose split
-// panels need more partial sums is rejected with SPC5_EOVERFLOW.
+// panels need more partial sums is rejected with SPC5_EOVERFLOW.  The
+// counters start at zero and every launch leaves them at zero.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -32,14 +35,16 @@ constexpr int kMaxDevices = 64;
 // fixup adds them), so nothing needs clearing; calls that overlap on the
 // GPU race on it.
 static __device__ __align__(256) double g_noalloc_scratch[kNoallocScratchDoubles];
+static __device__ uint32_t g_noalloc_sched[2];
 
 std::mutex g_mutex;
 double *g_scratch_addr[kMaxDevices] = {};
+uint32_t *g_sched_addr[kMaxDevices] = {};
 
 // Device address of the array on `dev`, looked up once per device with that
 // device current.  (In host code the array's name is only a host-side
 // stand-in, not a device address.)
-spc5_status scratch_address(int dev, double **out) {
+spc5_status scratch_address(int dev, double **out, uint32_t **sched) {
   if (dev < 0 || dev >= kMaxDevices) {
     set_error("device ordinal out of range for spc5_spmv_noalloc");
     return SPC5_EINVAL;
@@ -53,14 +58,17 @@ spc5_status scratch_address(int dev, double **out) {
       st = cuda_check(cudaSetDevice(dev), "cudaSetDevice");
       if (st != SPC5_OK) return st;
     }
-    void *p = nullptr;
+    void *p = nullptr, *q = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e == cudaSuccess) e = cudaGetSymbolAddress(&q, g_noalloc_sched);
     if (cur != dev) cudaSetDevice(cur);
     st = cuda_check(e, "cudaGetSymbolAddress(noalloc scratch)");
     if (st != SPC5_OK) return st;
     g_scratch_addr[dev] = static_cast<double *>(p);
+    g_sched_addr[dev] = static_cast<uint32_t *>(q);
   }
   *out = g_scratch_addr[dev];
+  *sched = g_sched_addr[dev];
   return SPC5_OK;
 }
 
@@ -89,7 +97,7 @@ extern "C" spc5_status spc5_spmv_noalloc(const spc5_matrix *A, const void *x, vo
     set_error("spc5_spmv_noalloc takes device vectors only (host vectors need staging buffers)");
     return SPC5_EINVAL;
   }
-  const int64_t need = A->npieces * A->r;
+  const int64_t need = spmv_pieces(A) * A->r;
   if (need > kNoallocScratchDoubles) {
     set_error("the matrix's split panels need " + std::to_string(need) +
               " partial sums; spc5_spmv_noalloc holds at most " +
@@ -97,7 +105,8 @@ extern "C" spc5_status spc5_spmv_noalloc(const spc5_matrix *A, const void *x, vo
     return SPC5_EOVERFLOW;
   }
   double *scratch = nullptr;
-  spc5_status st = scratch_address(A->device, &scratch);
+  uint32_t *sched = nullptr;
+  spc5_status st = scratch_address(A->device, &scratch, &sched);
   if (st != SPC5_OK) return st;
   int cur = -1;
   st = cuda_check(cudaGetDevice(&cur), "cudaGetDevice");
@@ -106,7 +115,7 @@ extern "C" spc5_status spc5_spmv_noalloc(const spc5_matrix *A, const void *x, vo
     st = cuda_check(cudaSetDevice(A->device), "cudaSetDevice");
     if (st != SPC5_OK) return st;
   }
-  st = spmv_device_scratch(A, x, y, alpha, beta, (cudaStream_t)stream, scratch);
+  st = spmv_device_scratch(A, x, y, alpha, beta, (cudaStream_t)stream, scratch, sched);
   if (cur != A->device) cudaSetDevice(cur);
   return st;
 }

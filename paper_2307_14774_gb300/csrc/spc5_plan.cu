@@ -152,6 +152,107 @@ __global__ void k_write_piece_tiles(PlanParams P, const int32_t *bpanel, const i
   }
 }
 
+// ---------------------------------------------------------- flat plan ----
+// Block-balanced plan: consecutive whole panels are packed into tiles of
+// about `fbcap` blocks (a panel joins the tile of the window of fbcap blocks
+// holding its first block), and panels of more than fbcap blocks are cut
+// into pieces of fbcap blocks whose row sums go to the partial buffer.
+
+struct FlatParams {
+  int64_t npanels, nblocks, nnz;
+  int32_t fbcap;
+  const int32_t *brp, *vptr;
+};
+
+__device__ __forceinline__ bool flat_long(const FlatParams &F, int64_t p) {
+  return F.brp[p + 1] - F.brp[p] > F.fbcap;
+}
+
+__device__ __forceinline__ bool flat_start(const FlatParams &F, int64_t p) {
+  if (flat_long(F, p)) return false;
+  if (p == 0 || flat_long(F, p - 1)) return true;
+  return F.brp[p] / F.fbcap != F.brp[p - 1] / F.fbcap;
+}
+
+__device__ __forceinline__ int32_t flat_pieces(const FlatParams &F, int64_t p) {
+  const int32_t nbp = F.brp[p + 1] - F.brp[p];
+  return nbp > F.fbcap ? (nbp + F.fbcap - 1) / F.fbcap : 0;
+}
+
+// tiles per panel, long-panel flags and pieces per panel
+__global__ void k_flat_counts(FlatParams F, int32_t *tc, int32_t *lf, int32_t *pc) {
+  GRID_STRIDE(p, F.npanels) {
+    const int32_t np_ = flat_pieces(F, p);
+    tc[p] = np_ > 0 ? np_ : (flat_start(F, p) ? 1 : 0);
+    lf[p] = np_ > 0 ? 1 : 0;
+    pc[p] = np_;
+  }
+}
+
+__global__ void k_flat_write(FlatParams F, const int32_t *tbase, const int32_t *lbase,
+                             const int32_t *sbase, const int32_t *boff, Tile *tiles,
+                             int32_t *long_panels, int32_t *long_slots) {
+  GRID_STRIDE(p, F.npanels) {
+    const int32_t np_ = flat_pieces(F, p);
+    if (np_ > 0) {
+      const int32_t l = lbase[p];
+      long_panels[l] = (int32_t)p;
+      long_slots[2 * l] = sbase[p];
+      long_slots[2 * l + 1] = sbase[p] + np_;
+      const int32_t first = F.brp[p], end = F.brp[p + 1];
+      for (int32_t k = 0; k < np_; ++k) {
+        const int32_t b0 = first + k * F.fbcap;
+        const int32_t b1 = (b0 + F.fbcap < end) ? b0 + F.fbcap : end;
+        const int32_t v1 = (b1 < F.nblocks) ? boff[b1] : (int32_t)F.nnz;
+        tiles[tbase[p] + k] = Tile{(int32_t)p, (int32_t)p + 1, b0, b1, boff[b0], v1, sbase[p] + k,
+                                   kFlat | kPartial};
+      }
+      continue;
+    }
+    const bool start = flat_start(F, p);
+    const int32_t idx = start ? tbase[p] : tbase[p] - 1;
+    if (start) {
+      tiles[idx].p0 = (int32_t)p;
+      tiles[idx].b0 = F.brp[p];
+      tiles[idx].v0 = F.vptr[p];
+      tiles[idx].slot = -1;
+      tiles[idx].mode = kFlat;
+    }
+    const bool last = (p + 1 == F.npanels) || flat_long(F, p + 1) || flat_start(F, p + 1);
+    if (last) {
+      tiles[idx].p1 = (int32_t)p + 1;
+      tiles[idx].b1 = F.brp[p + 1];
+      tiles[idx].v1 = F.vptr[p + 1];
+    }
+  }
+}
+
+// Busy share of the row-group plan's block slots: a group tile keeps
+// group_panels * G slots busy for as many rounds as its longest panel needs.
+__global__ void k_group_efficiency(const Tile *tiles, int64_t ntiles, const int32_t *brp, int gp,
+                                   unsigned long long *acc) {
+  unsigned long long used = 0, slots = 0;
+  GRID_STRIDE(t, ntiles) {
+    const Tile T = tiles[t];
+    const int64_t G = 1ll << (T.mode & 15);
+    if (T.mode & kSegment) {
+      const int64_t nbt = T.b1 - T.b0;
+      used += nbt;
+      slots += G * ((nbt + G - 1) / G);
+    } else {
+      int64_t mx = 0;
+      for (int32_t p = T.p0; p < T.p1; ++p) {
+        const int64_t nbp = brp[p + 1] - brp[p];
+        used += nbp;
+        mx = nbp > mx ? nbp : mx;
+      }
+      slots += (int64_t)gp * G * ((mx + G - 1) / G);
+    }
+  }
+  atomicAdd(&acc[0], used);
+  atomicAdd(&acc[1], slots);
+}
+
 template <typename T>
 struct Tmp {
   T *p = nullptr;
@@ -193,6 +294,109 @@ int round_up(int v, int m) { return (v + m - 1) / m * m; }
     spc5_status _st = cuda_check((call), (what)); \
     if (_st != SPC5_OK) return _st;               \
   } while (0)
+
+namespace {
+
+// Builds the block-balanced plan and decides which plan the SpMV uses.
+spc5_status plan_flat(spc5_matrix *A, const int32_t *boff, cudaStream_t s,
+                      const PlanOptions &opt) {
+  const int64_t np = A->npanels, nb = A->nblocks;
+  int dev = 0, sms = 1;
+  CK(cudaGetDevice(&dev), "cudaGetDevice");
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "sm count");
+  // about eight tiles for every resident warp (48 per SM)
+  const int64_t want = (int64_t)8 * sms * 48;
+  int64_t fb = (nb + want - 1) / want;
+  fb = (fb + 31) / 32 * 32;
+  fb = std::min<int64_t>(std::max<int64_t>(fb, 64), 2048);
+  int fbcap = opt.fbcap > 0 ? opt.fbcap : env_int("SPC5_FLAT_BCAP", (int)fb);
+  if (fbcap < 32) {
+    set_error("invalid flat tile capacity");
+    return SPC5_EINVAL;
+  }
+  A->flat_bcap = fbcap;
+  A->fntiles = A->fnlong = A->fnpieces = 0;
+  CK(cudaMalloc((void **)&A->fsched, 2 * sizeof(uint32_t)), "alloc tile counters");
+  CK(cudaMemsetAsync(A->fsched, 0, 2 * sizeof(uint32_t), s), "zero tile counters");
+  A->device_bytes += 8;
+
+  // busy share of the row-group plan
+  Tmp<unsigned long long> acc(s);
+  CK(acc.alloc(2), "alloc");
+  CK(cudaMemsetAsync(acc.p, 0, 2 * sizeof(unsigned long long), s), "memset");
+  if (A->ntiles > 0)
+    k_group_efficiency<<<std::min<unsigned>(grid_for(A->ntiles), 1024u), kThreads, 0, s>>>(
+        A->tiles, A->ntiles, A->block_rowptr, A->group_panels, acc.p);
+  unsigned long long hacc[2] = {0, 0};
+  CK(cudaMemcpyAsync(hacc, acc.p, sizeof(hacc), cudaMemcpyDeviceToHost, s), "rd");
+
+  int32_t counts[3] = {0, 0, 0};
+  Tmp<int32_t> tc(s), lf(s), pc(s), tbase(s), lbase(s), sbase(s), tmp(s);
+  FlatParams F{np, nb, A->nnz, fbcap, A->block_rowptr, A->panel_vptr};
+  if (np > 0) {
+    CK(tc.alloc(np), "alloc");
+    CK(lf.alloc(np), "alloc");
+    CK(pc.alloc(np), "alloc");
+    CK(tbase.alloc(np + 1), "alloc");
+    CK(lbase.alloc(np + 1), "alloc");
+    CK(sbase.alloc(np + 1), "alloc");
+    CK(tmp.alloc(scan_tmp_elems(np + 1)), "alloc");
+    k_flat_counts<<<grid_for(np), kThreads, 0, s>>>(F, tc.p, lf.p, pc.p);
+    CK(device_scan<int32_t>(np + 1, ReadI32Pad{tc.p, np}, WriteI32{tbase.p}, AddI32{}, 0, false,
+                            tmp.p, s),
+       "scan flat tiles");
+    CK(device_scan<int32_t>(np + 1, ReadI32Pad{lf.p, np}, WriteI32{lbase.p}, AddI32{}, 0, false,
+                            tmp.p, s),
+       "scan flat long panels");
+    CK(device_scan<int32_t>(np + 1, ReadI32Pad{pc.p, np}, WriteI32{sbase.p}, AddI32{}, 0, false,
+                            tmp.p, s),
+       "scan flat pieces");
+    CK(cudaMemcpyAsync(&counts[0], tbase.p + np, 4, cudaMemcpyDeviceToHost, s), "rd");
+    CK(cudaMemcpyAsync(&counts[1], lbase.p + np, 4, cudaMemcpyDeviceToHost, s), "rd");
+    CK(cudaMemcpyAsync(&counts[2], sbase.p + np, 4, cudaMemcpyDeviceToHost, s), "rd");
+  }
+  CK(cudaStreamSynchronize(s), "sync flat plan counts");
+  A->group_efficiency = hacc[1] > 0 ? (double)hacc[0] / (double)hacc[1] : 1.0;
+  A->fntiles = counts[0];
+  A->fnlong = counts[1];
+  A->fnpieces = counts[2];
+  CK(cudaMalloc((void **)&A->ftiles, (size_t)std::max<int64_t>(A->fntiles, 1) * sizeof(Tile)),
+     "alloc flat tiles");
+  CK(cudaMalloc((void **)&A->flong_panels, (size_t)std::max<int64_t>(A->fnlong, 1) * 4), "alloc");
+  CK(cudaMalloc((void **)&A->flong_slots, (size_t)std::max<int64_t>(A->fnlong, 1) * 8), "alloc");
+  CK(cudaMalloc((void **)&A->fpartial,
+                (size_t)std::max<int64_t>(A->fnpieces, 1) * A->r * sizeof(double)),
+     "alloc flat partial");
+  A->device_bytes += A->fntiles * (int64_t)sizeof(Tile) + A->fnlong * 12 +
+                     A->fnpieces * A->r * (int64_t)sizeof(double);
+  if (np > 0)
+    k_flat_write<<<grid_for(np), kThreads, 0, s>>>(F, tbase.p, lbase.p, sbase.p, boff, A->ftiles,
+                                                   A->flong_panels, A->flong_slots);
+  CK(cudaGetLastError(), "flat plan kernels");
+  // The staged kernel reads its tiles as contiguous panel ranges; the flat
+  // plan is for the direct kernel.
+  int flat = opt.flat >= 0 ? opt.flat : env_int("SPC5_FLAT", A->group_efficiency < 0.7 ? 1 : 0);
+  A->flat = (A->kernel == 0 && flat) ? 1 : 0;
+  return SPC5_OK;
+}
+
+void free_flat(spc5_matrix *A) {
+  cudaFree(A->ftiles);
+  cudaFree(A->flong_panels);
+  cudaFree(A->flong_slots);
+  cudaFree(A->fpartial);
+  cudaFree(A->fsched);
+  A->device_bytes -= A->fntiles * (int64_t)sizeof(Tile) + A->fnlong * 12 +
+                     A->fnpieces * A->r * (int64_t)sizeof(double) + 8;
+  A->ftiles = nullptr;
+  A->flong_panels = nullptr;
+  A->flong_slots = nullptr;
+  A->fpartial = nullptr;
+  A->fsched = nullptr;
+  A->fntiles = A->fnlong = A->fnpieces = 0;
+}
+
+}  // namespace
 
 spc5_status plan_tiles(spc5_matrix *A, const uint32_t *mask32, const int32_t *boff,
                        cudaStream_t s, const PlanOptions &opt) {
@@ -268,10 +472,10 @@ spc5_status plan_tiles(spc5_matrix *A, const uint32_t *mask32, const int32_t *bo
   A->consumers = consumers;
   A->stage_bytes = stage;
   // direct kernel bodies: 0 per-block set-bit loop, 1 per-block predicated
-  // loop over the c bits, 2 row stream across blocks (row-group tiles with one
-  // lane per row; other tiles use body 0)
+  // loop over the c bits, 2 row stream across blocks, 3 queued row stream
+  // (2 and 3 on row-group tiles with one lane per row; other tiles use body 0)
   A->body = staged ? body
-                   : std::min(std::max(opt.body >= 0 ? opt.body : env_int("SPC5_BODY", 0), 0), 2);
+                   : std::min(std::max(opt.body >= 0 ? opt.body : env_int("SPC5_BODY", 0), 0), 3);
 
   if (np == 0) return SPC5_OK;
   PlanParams P{np, nb, gp, vcap, bcap, vcap - 32, log2g, log2g_segment,
@@ -327,7 +531,7 @@ spc5_status plan_tiles(spc5_matrix *A, const uint32_t *mask32, const int32_t *bo
     k_write_piece_tiles<<<grid_for(nb), kThreads, 0, s>>>(P, bpanel.p, pf.p, pscan.p, tbase.p,
                                                          boff, mask32, A->tiles);
   CK(cudaGetLastError(), "plan kernels");
-  return SPC5_OK;
+  return plan_flat(A, boff, s, opt);
 }
 
 namespace {
@@ -354,6 +558,7 @@ spc5_status replan(spc5_matrix *A, cudaStream_t s, const PlanOptions &opt) {
   A->long_slots = nullptr;
   A->partial = nullptr;
   A->ntiles = A->nlong = A->npieces = 0;
+  free_flat(A);
   const int64_t nb = A->nblocks;
   Tmp<uint32_t> mask32(s);
   Tmp<int32_t> boff(s), tmp(s);

@@ -18,7 +18,7 @@
 // row are reduced with shuffles before one lane writes y (Section 3.2: one
 // write of the reduced row result instead of r separate updates).
 //
-// Staged kernel (default): persistent, one CTA per SM.  Warp 0 is a
+// Staged kernel (SPC5_KERNEL=1, FP64): persistent, one CTA per SM.  Warp 0 is a
 // producer: for each tile of the work plan it issues bulk asynchronous
 // copies (cp.async.bulk, completion counted on an mbarrier) of the tile's
 // values, block columns, masks and panel pointers into a ring of shared
@@ -159,6 +159,37 @@ __device__ __forceinline__ AT group_sum(AT acc, int G) {
   return acc;
 }
 
+// y = alpha * acc + beta * y with the FP64 operations the arguments need:
+// mode 0 (alpha = 1, beta = 0) stores acc, mode 1 (beta = 0) scales it,
+// mode 2 reads y.  On GB300 every FP64 instruction, even a compare, takes a
+// slot of the FP64 pipe that the products need, so the mode is decided on
+// the host.
+template <typename AT>
+struct Scale {
+  AT alpha, beta;
+  int mode;
+};
+
+template <typename AT>
+Scale<AT> make_scale(double alpha, double beta) {
+  return Scale<AT>{(AT)alpha, (AT)beta, beta != 0.0 ? 2 : (alpha != 1.0 ? 1 : 0)};
+}
+
+template <typename AT>
+__device__ __forceinline__ void put_row(const Scale<AT> &sc, AT *y, int64_t row, AT acc) {
+  if (sc.mode == 0)
+    y[row] = acc;
+  else if (sc.mode == 1)
+    y[row] = sc.alpha * acc;
+  else
+    y[row] = fma(sc.beta, y[row], sc.alpha * acc);
+}
+
+template <typename AT>
+__device__ __forceinline__ void put_empty_row(const Scale<AT> &sc, AT *y, int64_t row) {
+  y[row] = (sc.mode == 2) ? sc.beta * y[row] : (AT)0;
+}
+
 // ------------------------------------------------------------ direct kernel --
 
 // Tile-scheduled kernel reading global memory directly.  Each warp walks the
@@ -168,47 +199,123 @@ __device__ __forceinline__ AT group_sum(AT acc, int G) {
 // instead of two (metadata, then values).  Many resident warps (up to 64
 // per SM) keep the FP64 pipe and the memory system busy.
 // Row-stream body for row-group tiles with one lane per row: the lane walks
-// its row's values across the panel's blocks (moving to the next block when
-// the current row mask is used up, with the next block's metadata loaded one
-// block ahead), one FMA per loop trip.  A warp then issues as many FP64 FMAs
-// as its longest row has values in the tile, instead of the sum over blocks
-// of the largest per-block bit count, which keeps the FP64 pipe's lanes busy
-// when rows have uneven bit counts per block.
+// its row's values across the panel's blocks, one FMA per loop trip, so a
+// warp issues as many FP64 FMAs as its longest row has values (plus one trip
+// for every block in which a row has no value), instead of the sum over
+// blocks of the largest per-block bit count.  Entering the next block is
+// written without branches (the new block's row bits, value offset and start
+// column are computed by every lane and selected where the current row bits
+// are used up), so the warp does not serialise lanes that change blocks at
+// different trips; the block after next is prefetched one block ahead.
 template <int R, int C, typename VT, typename AT, typename MaskT>
 __device__ __forceinline__ AT row_stream(const MaskT *__restrict__ masks,
                                          const int32_t *__restrict__ block_colidx,
                                          const VT *__restrict__ vals, const AT *__restrict__ x,
                                          int32_t bl, int32_t nbp, int32_t v, int q) {
-  const uint32_t row_low = (q == 0) ? 0u : ((1u << (q * C)) - 1u);
+  const int qc = q * C;
+  const uint32_t row_low = (1u << qc) - 1u;
   const uint32_t cmask = (1u << C) - 1u;
-  uint32_t m_next = 0u;
-  int32_t c_next = 0;
+  uint32_t m1 = 0u;  // next block to enter: mask word and start column
+  int32_t c1 = 0;
   if (nbp > 0) {
-    m_next = (uint32_t)masks[bl];
-    c_next = block_colidx[bl];
+    m1 = (uint32_t)masks[bl];
+    c1 = block_colidx[bl];
   }
-  int32_t b = 0, off = 0, col = 0;
+  int32_t b = 0;  // blocks entered
   uint32_t mq = 0u;
+  int32_t off = 0, col = 0;
   AT acc = 0;
   for (;;) {
-    while (mq == 0u && b < nbp) {
-      const uint32_t m = m_next;
-      col = c_next;
+    const bool enter = (mq == 0u) && (b < nbp);
+    if (!__any_sync(kFull, enter || mq != 0u)) break;
+    if (enter) {
+      mq = (m1 >> qc) & cmask;
+      off = v + __popc(m1 & row_low);
+      v += __popc(m1);
+      col = c1;
       ++b;
+      m1 = 0u;
       if (b < nbp) {
-        m_next = (uint32_t)masks[bl + b];
-        c_next = block_colidx[bl + b];
+        m1 = (uint32_t)masks[bl + b];
+        c1 = block_colidx[bl + b];
       }
-      off = v + __popc(m & row_low);
-      v += __popc(m);
-      mq = (m >> (q * C)) & cmask;
     }
-    if (!__any_sync(kFull, mq != 0u)) break;
     if (mq) {
       const int k = __ffs(mq) - 1;
-      mq &= mq - 1u;
       acc = fma((AT)widen(vals[off]), __ldg(x + col + k), acc);
+      mq &= mq - 1u;
       ++off;
+    }
+  }
+  return acc;
+}
+
+// Queued row-stream body (one lane per row): the lane loads the metadata of
+// its panel's next four blocks at once and packs its row's bits of the four
+// blocks into one word (block i at bits [i*c, (i+1)*c)), with each block's
+// start column and the value index of the row's first value in it.  A loop
+// trip then takes the lowest pending bit, selects its block's column and
+// value index (branch-free selects over the four slots) and does one FMA;
+// blocks in which the row has no value cost nothing, and the queue is
+// refilled only every four blocks, so a trip is a few integer instructions
+// around one FP64 FMA.
+template <typename T>
+__device__ __forceinline__ T sel4(int i, T a0, T a1, T a2, T a3) {
+  const T lo = (i & 1) ? a1 : a0;
+  const T hi = (i & 1) ? a3 : a2;
+  return (i & 2) ? hi : lo;
+}
+
+template <int R, int C, typename VT, typename AT, typename MaskT>
+__device__ __forceinline__ AT row_queue(const MaskT *__restrict__ masks,
+                                        const int32_t *__restrict__ block_colidx,
+                                        const VT *__restrict__ vals, const AT *__restrict__ x,
+                                        int32_t bl, int32_t nbp, int32_t v, int q) {
+  constexpr int LOG2C = C == 8 ? 3 : 2;
+  const int qc = q * C;
+  const uint32_t row_low = (1u << qc) - 1u;
+  const uint32_t cmask = (1u << C) - 1u;
+  int32_t b = 0;        // blocks queued so far
+  uint32_t w = 0u;      // pending row bits of the queued blocks
+  int32_t c0 = 0, c1 = 0, c2 = 0, c3 = 0;  // start columns of the queued blocks
+  int32_t o0 = 0, o1 = 0, o2 = 0, o3 = 0;  // value index of the row's first value in each
+  int slot = 0;
+  int32_t off = 0, col = 0;
+  AT acc = 0;
+  for (;;) {
+    const bool refill = (w == 0u) && (b < nbp);
+    if (!__any_sync(kFull, refill || w != 0u)) break;
+    if (refill) {
+      uint32_t m[4];
+      int32_t cc[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const bool ok = b + i < nbp;
+        m[i] = ok ? (uint32_t)masks[bl + b + i] : 0u;
+        cc[i] = ok ? block_colidx[bl + b + i] : 0;
+      }
+      int32_t o[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        o[i] = v + __popc(m[i] & row_low);
+        v += __popc(m[i]);
+        w |= ((m[i] >> qc) & cmask) << (i * C);
+      }
+      c0 = cc[0], c1 = cc[1], c2 = cc[2], c3 = cc[3];
+      o0 = o[0], o1 = o[1], o2 = o[2], o3 = o[3];
+      b += 4;
+      slot = -1;
+    }
+    if (w) {
+      const int k = __ffs(w) - 1;
+      const int i = k >> LOG2C;
+      const bool fresh = i != slot;
+      off = fresh ? sel4(i, o0, o1, o2, o3) : off;
+      col = fresh ? sel4(i, c0, c1, c2, c3) : col;
+      slot = i;
+      acc = fma((AT)widen(vals[off]), __ldg(x + col + (k & (C - 1))), acc);
+      ++off;
+      w &= w - 1u;
     }
   }
   return acc;
@@ -221,7 +328,7 @@ __global__ void __launch_bounds__(kDirectThreads, kDirectBlocksPerSM)
                  const int32_t *__restrict__ block_colidx,
                  const typename MaskType<R, C>::T *__restrict__ masks,
                  const VT *__restrict__ vals, const AT *__restrict__ x, AT *__restrict__ y,
-                 AT *__restrict__ partial, AT alpha, AT beta, int64_t nrows) {
+                 AT *__restrict__ partial, Scale<AT> sc, int64_t nrows) {
   constexpr int LOG2R = Log2<R>::v;
   const int lane = threadIdx.x & 31;
   const uint32_t cmask = (1u << C) - 1u;
@@ -258,6 +365,8 @@ __global__ void __launch_bounds__(kDirectThreads, kDirectBlocksPerSM)
     AT acc = 0;
     if (BODY == 2 && G == 1) {
       acc = row_stream<R, C>(masks, block_colidx, vals, x, bl, nbp, v, q);
+    } else if (BODY == 3 && G == 1) {
+      acc = row_queue<R, C>(masks, block_colidx, vals, x, bl, nbp, v, q);
     } else {
     constexpr bool UNROLL = BODY == 1;
     const int32_t maxnb = __reduce_max_sync(kFull, nbp);
@@ -292,15 +401,213 @@ __global__ void __launch_bounds__(kDirectThreads, kDirectBlocksPerSM)
         partial[(int64_t)cur.slot * R + q] = acc;
       } else {
         const int64_t row = ((int64_t)cur.p0 + j) * R + q;
-        if (row < nrows) {
-          AT out = alpha * acc;
-          if (beta != (AT)0) out = fma(beta, y[row], out);
-          y[row] = out;
-        }
+        if (row < nrows) put_row(sc, y, row, acc);
       }
     }
     cur = nxt;
     t = tn;
+  }
+}
+
+// -------------------------------------------------------------- flat kernel --
+
+// Block-balanced kernel for matrices whose panels hold very different
+// numbers of blocks (power-law rows): with lanes owning rows, a warp waits
+// for its longest row while the other lanes idle.  Here the blocks of a tile
+// (consecutive whole panels) are dealt to the lanes one block per lane per
+// round, so every lane has a block whatever the row lengths:
+//   - the value offset of a lane's block is the running offset plus the
+//     exclusive warp scan of the blocks' popcounts (Algorithm 1's idxVal);
+//   - a lane forms its block's r row sums (one FMA per set bit, x through
+//     L1/L2);
+//   - the panels ending inside the round are found from block_rowptr (a
+//     window of up to 32 panels per step, marked in a 32-bit word by a warp
+//     OR-reduction, their ids passed to the lanes through shared memory);
+//   - a segmented inclusive scan over the lanes adds the block sums of each
+//     panel; the lane holding a panel's last block writes the panel's r rows
+//     of y (one write per row, as in Section 3.2), and the panel still open
+//     at the end of the round carries its sums into the next round.
+// A piece of a long panel (mode & kPartial) holds one panel only: the lanes
+// keep private row sums over all rounds, reduce them with shuffles at the
+// end and write them to the partial buffer for the fixup kernel.
+// Warps take tiles from a counter (dynamic scheduling); the last warp to
+// finish resets the counter for the next launch.
+template <typename AT>
+__device__ __forceinline__ AT warp_sum(AT v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+
+__device__ __forceinline__ int warp_excl_scan(int v, int lane, int *total) {
+  int incl = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(kFull, incl, o);
+    if (lane >= o) incl += t;
+  }
+  *total = __shfl_sync(kFull, incl, 31);
+  return incl - v;
+}
+
+// Adds the block's products to s[q] (q < R): values packed row by row,
+// ascending bit within a row (Algorithm 1's order).
+template <int R, int C, typename VT, typename AT>
+__device__ __forceinline__ void block_rows(AT (&s)[R], uint32_t m, const VT *__restrict__ vals,
+                                           const AT *__restrict__ xp) {
+  const uint32_t cmask = (1u << C) - 1u;
+  int o = 0;
+#pragma unroll
+  for (int q = 0; q < R; ++q) {
+    uint32_t mq = (m >> (q * C)) & cmask;
+    AT acc = s[q];
+    while (mq) {
+      const int k = __ffs(mq) - 1;
+      mq &= mq - 1u;
+      acc = fma((AT)widen(vals[o]), __ldg(xp + k), acc);
+      ++o;
+    }
+    s[q] = acc;
+  }
+}
+
+template <int R>
+struct FlatBlocksPerSM {
+  static constexpr int v = R >= 4 ? 4 : 6;
+};
+
+template <int R, int C, typename VT, typename AT>
+__global__ void __launch_bounds__(kDirectThreads, FlatBlocksPerSM<R>::v)
+    k_spmv_flat(const Tile *__restrict__ tiles, int32_t ntiles, uint32_t *sched,
+                const int32_t *__restrict__ brp, const int32_t *__restrict__ block_colidx,
+                const typename MaskType<R, C>::T *__restrict__ masks,
+                const VT *__restrict__ vals, const AT *__restrict__ x, AT *__restrict__ y,
+                AT *__restrict__ partial, Scale<AT> sc, int64_t nrows) {
+  __shared__ int32_t s_pid[kDirectThreads];
+  int32_t *pid = s_pid + (threadIdx.x & ~31);
+  const int lane = threadIdx.x & 31;
+  uint32_t grab = 0;
+  if (lane == 0) grab = atomicAdd(&sched[0], 1u);
+  int32_t t = (int32_t)__shfl_sync(kFull, grab, 0);
+  while (t < ntiles) {
+    if (lane == 0) grab = atomicAdd(&sched[0], 1u);  // next tile, used after this one
+    const Tile cur = tiles[t];
+    int32_t v = cur.v0;
+    uint32_t m_next = 0u;
+    int32_t c_next = 0;
+    if (cur.b0 + lane < cur.b1) {
+      m_next = (uint32_t)masks[cur.b0 + lane];
+      c_next = block_colidx[cur.b0 + lane];
+    }
+    if (cur.mode & kPartial) {
+      AT s[R];
+#pragma unroll
+      for (int q = 0; q < R; ++q) s[q] = 0;
+      for (int32_t base = cur.b0; base < cur.b1; base += 32) {
+        const uint32_t m = m_next;
+        const int32_t col = c_next;
+        const int32_t bn = base + 32 + lane;
+        m_next = bn < cur.b1 ? (uint32_t)masks[bn] : 0u;
+        c_next = bn < cur.b1 ? block_colidx[bn] : 0;
+        int total;
+        const int excl = warp_excl_scan(__popc(m), lane, &total);
+        block_rows<R, C>(s, m, vals + v + excl, x + col);
+        v += total;
+      }
+#pragma unroll
+      for (int q = 0; q < R; ++q) {
+        const AT tot = warp_sum(s[q]);
+        if (lane == q) partial[(int64_t)cur.slot * R + q] = tot;
+      }
+    } else {
+      // rows of the tile's empty panels
+      for (int32_t p = cur.p0 + lane; p < cur.p1; p += 32) {
+        if (brp[p] == brp[p + 1]) {
+#pragma unroll
+          for (int q = 0; q < R; ++q) {
+            const int64_t row = (int64_t)p * R + q;
+            if (row < nrows) put_empty_row(sc, y, row);
+          }
+        }
+      }
+      AT carry = 0;  // lane q < R: row q's sum of the panel still open
+      int32_t pcur = cur.p0;
+      for (int32_t base = cur.b0; base < cur.b1; base += 32) {
+        const int32_t lim = (base + 32 < cur.b1) ? base + 32 : cur.b1;
+        const uint32_t m = m_next;
+        const int32_t col = c_next;
+        const int32_t bn = base + 32 + lane;
+        m_next = bn < cur.b1 ? (uint32_t)masks[bn] : 0u;
+        c_next = bn < cur.b1 ? block_colidx[bn] : 0;
+        int total;
+        const int excl = warp_excl_scan(__popc(m), lane, &total);
+        AT s[R];
+#pragma unroll
+        for (int q = 0; q < R; ++q) s[q] = 0;
+        block_rows<R, C>(s, m, vals + v + excl, x + col);
+        v += total;
+        // panels whose last block lies in [base, lim): bit (end - 1 - base)
+        uint32_t ends = 0u;
+        for (int32_t w = pcur;; w += 32) {
+          const int32_t p = w + lane;
+          const bool in = p < cur.p1;
+          const int32_t st = in ? brp[p] : 0;
+          const int32_t en = in ? brp[p + 1] : 0;
+          const bool mark = in && en > st && en > base && en <= lim;
+          if (mark) pid[en - 1 - base] = p;
+          ends |= __reduce_or_sync(kFull, mark ? (1u << (en - 1 - base)) : 0u);
+          const unsigned beyond = __ballot_sync(kFull, !in || en > lim);
+          if (beyond) {
+            pcur = w + __ffs(beyond) - 1;
+            break;
+          }
+        }
+        __syncwarp();
+        // segmented inclusive scan: lane adds lane - o when no panel ends in [lane - o, lane)
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const bool same = lane >= o && ((ends >> (lane - o)) & ((1u << o) - 1u)) == 0u;
+#pragma unroll
+          for (int q = 0; q < R; ++q) {
+            const AT tq = __shfl_up_sync(kFull, s[q], o);
+            if (same) s[q] += tq;
+          }
+        }
+        const int last = lim - 1 - base;
+        const int first_end = ends ? __ffs(ends) - 1 : last;
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+          const AT cq = __shfl_sync(kFull, carry, q);
+          if (lane == first_end) s[q] += cq;
+        }
+        if ((ends >> lane) & 1u) {
+          const int64_t p = pid[lane];
+#pragma unroll
+          for (int q = 0; q < R; ++q) {
+            const int64_t row = p * R + q;
+            if (row < nrows) put_row(sc, y, row, s[q]);
+          }
+        }
+        // the segment after the last end stays open (its sums include the
+        // carry when it is also the first segment)
+        const bool open = ((ends >> last) & 1u) == 0u;
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+          const AT sq = __shfl_sync(kFull, s[q], last);
+          if (lane == q) carry = open ? sq : (AT)0;
+        }
+        __syncwarp();
+      }
+    }
+    t = (int32_t)__shfl_sync(kFull, grab, 0);
+  }
+  // every warp has made its last grab: the last one to finish resets the counters
+  if (lane == 0) {
+    const uint32_t nwarps = gridDim.x * (blockDim.x >> 5);
+    if (atomicAdd(&sched[1], 1u) == nwarps - 1) {
+      atomicExch(&sched[0], 0u);
+      atomicExch(&sched[1], 0u);
+    }
   }
 }
 
@@ -623,7 +930,7 @@ __global__ void __launch_bounds__(32 * 17, 1) k_spmv_staged(const StagedParams P
 // y rows of panels that were cut into pieces: add the pieces in order.
 template <int R, typename AT>
 __global__ void k_fixup(int64_t nlong, const int32_t *long_panels, const int32_t *long_slots,
-                        const AT *partial, AT *y, AT alpha, AT beta, int64_t nrows) {
+                        const AT *partial, AT *y, Scale<AT> sc, int64_t nrows) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nlong * R;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t l = i / R;
@@ -632,11 +939,7 @@ __global__ void k_fixup(int64_t nlong, const int32_t *long_panels, const int32_t
     AT acc = 0;
     for (int32_t s = long_slots[2 * l]; s < long_slots[2 * l + 1]; ++s)
       acc += partial[(int64_t)s * R + q];
-    if (row < nrows) {
-      AT out = alpha * acc;
-      if (beta != (AT)0) out = fma(beta, y[row], out);
-      y[row] = out;
-    }
+    if (row < nrows) put_row(sc, y, row, acc);
   }
 }
 
@@ -704,7 +1007,7 @@ cudaError_t launch_staged(const spc5_matrix *A, const double *x, double *y, doub
     int64_t threads = A->nlong * R;
     int blocks = (int)std::min<int64_t>((threads + 255) / 256, 4096);
     k_fixup<R, double><<<blocks, 256, 0, s>>>(A->nlong, A->long_panels, A->long_slots, partial,
-                                              y, alpha, beta, A->nrows);
+                                              y, make_scale<double>(alpha, beta), A->nrows);
     e = cudaGetLastError();
   }
   return e;
@@ -722,8 +1025,8 @@ cudaError_t launch_direct(const spc5_matrix *A, const AT *x, AT *y, double alpha
     if (blocks > resident) blocks = resident;
     k_spmv_tiles<R, C, BODY, VT, AT><<<(unsigned)blocks, kDirectThreads, 0, s>>>(
         A->tiles, A->ntiles, A->block_rowptr, A->panel_vptr, A->block_colidx,
-        (const MaskT *)A->masks, (const VT *)A->values, x, y, partial, (AT)alpha, (AT)beta,
-        A->nrows);
+        (const MaskT *)A->masks, (const VT *)A->values, x, y, partial,
+        make_scale<AT>(alpha, beta), A->nrows);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -731,7 +1034,34 @@ cudaError_t launch_direct(const spc5_matrix *A, const AT *x, AT *y, double alpha
     int64_t threads = A->nlong * R;
     int fblocks = (int)std::min<int64_t>((threads + 255) / 256, 4096);
     k_fixup<R, AT><<<fblocks, 256, 0, s>>>(A->nlong, A->long_panels, A->long_slots, partial, y,
-                                           (AT)alpha, (AT)beta, A->nrows);
+                                           make_scale<AT>(alpha, beta), A->nrows);
+    e = cudaGetLastError();
+  }
+  return e;
+}
+
+template <int R, int C, typename VT, typename AT>
+cudaError_t launch_flat(const spc5_matrix *A, const AT *x, AT *y, double alpha, double beta,
+                        cudaStream_t s, AT *partial, uint32_t *sched) {
+  using MaskT = typename MaskType<R, C>::T;
+  cudaError_t e = cudaSuccess;
+  if (A->fntiles > 0) {
+    const int warps_per_block = kDirectThreads / 32;
+    int64_t blocks = (A->fntiles + warps_per_block - 1) / warps_per_block;
+    const int64_t resident = (int64_t)num_sms() * FlatBlocksPerSM<R>::v;
+    if (blocks > resident) blocks = resident;
+    k_spmv_flat<R, C, VT, AT><<<(unsigned)blocks, kDirectThreads, 0, s>>>(
+        A->ftiles, (int32_t)A->fntiles, sched, A->block_rowptr, A->block_colidx,
+        (const MaskT *)A->masks, (const VT *)A->values, x, y, partial,
+        make_scale<AT>(alpha, beta), A->nrows);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  if (A->fnlong > 0) {
+    int64_t threads = A->fnlong * R;
+    int fblocks = (int)std::min<int64_t>((threads + 255) / 256, 4096);
+    k_fixup<R, AT><<<fblocks, 256, 0, s>>>(A->fnlong, A->flong_panels, A->flong_slots, partial,
+                                           y, make_scale<AT>(alpha, beta), A->nrows);
     e = cudaGetLastError();
   }
   return e;
@@ -747,6 +1077,9 @@ cudaError_t launch_direct_body(const spc5_matrix *A, const void *x, void *y, dou
     case 2:
       return launch_direct<R, C, 2, VT, AT>(A, (const AT *)x, (AT *)y, alpha, beta, s,
                                             (AT *)partial);
+    case 3:
+      return launch_direct<R, C, 3, VT, AT>(A, (const AT *)x, (AT *)y, alpha, beta, s,
+                                            (AT *)partial);
     default:
       return launch_direct<R, C, 0, VT, AT>(A, (const AT *)x, (AT *)y, alpha, beta, s,
                                             (AT *)partial);
@@ -755,7 +1088,17 @@ cudaError_t launch_direct_body(const spc5_matrix *A, const void *x, void *y, dou
 
 template <int R, int C>
 cudaError_t launch(const spc5_matrix *A, const void *x, void *y, double alpha, double beta,
-                   cudaStream_t s, void *partial) {
+                   cudaStream_t s, void *partial, uint32_t *sched) {
+  if (A->flat) {
+    if (A->value_dtype == SPC5_F32)
+      return launch_flat<R, C, float, float>(A, (const float *)x, (float *)y, alpha, beta, s,
+                                             (float *)partial, sched);
+    if (A->value_dtype == SPC5_BF16)
+      return launch_flat<R, C, uint16_t, float>(A, (const float *)x, (float *)y, alpha, beta, s,
+                                                (float *)partial, sched);
+    return launch_flat<R, C, double, double>(A, (const double *)x, (double *)y, alpha, beta, s,
+                                             (double *)partial, sched);
+  }
   if (A->value_dtype == SPC5_F32)
     return launch_direct_body<R, C, float, float>(A, x, y, alpha, beta, s, partial);
   if (A->value_dtype == SPC5_BF16)
@@ -776,20 +1119,23 @@ cudaError_t launch(const spc5_matrix *A, const void *x, void *y, double alpha, d
 
 int spmv_launches(const spc5_matrix *A) {
   if (A->nrows == 0) return 0;
+  if (A->flat) return (A->fntiles > 0 ? 1 : 0) + (A->fnlong > 0 ? 1 : 0);
   return (A->ntiles > 0 ? 1 : 0) + (A->nlong > 0 ? 1 : 0);
 }
 
+int64_t spmv_pieces(const spc5_matrix *A) { return A->flat ? A->fnpieces : A->npieces; }
+
 spc5_status spmv_device_scratch(const spc5_matrix *A, const void *x, void *y, double alpha,
-                                double beta, cudaStream_t s, void *partial) {
+                                double beta, cudaStream_t s, void *partial, uint32_t *sched) {
   if (A->nrows == 0) return SPC5_OK;
   cudaError_t e;
   switch (A->r * 100 + A->c) {
-    case 108: e = launch<1, 8>(A, x, y, alpha, beta, s, partial); break;
-    case 204: e = launch<2, 4>(A, x, y, alpha, beta, s, partial); break;
-    case 208: e = launch<2, 8>(A, x, y, alpha, beta, s, partial); break;
-    case 404: e = launch<4, 4>(A, x, y, alpha, beta, s, partial); break;
-    case 408: e = launch<4, 8>(A, x, y, alpha, beta, s, partial); break;
-    case 804: e = launch<8, 4>(A, x, y, alpha, beta, s, partial); break;
+    case 108: e = launch<1, 8>(A, x, y, alpha, beta, s, partial, sched); break;
+    case 204: e = launch<2, 4>(A, x, y, alpha, beta, s, partial, sched); break;
+    case 208: e = launch<2, 8>(A, x, y, alpha, beta, s, partial, sched); break;
+    case 404: e = launch<4, 4>(A, x, y, alpha, beta, s, partial, sched); break;
+    case 408: e = launch<4, 8>(A, x, y, alpha, beta, s, partial, sched); break;
+    case 804: e = launch<8, 4>(A, x, y, alpha, beta, s, partial, sched); break;
     default:
       set_error("unsupported block shape");
       return SPC5_EUNSUPPORTED_RC;
@@ -799,7 +1145,8 @@ spc5_status spmv_device_scratch(const spc5_matrix *A, const void *x, void *y, do
 
 spc5_status spmv_device(const spc5_matrix *A, const void *x, void *y, double alpha, double beta,
                         cudaStream_t s) {
-  return spmv_device_scratch(A, x, y, alpha, beta, s, A->partial);
+  return spmv_device_scratch(A, x, y, alpha, beta, s, A->flat ? A->fpartial : A->partial,
+                             A->fsched);
 }
 
 }  // namespace spc5

@@ -5,7 +5,8 @@
 // lanes per row shorten each warp's serial block loop, fewer lanes keep the
 // x accesses of neighbouring rows together.  Rather than a model, the tuner
 // times the candidates on the caller's vectors:
-//   spc5_tune           G in {1, 2, 4, 8} (those that fit 32 / r) for one
+//   spc5_tune           G in {1, 2, 4, 8} (those that fit 32 / r), the two
+//                       row-stream bodies and the block-balanced plan for one
 //                       converted matrix, keeping the fastest plan;
 //   spc5_convert_tuned  every requested beta(r,c), each tuned, keeping the
 //                       fastest matrix.
@@ -55,17 +56,24 @@ spc5_status tune(spc5_matrix *A, const void *x, void *y, int iters, cudaStream_t
   int log2r = 0;
   while ((1 << log2r) < A->r) ++log2r;
   const int max_log2g = std::min(3, 5 - log2r);
-  double best = -1.0;
-  int best_g = 0, best_body = 0;
-  // candidates: (lanes per row, body); the row-stream body needs one lane per row
-  std::vector<std::pair<int, int>> cands;
-  cands.push_back({0, 2});
-  for (int lg = 0; lg <= max_log2g; ++lg) cands.push_back({lg, 0});
+  struct Cand {
+    int log2g, body, flat;
+  };
+  // row-group plans (lanes per row; the row-stream bodies need one lane per
+  // row) and the block-balanced plan
+  std::vector<Cand> cands;
+  cands.push_back({0, 0, 1});
+  cands.push_back({0, 2, 0});
+  cands.push_back({0, 3, 0});
+  for (int lg = 0; lg <= max_log2g; ++lg) cands.push_back({lg, 0, 0});
+  double best = -1.0, best_rows = -1.0;
+  size_t best_i = 0, best_rows_i = 1;
   for (size_t i = 0; i < cands.size(); ++i) {
     PlanOptions o;
     o.kernel = 0;
-    o.log2g = cands[i].first;
-    o.body = cands[i].second;
+    o.log2g = cands[i].log2g;
+    o.body = cands[i].body;
+    o.flat = cands[i].flat;
     spc5_status st = replan(A, s, o);
     if (st != SPC5_OK) return st;
     double us = time_spmv(A, x, y, iters, s);
@@ -75,15 +83,21 @@ spc5_status tune(spc5_matrix *A, const void *x, void *y, int iters, cudaStream_t
     }
     if (best < 0 || us < best) {
       best = us;
-      best_g = cands[i].first;
-      best_body = cands[i].second;
+      best_i = i;
+    }
+    if (!cands[i].flat && (best_rows < 0 || us < best_rows)) {
+      best_rows = us;
+      best_rows_i = i;
     }
   }
-  if (best_g != cands.back().first || best_body != cands.back().second) {
+  // The row-group plan is kept at its own best (the transposed product, the
+  // gradient and the batched kernel use it even when the SpMV is flat).
+  if (best_i != cands.size() - 1 || best_rows_i != cands.size() - 1) {
     PlanOptions o;
     o.kernel = 0;
-    o.log2g = best_g;
-    o.body = best_body;
+    o.log2g = cands[best_rows_i].log2g;
+    o.body = cands[best_rows_i].body;
+    o.flat = cands[best_i].flat;
     spc5_status st = replan(A, s, o);
     if (st != SPC5_OK) return st;
   }

@@ -46,7 +46,8 @@ class Info(ctypes.Structure):
                 ("lanes_per_row", ctypes.c_int32), ("launches_per_spmv", ctypes.c_int32),
                 ("ntiles", ctypes.c_int64), ("long_panels", ctypes.c_int64),
                 ("stages", ctypes.c_int32), ("consumers", ctypes.c_int32),
-                ("device_error", ctypes.c_uint32), ("tuned_us", ctypes.c_double)]
+                ("device_error", ctypes.c_uint32), ("tuned_us", ctypes.c_double),
+                ("flat", ctypes.c_int32), ("group_efficiency", ctypes.c_double)]
 
 
 class CGReport(ctypes.Structure):

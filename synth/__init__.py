@@ -178,6 +178,9 @@ def uniform(nrows: int, per_row: int = 16, ncols: int | None = None,
 
 def powerlaw(n: int, s: float = 2.0, mean: float = 20.0, sigma: float = 1000.0,
              long_row: int = 4000, seed: int = 3) -> CSR:
+    """Zipf(s) row lengths rescaled to `mean`; rows of at most `long_row`
+    entries take distinct columns round(i + N(0, sigma)), longer rows take
+    distinct uniform columns.  Requires long_row <= 4 * sigma."""
     return _call("synth_powerlaw", n, s, mean, sigma, long_row, seed,
                  name=f"powerlaw_{n}")
 

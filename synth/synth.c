@@ -278,6 +278,9 @@ int synth_powerlaw(int64_t n, double s, double mean, double sigma, int64_t long_
                    uint64_t seed, synth_csr *out) {
   memset(out, 0, sizeof(*out));
   if (n < 1 || s <= 0.0 || mean <= 0.0 || sigma <= 0.0) return SYNTH_EINVAL;
+  /* rows of up to long_row entries draw distinct columns from N(i, sigma)
+   * by rejection, which needs about 4 sigma of room for long_row columns */
+  if ((double)long_row > 4.0 * sigma) return SYNTH_EINVAL;
   double *cdf = (double *)malloc((size_t)n * sizeof(double));
   int64_t *len = (int64_t *)malloc((size_t)n * sizeof(int64_t));
   if (!cdf || !len) {

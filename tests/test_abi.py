@@ -61,3 +61,26 @@ def test_rejects_unsupported_shape_before_touching_the_gpu():
     assert lib.spc5_spmv(None, None, None, 1.0, 0.0, None) == 1  # EINVAL on a NULL handle
     assert lib.spc5_matrix_info(None, None) == 1
     assert lib.spc5_destroy(None) == 0
+
+
+@pytest.mark.parametrize("cname,pystruct", [("spc5_info", "Info"), ("spc5_cg_report", "CGReport")])
+def test_struct_layout_matches_header(tmp_path, cname, pystruct):
+    """The binding's ctypes mirrors of the header's structs have the C
+    compiler's size and field offsets."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    cls = getattr(spc5.spc5, pystruct)
+    lines = [f'printf("%zu\\n", sizeof({cname}));']
+    lines += [f'printf("%zu\\n", offsetof({cname}, {f}));' for f, _ in cls._fields_]
+    src = tmp_path / "layout.c"
+    src.write_text('#include <stddef.h>\n#include <stdio.h>\n#include "spc5.h"\n'
+                   "int main(void) {\n" + "\n".join(lines) + "\nreturn 0;\n}\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)],
+                   check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], check=True, capture_output=True,
+                                          text=True).stdout.split()]
+    assert got[0] == ctypes.sizeof(cls)
+    assert got[1:] == [getattr(cls, f).offset for f, _ in cls._fields_]

@@ -171,15 +171,17 @@ def test_invalid_csr_is_rejected_on_device():
 
 @pytest.mark.parametrize("log2g", [0, 1, 2, 3])
 def test_direct_kernel_lane_mappings(monkeypatch, log2g):
-    """The direct tile kernel with every lanes-per-row mapping and both row
-    bodies, with and without long-panel pieces."""
+    """The direct tile kernel with every lanes-per-row mapping and every row
+    body (set-bit loop, predicated loop, row stream, queued row stream), with
+    and without long-panel pieces."""
     monkeypatch.setenv("SPC5_KERNEL", "0")
+    monkeypatch.setenv("SPC5_FLAT", "0")
     monkeypatch.setenv("SPC5_LOG2G_GROUP", str(log2g))
     A = synth.powerlaw(30_000, seed=12)
     x = synth.vector_uniform(A.ncols, seed=4)
     y_ref, scale = oracle.csr_spmv(A, x)
     for r, c in [(1, 8), (4, 4), (8, 4)]:
-        for body in ("0", "1", "2"):
+        for body in ("0", "1", "2", "3"):
             for vcap in ("", "2048"):
                 monkeypatch.setenv("SPC5_BODY", body)
                 if vcap:
@@ -238,6 +240,7 @@ def test_staged_kernel_plans(monkeypatch, setting, r, c):
 def test_integer_exact_with_pieces(monkeypatch, kernel):
     """Integer data through pieces and fixup: bit-exact, both kernels."""
     monkeypatch.setenv("SPC5_KERNEL", kernel)
+    monkeypatch.setenv("SPC5_FLAT", "0")
     monkeypatch.setenv("SPC5_VCAP", "512")
     monkeypatch.setenv("SPC5_BCAP", "128")
     A = synth.bernoulli(40, 20_000, 0.3, seed=9, integer_values=True)

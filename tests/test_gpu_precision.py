@@ -90,9 +90,10 @@ def test_reduced_precision_spmv_error(mats, dtype, r, c):
         assert np.all(np.abs(y - y_dq) <= (k + 2) * 2.0 ** -24 * scale_dq)
 
 
-@pytest.mark.parametrize("body", ["0", "2"])
+@pytest.mark.parametrize("body", ["0", "2", "3"])
 @pytest.mark.parametrize("dtype", list(DTYPES))
 def test_reduced_precision_integer_exact(monkeypatch, dtype, body):
+    monkeypatch.setenv("SPC5_FLAT", "0")
     monkeypatch.setenv("SPC5_BODY", body)
     for seed in range(3):
         A = synth.bernoulli(77, 300, 0.4, seed=seed, integer_values=True)
@@ -102,14 +103,17 @@ def test_reduced_precision_integer_exact(monkeypatch, dtype, body):
             assert np.array_equal(y, A.todense() @ x.astype(np.float64))
 
 
+@pytest.mark.parametrize("flat", ["0", "1"])
 @pytest.mark.parametrize("dtype", list(DTYPES))
-def test_reduced_precision_pieces_alpha_beta_host(monkeypatch, dtype):
+def test_reduced_precision_pieces_alpha_beta_host(monkeypatch, dtype, flat):
+    monkeypatch.setenv("SPC5_FLAT", flat)
     monkeypatch.setenv("SPC5_VCAP", "2048")
     monkeypatch.setenv("SPC5_BCAP", "256")
     tol = DTYPES[dtype][1]
     A = synth.powerlaw(50_000, seed=7)
     M = _convert(A, 4, 8, dtype)
     assert M.info()["long_panels"] > 0
+    assert M.info()["flat"] == int(flat)
     x = synth.vector_uniform(A.ncols, seed=2)
     x32 = x.astype(np.float32)
     y0 = synth.vector_normal(A.nrows, seed=5).astype(np.float32)
