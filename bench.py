@@ -64,6 +64,7 @@ def parse_args():
     ap.add_argument("--no-precision", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-cg", action="store_true")
+    ap.add_argument("--no-grad", action="store_true")
     ap.add_argument("--no-tune", action="store_true",
                     help="keep the planner's default mapping instead of autotuning it")
     ap.add_argument("--cases-out", default=None, help="write the per-case table here")
@@ -342,6 +343,51 @@ def cg_section(torch, spc5, synth, stream, log):
     return out
 
 
+def grad_section(torch, spc5, synth, log, reps=10):
+    """torch.autograd.Function y = A(vals) x on the 27-point stencil on 100^3
+    with FP32 value storage, x ~ U[-1,1) FP32: forward (values stored into the
+    matrix, then the SpMV) and backward (dx = A^T g and dvals = g[row] x[col]
+    over the stored entries), timed with CUDA events."""
+    from paper_2307_14774_gb300.autograd import SpMVFunction
+    A = synth.workload("stencil27")
+    dev = [torch.from_numpy(a).cuda() for a in (A.rowptr, A.colidx, A.vals)]
+    M = spc5.spc5_convert_csr(A.nrows, A.ncols, A.nnz, *dev, store_dtype=spc5.SPC5_F32,
+                              r=4, c=8)
+    vals = dev[2].clone().requires_grad_(True)
+    x = torch.from_numpy(synth.vector_uniform(A.ncols, seed=1).astype("float32")).cuda()
+    x.requires_grad_(True)
+    g = torch.from_numpy(synth.vector_normal(A.nrows, seed=2).astype("float32")).cuda()
+    flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device="cuda")
+
+    def step(backward):
+        vals.grad = None
+        x.grad = None
+        y = SpMVFunction.apply(M, vals, x)
+        if backward:
+            y.backward(g)
+
+    out = {"matrix": "27-point stencil 100^3, FP32 values", "nnz": A.nnz}
+    for name, bwd in (("forward", False), ("forward_backward", True)):
+        for _ in range(3):
+            step(bwd)
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            step(bwd)
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        ms = sorted(ts)[len(ts) // 2]
+        # forward: 2 nnz flops; backward: 2 nnz (A^T g) + nnz (g[row] x[col])
+        flops = 2 * A.nnz + (3 * A.nnz if bwd else 0)
+        out[name] = {"ms": round(ms, 4), "gflops": round(flops / (ms * 1e-3) / 1e9, 1)}
+    log(f"autograd: {out}")
+    del M, dev, flush
+    return out
+
+
 def batched_section(torch, spc5, synth, stream, log, nmat=256, reps=10):
     """256 matrices of uneven size (n log-uniform in [1e3, 2e5]; 5-point,
     27-point and power-law generators in turn), FP32 values, each converted
@@ -570,6 +616,8 @@ def run_native(args):
         result["batched"] = batched_section(torch, spc5, synth, stream, log)
     if not args.no_cg and rank == 0:
         result["ircg"] = cg_section(torch, spc5, synth, stream, log)
+    if not args.no_grad and rank == 0:
+        result["autograd"] = grad_section(torch, spc5, synth, log)
 
     # end to end through the C-ABI with host vectors: every step copies x from
     # pinned host memory and reads y back

@@ -117,3 +117,35 @@ def test_autograd_gradcheck_small():
     x = torch.from_numpy(synth.vector_uniform(A.ncols, seed=1)).cuda().requires_grad_(True)
     assert torch.autograd.gradcheck(lambda v, xx: SpMVFunction.apply(M, v, xx), (vals, x),
                                     eps=1e-6, atol=1e-9)
+
+
+def test_autograd_fp32_storage_against_dense_gradient():
+    """FP32 value storage (the differentiation workload's precision): the
+    gradients, computed in FP32, against the dense FP64 gradient of the same
+    function on the FP32-rounded values and x, within FP32 rounding of
+    sum |terms|; values gradient per stored entry, in CSR order."""
+    torch = torch_cuda()
+    A = synth.stencil27(16, 16, 16, values="normal")
+    rowptr, colidx, vv = (torch.from_numpy(a).cuda() for a in (A.rowptr, A.colidx, A.vals))
+    M = spc5.spc5_convert_csr(A.nrows, A.ncols, A.nnz, rowptr, colidx, vv,
+                              store_dtype=spc5.SPC5_F32, r=4, c=8)
+    vals = torch.from_numpy(A.vals.copy()).cuda().requires_grad_(True)
+    x32 = synth.vector_uniform(A.ncols, seed=2).astype(np.float32)
+    x = torch.from_numpy(x32).cuda().requires_grad_(True)
+    w = torch.from_numpy(synth.vector_normal(A.nrows, seed=3).astype(np.float32)).cuda()
+    y = SpMVFunction.apply(M, vals, x)
+    assert y.dtype == torch.float32
+    (y * w).sum().backward()
+    assert vals.grad.dtype == torch.float64 and x.grad.dtype == torch.float32
+    gv, gx = vals.grad.cpu().numpy(), x.grad.cpu().numpy().astype(np.float64)
+    wn = w.cpu().numpy().astype(np.float64)
+    q = oracle.quantize(A.vals, "f32").astype(np.float64)
+    Aq = synth.CSR(A.nrows, A.ncols, A.rowptr, A.colidx, q)
+    D = Aq.todense()
+    # dx = A^T w: FP32 accumulation of at most 27 terms per column
+    bound = 30 * 2.0 ** -24 * (np.abs(D.T) @ np.abs(wn))
+    assert np.all(np.abs(gx - D.T @ wn) <= bound)
+    # dvals[e] = w[row] * x[col]: one FP32 product, exactly rounded
+    rows = np.repeat(np.arange(A.nrows), np.diff(A.rowptr))
+    exact = wn[rows] * x32.astype(np.float64)[A.colidx]
+    assert np.array_equal(gv, exact.astype(np.float32).astype(np.float64))
