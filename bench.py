@@ -569,8 +569,8 @@ def run_native(args):
                           "fp64_frac": round(gf / (FP64_PEAK_TFLOPS * 1e3), 3),
                           "bound": "alu" if t_fp64 > t_hbm else "hbm",
                           "floor_us": round(max(t_hbm, t_fp64), 2),
-                          "plan": ("flat" if cs["info"]["flat"]
-                                   else f"rows/G{cs['info']['lanes_per_row']}"),
+                          "plan": ({1: "blocks", 2: "expanded"}.get(cs["info"]["flat"])
+                                   or f"rows/G{cs['info']['lanes_per_row']}"),
                           "convert_ms": round(cs["convert_s"] * 1e3, 2)})
 
     result = {
@@ -586,7 +586,7 @@ def run_native(args):
                          f"{min(cs['bytes'] for cs in cases) / 1e6:.0f} MB (L2 129 MB)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "mapping": "autotuned per matrix during setup (spc5_tune): lanes per row, "
-                              "row-stream body, or the block-balanced plan"
+                              "row-stream bodies, block-balanced or expanded plan"
                               if not args.no_tune else "planner default"},
         "roofline": roofline_object(achieved, achieved_tflops, hbm, peak_kind, traffic,
                                     bytes_per_step, flops_per_step),

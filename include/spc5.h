@@ -80,10 +80,11 @@ typedef struct {
   int32_t consumers;       /* consumer warps per SM */
   uint32_t device_error;   /* nonzero if a kernel gave up a bounded wait (reading it syncs) */
   double tuned_us;         /* SpMV time of the plan chosen by spc5_tune, 0 if untuned */
-  int32_t flat;            /* 1: the SpMV deals blocks to lanes evenly (block-balanced plan);
-                              0: lanes own rows (row-group plan) */
-  double group_efficiency; /* busy share of the row-group plan's block slots; the converter
-                              picks the block-balanced plan below 0.7 */
+  int32_t flat;            /* work mapping of the SpMV: 0 lanes own rows (row-group plan);
+                              1 blocks dealt to lanes evenly (block-balanced plan);
+                              2 each tile's values split evenly over the lanes (expanded) */
+  double group_efficiency; /* busy share of the row-group plan's block slots; below 0.7 the
+                              converter picks plan 1 for r <= 2 and plan 2 for r >= 4 */
 } spc5_info;
 
 /*
@@ -154,11 +155,13 @@ spc5_status spc5_export(const spc5_matrix *A, const int32_t **block_rowptr,
  * share the handle's buffer of partial sums and its tile counter.
  *
  * Work mapping (chosen at conversion, see spc5_info.flat): lanes own rows
- * of groups of panels (row-group plan), or the blocks of runs of whole
- * panels are dealt to the lanes evenly and the row sums are assembled by a
- * segmented warp scan (block-balanced plan, for matrices whose panels hold
- * very different numbers of blocks).  Both give y within the same error
- * bound; the summation order differs.
+ * of groups of panels (row-group plan); or, for matrices whose rows have
+ * very different lengths, the blocks of runs of panels are dealt to the
+ * lanes evenly and row sums are assembled by a segmented warp scan
+ * (block-balanced plan), or a warp lays the values of a run of panels out
+ * row by row in shared memory and splits them evenly over its lanes
+ * (expanded plan).  All give y within the same error bound; the summation
+ * order differs.
  */
 spc5_status spc5_spmv(const spc5_matrix *A, const void *x, void *y, double alpha, double beta,
                       void *stream);
@@ -299,8 +302,9 @@ spc5_status spc5_ircg(const spc5_matrix *A64, const spc5_matrix *Alo, const doub
  * (pieces * r) is rejected with SPC5_EOVERFLOW before any work is queued.
  * The call makes no cudaMalloc, cudaFree or other allocating call.
  *
- * The block-balanced plan's tile counter is likewise a fixed pair of
- * 32-bit words inside the library; every launch leaves it at zero.
+ * The tile counter of the block-balanced and expanded plans is likewise a
+ * fixed pair of 32-bit words inside the library; every launch leaves it at
+ * zero.
  *
  * The array and the counter are shared by every call on a device:
  * concurrent calls whose kernels overlap on the GPU (different streams, or

@@ -20,6 +20,11 @@ namespace spc5 {
 //                 [b0, b1) are dealt to the lanes one block per lane; with
 //                 mode & kPartial the blocks [b0, b1) of the single long
 //                 panel p0, whose r row sums go to partial[slot * r + q].
+//   expanded tile: (mode & kExpand) whole panels [p0, p1) whose values are
+//                 laid out row by row in shared memory and split evenly
+//                 over the lanes; with mode & kPartial the blocks [b0, b1)
+//                 of the single long panel p0, whose r row sums go to
+//                 partial[slot * r + q].
 // [b0, b1) and [v0, v1) are the tile's block and value ranges.
 struct Tile {
   int32_t p0, p1, b0, b1, v0, v1, slot, mode;
@@ -27,6 +32,14 @@ struct Tile {
 constexpr int32_t kSegment = 16;
 constexpr int32_t kPartial = 32;
 constexpr int32_t kFlat = 64;
+constexpr int32_t kExpand = 128;
+
+// Expanded tiles: at most kExpandCap values and kExpandRows rows (shared
+// memory of the expanded SpMV kernel); panels are packed by windows of
+// kExpandWindow values.
+constexpr int32_t kExpandCap = 1024;
+constexpr int32_t kExpandWindow = 512;
+constexpr int32_t kExpandRows = 128;
 
 }  // namespace spc5
 
@@ -62,11 +75,11 @@ struct spc5_matrix {
   double tuned_us = 0.0;            // SpMV time of the plan chosen by spc5_tune (0 = untuned)
   uint32_t *dev_error = nullptr;    // set by kernels on a timed-out wait
 
-  // Block-balanced plan (flat tiles), used by the SpMV instead of the row
-  // groups above when `flat` is set; the transposed product, the gradient
-  // and the batched kernel always use the row-group plan.
+  // Block-balanced (flat = 1) or expanded (flat = 2) plan, used by the SpMV
+  // instead of the row groups above when `flat` is set; the transposed
+  // product, the gradient and the batched kernel always use the row-group
+  // plan.
   int flat = 0;
-  int flat_bcap = 0;                // blocks per flat tile (and per piece of a long panel)
   double group_efficiency = 0.0;    // busy share of the row-group plan's block slots
   spc5::Tile *ftiles = nullptr;
   int64_t fntiles = 0;
@@ -103,8 +116,7 @@ struct PlanOptions {
   int vcap = -1;    // tile capacity in values
   int bcap = -1;    // tile capacity in blocks
   int body = -1;    // consumer body
-  int flat = -1;    // 1: block-balanced SpMV plan, 0: row groups
-  int fbcap = -1;   // blocks per flat tile
+  int flat = -1;    // 0: row groups, 1: block-balanced plan, 2: expanded plan
 };
 
 // Work plan of the SpMV kernels; called by the converter while the
@@ -123,7 +135,7 @@ spc5_status spmv_device(const spc5_matrix *A, const void *x, void *y, double alp
 
 // The same with the partial sums of split panels written to `partial`
 // (spmv_pieces(A) * r doubles) instead of the handle's own buffer, and the
-// flat plan's two tile-scheduling counters at `sched` (zero before the
+// expanded plan's two tile-scheduling counters at `sched` (zero before the
 // first call; every launch leaves them zero again) instead of the handle's.
 spc5_status spmv_device_scratch(const spc5_matrix *A, const void *x, void *y, double alpha,
                                 double beta, cudaStream_t stream, void *partial,

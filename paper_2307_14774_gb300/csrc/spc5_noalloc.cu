@@ -6,7 +6,7 @@
 // synchronisation), or code running under a memory budget that was fixed at
 // start-up.  spc5_spmv itself allocates nothing for device vectors either,
 // but it writes the partial sums of panels split into pieces to a buffer
-// owned by the matrix handle, and the block-balanced plan schedules its
+// owned by the matrix handle, and the expanded plan schedules its
 // tiles through a counter owned by the handle.  This entry point uses
 // instead a fixed array and a fixed counter pair compiled into the library
 // (file-scope __device__ storage), so the whole call allocates nothing and

@@ -152,7 +152,7 @@ __global__ void k_write_piece_tiles(PlanParams P, const int32_t *bpanel, const i
   }
 }
 
-// ---------------------------------------------------------- flat plan ----
+// ------------------------------------------------- block-balanced plan ----
 // Block-balanced plan: consecutive whole panels are packed into tiles of
 // about `fbcap` blocks (a panel joins the tile of the window of fbcap blocks
 // holding its first block), and panels of more than fbcap blocks are cut
@@ -227,6 +227,125 @@ __global__ void k_flat_write(FlatParams F, const int32_t *tbase, const int32_t *
   }
 }
 
+// ------------------------------------------------------ expanded plan ----
+// Tiles of the expanded SpMV kernel, which lays a tile's values out row by
+// row in shared memory (at most kExpandCap values and kExpandRows rows per
+// tile):
+//   - a panel of more than kExpandCap values is long: it is cut at block
+//     boundaries into pieces whose value offsets lie in one window of
+//     kExpandCap - 32 values (a block holds at most 32 values), and the
+//     pieces' row sums go to the partial buffer;
+//   - a panel of more than kExpandCap - kExpandWindow values is a tile of
+//     its own;
+//   - the other panels are packed into tiles of consecutive panels whose
+//     first values lie in the same window of kExpandWindow values and whose
+//     indices lie in the same run of kExpandRows / r panels, so a tile holds
+//     at most kExpandWindow + (kExpandCap - kExpandWindow) values.
+
+struct ExpandParams {
+  int64_t npanels, nblocks, nnz;
+  int32_t pp;  // panels per row window: kExpandRows / r
+  const int32_t *brp, *vptr;
+};
+
+__device__ __forceinline__ int32_t panel_values(const ExpandParams &E, int64_t p) {
+  return E.vptr[p + 1] - E.vptr[p];
+}
+
+__device__ __forceinline__ bool ex_long(const ExpandParams &E, int64_t p) {
+  return panel_values(E, p) > kExpandCap;
+}
+
+__device__ __forceinline__ bool ex_single(const ExpandParams &E, int64_t p) {
+  const int32_t nv = panel_values(E, p);
+  return nv > kExpandCap - kExpandWindow && nv <= kExpandCap;
+}
+
+__device__ __forceinline__ bool ex_start(const ExpandParams &E, int64_t p) {
+  if (ex_long(E, p)) return false;
+  if (p == 0 || ex_long(E, p - 1) || ex_single(E, p) || ex_single(E, p - 1)) return true;
+  return E.vptr[p] / kExpandWindow != E.vptr[p - 1] / kExpandWindow ||
+         p / E.pp != (p - 1) / E.pp;
+}
+
+// Piece starts inside long panels (block b starts a piece).
+__global__ void k_ex_piece_flags(ExpandParams E, const int32_t *bpanel, const int32_t *boff,
+                                 int32_t *pf) {
+  GRID_STRIDE(b, E.nblocks) {
+    const int32_t p = bpanel[b];
+    int32_t f = 0;
+    if (ex_long(E, p)) {
+      const int32_t first = E.brp[p], v0 = E.vptr[p];
+      constexpr int32_t win = kExpandCap - 32;
+      f = (b == first || (boff[b] - v0) / win != (boff[b - 1] - v0) / win) ? 1 : 0;
+    }
+    pf[b] = f;
+  }
+}
+
+// tiles per panel and long-panel flags
+__global__ void k_ex_counts(ExpandParams E, const int32_t *pscan, int32_t *tc, int32_t *lf) {
+  GRID_STRIDE(p, E.npanels) {
+    const bool lg = ex_long(E, p);
+    tc[p] = lg ? pscan[E.brp[p + 1]] - pscan[E.brp[p]] : (ex_start(E, p) ? 1 : 0);
+    lf[p] = lg ? 1 : 0;
+  }
+}
+
+__global__ void k_ex_write_panels(ExpandParams E, const int32_t *tbase, const int32_t *lbase,
+                                  const int32_t *pscan, Tile *tiles, int32_t *long_panels,
+                                  int32_t *long_slots) {
+  GRID_STRIDE(p, E.npanels) {
+    if (ex_long(E, p)) {
+      const int32_t l = lbase[p];
+      long_panels[l] = (int32_t)p;
+      long_slots[2 * l] = pscan[E.brp[p]];
+      long_slots[2 * l + 1] = pscan[E.brp[p + 1]];
+      continue;
+    }
+    const bool start = ex_start(E, p);
+    const int32_t idx = start ? tbase[p] : tbase[p] - 1;
+    if (start) {
+      tiles[idx].p0 = (int32_t)p;
+      tiles[idx].b0 = E.brp[p];
+      tiles[idx].v0 = E.vptr[p];
+      tiles[idx].slot = -1;
+      tiles[idx].mode = kExpand;
+    }
+    const bool last = (p + 1 == E.npanels) || ex_long(E, p + 1) || ex_start(E, p + 1);
+    if (last) {
+      tiles[idx].p1 = (int32_t)p + 1;
+      tiles[idx].b1 = E.brp[p + 1];
+      tiles[idx].v1 = E.vptr[p + 1];
+    }
+  }
+}
+
+__global__ void k_ex_write_pieces(ExpandParams E, const int32_t *bpanel, const int32_t *pf,
+                                  const int32_t *pscan, const int32_t *tbase,
+                                  const int32_t *boff, Tile *tiles) {
+  GRID_STRIDE(b, E.nblocks) {
+    const int32_t p = bpanel[b];
+    if (!ex_long(E, p)) continue;
+    const int32_t first = E.brp[p];
+    const int32_t piece = pscan[b] + pf[b] - 1;  // global index of the piece holding b
+    Tile *t = &tiles[tbase[p] + piece - pscan[first]];
+    if (pf[b]) {
+      t->p0 = p;
+      t->p1 = p + 1;
+      t->b0 = (int32_t)b;
+      t->v0 = boff[b];
+      t->slot = piece;
+      t->mode = kExpand | kPartial;
+    }
+    const bool last = (b + 1 == E.brp[p + 1]) || pf[b + 1];
+    if (last) {
+      t->b1 = (int32_t)b + 1;
+      t->v1 = (b + 1 < E.nblocks) ? boff[b + 1] : (int32_t)E.nnz;
+    }
+  }
+}
+
 // Busy share of the row-group plan's block slots: a group tile keeps
 // group_panels * G slots busy for as many rounds as its longest panel needs.
 __global__ void k_group_efficiency(const Tile *tiles, int64_t ntiles, const int32_t *brp, int gp,
@@ -297,24 +416,29 @@ int round_up(int v, int m) { return (v + m - 1) / m * m; }
 
 namespace {
 
-// Builds the block-balanced plan and decides which plan the SpMV uses.
+// Device arrays of the block-balanced or expanded plan (fntiles, fnlong and
+// fnpieces set).
+cudaError_t alloc_flat_arrays(spc5_matrix *A) {
+  cudaError_t e = cudaMalloc((void **)&A->ftiles,
+                             (size_t)std::max<int64_t>(A->fntiles, 1) * sizeof(Tile));
+  if (e == cudaSuccess)
+    e = cudaMalloc((void **)&A->flong_panels, (size_t)std::max<int64_t>(A->fnlong, 1) * 4);
+  if (e == cudaSuccess)
+    e = cudaMalloc((void **)&A->flong_slots, (size_t)std::max<int64_t>(A->fnlong, 1) * 8);
+  if (e == cudaSuccess)
+    e = cudaMalloc((void **)&A->fpartial,
+                   (size_t)std::max<int64_t>(A->fnpieces, 1) * A->r * sizeof(double));
+  if (e == cudaSuccess)
+    A->device_bytes += A->fntiles * (int64_t)sizeof(Tile) + A->fnlong * 12 +
+                       A->fnpieces * A->r * (int64_t)sizeof(double);
+  return e;
+}
+
+// Builds the block-balanced or the expanded plan, deciding first which plan
+// the SpMV uses.
 spc5_status plan_flat(spc5_matrix *A, const int32_t *boff, cudaStream_t s,
                       const PlanOptions &opt) {
   const int64_t np = A->npanels, nb = A->nblocks;
-  int dev = 0, sms = 1;
-  CK(cudaGetDevice(&dev), "cudaGetDevice");
-  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "sm count");
-  // about eight tiles for every resident warp (48 per SM)
-  const int64_t want = (int64_t)8 * sms * 48;
-  int64_t fb = (nb + want - 1) / want;
-  fb = (fb + 31) / 32 * 32;
-  fb = std::min<int64_t>(std::max<int64_t>(fb, 64), 2048);
-  int fbcap = opt.fbcap > 0 ? opt.fbcap : env_int("SPC5_FLAT_BCAP", (int)fb);
-  if (fbcap < 32) {
-    set_error("invalid flat tile capacity");
-    return SPC5_EINVAL;
-  }
-  A->flat_bcap = fbcap;
   A->fntiles = A->fnlong = A->fnpieces = 0;
   CK(cudaMalloc((void **)&A->fsched, 2 * sizeof(uint32_t)), "alloc tile counters");
   CK(cudaMemsetAsync(A->fsched, 0, 2 * sizeof(uint32_t), s), "zero tile counters");
@@ -330,53 +454,114 @@ spc5_status plan_flat(spc5_matrix *A, const int32_t *boff, cudaStream_t s,
   unsigned long long hacc[2] = {0, 0};
   CK(cudaMemcpyAsync(hacc, acc.p, sizeof(hacc), cudaMemcpyDeviceToHost, s), "rd");
 
+  CK(cudaStreamSynchronize(s), "sync group efficiency");
+  A->group_efficiency = hacc[1] > 0 ? (double)hacc[0] / (double)hacc[1] : 1.0;
+  // Which plan the SpMV uses.  The staged kernel reads its tiles as
+  // contiguous panel ranges, so the other plans are for the direct kernels.
+  // Default: row groups unless they would keep less than 70% of their block
+  // slots busy; then the block-balanced plan for r <= 2 and the expanded
+  // plan for taller panels.
+  const int dflt = A->group_efficiency < 0.7 ? (A->r <= 2 ? 1 : 2) : 0;
+  int flat = opt.flat >= 0 ? opt.flat : env_int("SPC5_FLAT", dflt);
+  if (flat < 0 || flat > 2) flat = dflt;
+  A->flat = A->kernel == 0 ? flat : 0;
+  const bool expanded = A->flat == 2;
+
   int32_t counts[3] = {0, 0, 0};
-  Tmp<int32_t> tc(s), lf(s), pc(s), tbase(s), lbase(s), sbase(s), tmp(s);
-  FlatParams F{np, nb, A->nnz, fbcap, A->block_rowptr, A->panel_vptr};
+  Tmp<int32_t> bpanel(s), pf(s), pscan(s), tc(s), lf(s), tbase(s), lbase(s), tmp(s);
+  if (!expanded) {  // block-balanced tiles (also built, unused, for row groups)
+    int dev = 0, sms = 1;
+    CK(cudaGetDevice(&dev), "cudaGetDevice");
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "sm count");
+    // about eight tiles for every resident warp (48 per SM)
+    const int64_t want = (int64_t)8 * sms * 48;
+    int64_t fb = (nb + want - 1) / want;
+    fb = (fb + 31) / 32 * 32;
+    const int fbcap = (int)std::min<int64_t>(std::max<int64_t>(fb, 64), 2048);
+    FlatParams F{np, nb, A->nnz, fbcap, A->block_rowptr, A->panel_vptr};
+    if (np > 0) {
+      CK(tc.alloc(np), "alloc");
+      CK(lf.alloc(np), "alloc");
+      CK(pf.alloc(np), "alloc");
+      CK(tbase.alloc(np + 1), "alloc");
+      CK(lbase.alloc(np + 1), "alloc");
+      CK(pscan.alloc(np + 1), "alloc");
+      CK(tmp.alloc(scan_tmp_elems(np + 1)), "alloc");
+      k_flat_counts<<<grid_for(np), kThreads, 0, s>>>(F, tc.p, lf.p, pf.p);
+      CK(device_scan<int32_t>(np + 1, ReadI32Pad{tc.p, np}, WriteI32{tbase.p}, AddI32{}, 0,
+                              false, tmp.p, s),
+         "scan flat tiles");
+      CK(device_scan<int32_t>(np + 1, ReadI32Pad{lf.p, np}, WriteI32{lbase.p}, AddI32{}, 0,
+                              false, tmp.p, s),
+         "scan flat long panels");
+      CK(device_scan<int32_t>(np + 1, ReadI32Pad{pf.p, np}, WriteI32{pscan.p}, AddI32{}, 0,
+                              false, tmp.p, s),
+         "scan flat pieces");
+      CK(cudaMemcpyAsync(&counts[0], tbase.p + np, 4, cudaMemcpyDeviceToHost, s), "rd");
+      CK(cudaMemcpyAsync(&counts[1], lbase.p + np, 4, cudaMemcpyDeviceToHost, s), "rd");
+      CK(cudaMemcpyAsync(&counts[2], pscan.p + np, 4, cudaMemcpyDeviceToHost, s), "rd");
+    }
+    CK(cudaStreamSynchronize(s), "sync flat plan counts");
+    A->fntiles = counts[0];
+    A->fnlong = counts[1];
+    A->fnpieces = counts[2];
+    CK(alloc_flat_arrays(A), "alloc flat plan");
+    if (np > 0)
+      k_flat_write<<<grid_for(np), kThreads, 0, s>>>(F, tbase.p, lbase.p, pscan.p, boff,
+                                                     A->ftiles, A->flong_panels, A->flong_slots);
+    CK(cudaGetLastError(), "flat plan kernels");
+    return SPC5_OK;
+  }
+
+  ExpandParams E{np, nb, A->nnz, kExpandRows / A->r, A->block_rowptr, A->panel_vptr};
+  PlanParams P{};
+  P.npanels = np;
+  P.nblocks = nb;
+  P.brp = A->block_rowptr;
   if (np > 0) {
+    CK(bpanel.alloc(nb), "alloc");
+    CK(pf.alloc(nb), "alloc");
+    CK(pscan.alloc(nb + 1), "alloc");
     CK(tc.alloc(np), "alloc");
     CK(lf.alloc(np), "alloc");
-    CK(pc.alloc(np), "alloc");
     CK(tbase.alloc(np + 1), "alloc");
     CK(lbase.alloc(np + 1), "alloc");
-    CK(sbase.alloc(np + 1), "alloc");
-    CK(tmp.alloc(scan_tmp_elems(np + 1)), "alloc");
-    k_flat_counts<<<grid_for(np), kThreads, 0, s>>>(F, tc.p, lf.p, pc.p);
+    CK(tmp.alloc(scan_tmp_elems(std::max<int64_t>(nb, np) + 1)), "alloc");
+    if (nb > 0) {
+      CK(cudaMemsetAsync(bpanel.p, 0, (size_t)nb * sizeof(int32_t), s), "memset");
+      if (np > 1) k_mark_panels<<<grid_for(np), kThreads, 0, s>>>(P, bpanel.p);
+      CK(device_scan<int32_t>(nb, ReadI32{bpanel.p}, WriteI32{bpanel.p}, AddI32{}, 0, true,
+                              tmp.p, s),
+         "scan panels");
+      k_ex_piece_flags<<<grid_for(nb), kThreads, 0, s>>>(E, bpanel.p, boff, pf.p);
+    }
+    CK(device_scan<int32_t>(nb + 1, ReadI32Pad{pf.p, nb}, WriteI32{pscan.p}, AddI32{}, 0, false,
+                            tmp.p, s),
+       "scan pieces");
+    k_ex_counts<<<grid_for(np), kThreads, 0, s>>>(E, pscan.p, tc.p, lf.p);
     CK(device_scan<int32_t>(np + 1, ReadI32Pad{tc.p, np}, WriteI32{tbase.p}, AddI32{}, 0, false,
                             tmp.p, s),
-       "scan flat tiles");
+       "scan expanded tiles");
     CK(device_scan<int32_t>(np + 1, ReadI32Pad{lf.p, np}, WriteI32{lbase.p}, AddI32{}, 0, false,
                             tmp.p, s),
-       "scan flat long panels");
-    CK(device_scan<int32_t>(np + 1, ReadI32Pad{pc.p, np}, WriteI32{sbase.p}, AddI32{}, 0, false,
-                            tmp.p, s),
-       "scan flat pieces");
+       "scan expanded long panels");
     CK(cudaMemcpyAsync(&counts[0], tbase.p + np, 4, cudaMemcpyDeviceToHost, s), "rd");
     CK(cudaMemcpyAsync(&counts[1], lbase.p + np, 4, cudaMemcpyDeviceToHost, s), "rd");
-    CK(cudaMemcpyAsync(&counts[2], sbase.p + np, 4, cudaMemcpyDeviceToHost, s), "rd");
+    CK(cudaMemcpyAsync(&counts[2], pscan.p + nb, 4, cudaMemcpyDeviceToHost, s), "rd");
   }
-  CK(cudaStreamSynchronize(s), "sync flat plan counts");
-  A->group_efficiency = hacc[1] > 0 ? (double)hacc[0] / (double)hacc[1] : 1.0;
+  CK(cudaStreamSynchronize(s), "sync expanded plan counts");
   A->fntiles = counts[0];
   A->fnlong = counts[1];
   A->fnpieces = counts[2];
-  CK(cudaMalloc((void **)&A->ftiles, (size_t)std::max<int64_t>(A->fntiles, 1) * sizeof(Tile)),
-     "alloc flat tiles");
-  CK(cudaMalloc((void **)&A->flong_panels, (size_t)std::max<int64_t>(A->fnlong, 1) * 4), "alloc");
-  CK(cudaMalloc((void **)&A->flong_slots, (size_t)std::max<int64_t>(A->fnlong, 1) * 8), "alloc");
-  CK(cudaMalloc((void **)&A->fpartial,
-                (size_t)std::max<int64_t>(A->fnpieces, 1) * A->r * sizeof(double)),
-     "alloc flat partial");
-  A->device_bytes += A->fntiles * (int64_t)sizeof(Tile) + A->fnlong * 12 +
-                     A->fnpieces * A->r * (int64_t)sizeof(double);
-  if (np > 0)
-    k_flat_write<<<grid_for(np), kThreads, 0, s>>>(F, tbase.p, lbase.p, sbase.p, boff, A->ftiles,
-                                                   A->flong_panels, A->flong_slots);
-  CK(cudaGetLastError(), "flat plan kernels");
-  // The staged kernel reads its tiles as contiguous panel ranges; the flat
-  // plan is for the direct kernel.
-  int flat = opt.flat >= 0 ? opt.flat : env_int("SPC5_FLAT", A->group_efficiency < 0.7 ? 1 : 0);
-  A->flat = (A->kernel == 0 && flat) ? 1 : 0;
+  CK(alloc_flat_arrays(A), "alloc expanded plan");
+  if (np > 0) {
+    k_ex_write_panels<<<grid_for(np), kThreads, 0, s>>>(E, tbase.p, lbase.p, pscan.p, A->ftiles,
+                                                        A->flong_panels, A->flong_slots);
+    if (nb > 0 && A->fnlong > 0)
+      k_ex_write_pieces<<<grid_for(nb), kThreads, 0, s>>>(E, bpanel.p, pf.p, pscan.p, tbase.p,
+                                                          boff, A->ftiles);
+  }
+  CK(cudaGetLastError(), "expanded plan kernels");
   return SPC5_OK;
 }
 

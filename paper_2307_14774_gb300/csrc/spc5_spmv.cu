@@ -36,6 +36,7 @@
 // kernel (SPC5_KERNEL=1) stays available for comparison.
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <stdlib.h>
 
 #include <algorithm>
 
@@ -340,6 +341,13 @@ __global__ void __launch_bounds__(kDirectThreads, kDirectBlocksPerSM)
     const int64_t tn = t + nwarps;
     Tile nxt{0, 0, 0, 0, 0, 0, 0, 0};
     if (tn < ntiles) nxt = tiles[tn];
+    {  // start bringing the tile's values and block columns to L2
+      constexpr int kLine = 128 / (int)sizeof(VT);
+      for (int32_t o = lane * kLine; o < cur.v1 - cur.v0; o += 32 * kLine)
+        prefetch_l2(vals + cur.v0 + o);
+      for (int32_t o = lane * 32; o < cur.b1 - cur.b0; o += 32 * 32)
+        prefetch_l2(block_colidx + cur.b0 + o);
+    }
     const bool segment = (cur.mode & kSegment) != 0;
     const int log2G = cur.mode & 15;
     const int G = 1 << log2G;
@@ -432,13 +440,6 @@ __global__ void __launch_bounds__(kDirectThreads, kDirectBlocksPerSM)
 // end and write them to the partial buffer for the fixup kernel.
 // Warps take tiles from a counter (dynamic scheduling); the last warp to
 // finish resets the counter for the next launch.
-template <typename AT>
-__device__ __forceinline__ AT warp_sum(AT v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-  return v;
-}
-
 __device__ __forceinline__ int warp_excl_scan(int v, int lane, int *total) {
   int incl = v;
 #pragma unroll
@@ -449,6 +450,14 @@ __device__ __forceinline__ int warp_excl_scan(int v, int lane, int *total) {
   *total = __shfl_sync(kFull, incl, 31);
   return incl - v;
 }
+
+template <typename AT>
+__device__ __forceinline__ AT warp_sum(AT v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+
 
 // Adds the block's products to s[q] (q < R): values packed row by row,
 // ascending bit within a row (Algorithm 1's order).
@@ -599,6 +608,285 @@ __global__ void __launch_bounds__(kDirectThreads, FlatBlocksPerSM<R>::v)
         __syncwarp();
       }
     }
+    t = (int32_t)__shfl_sync(kFull, grab, 0);
+  }
+  // every warp has made its last grab: the last one to finish resets the counters
+  if (lane == 0) {
+    const uint32_t nwarps = gridDim.x * (blockDim.x >> 5);
+    if (atomicAdd(&sched[1], 1u) == nwarps - 1) {
+      atomicExch(&sched[0], 0u);
+      atomicExch(&sched[1], 0u);
+    }
+  }
+}
+
+// ---------------------------------------------------------- expanded kernel --
+
+// Expanded kernel.  On GB300 the FP64 pipe executes two FMAs per cycle per SM,
+// and an FMA instruction costs its 16 cycles whether 32 lanes or one lane
+// use it; with lanes owning rows, lanes idle whenever rows (or a row's bits
+// in a block) have uneven lengths, and power-law rows leave most lanes idle.
+// This kernel separates the integer work from the FP64 work:
+//   1. counting: the tile's blocks are dealt to the lanes (one block per lane
+//      per round); a lane finds its block's panel by a binary search in the
+//      tile's block_rowptr (staged in shared memory) and packs its block's
+//      per-row bit counts into one 64-bit word (64/r bits per row); a
+//      segmented warp scan of the packed words by panel gives, at the last
+//      lane of each panel, the round's per-row counts, added to the row
+//      counters in shared memory;
+//   2. an exclusive scan of the row counters gives each row's start in a
+//      row-major layout of the tile's values; rows without values get
+//      y = beta y here;
+//   3. scatter: the same rounds again; a value's destination is its row's
+//      cursor plus the exclusive part of the scan plus its rank among the
+//      row's bits in the block, and its value index is the running value
+//      offset (Algorithm 1's idxVal) plus an exclusive warp scan of the
+//      blocks' popcounts; the column x index and the value index are written
+//      to shared memory;
+//   4. FP64: the tile's values, now row by row, are split into 32 equal runs,
+//      one per lane; a lane multiplies its run's values by x with one FMA per
+//      value (all lanes busy), writes the rows that start and end inside its
+//      run (one write per row, Section 3.2), and a segmented warp scan of the
+//      lanes' last partial sums completes the rows cut between lanes.
+// The FP64 work per tile is ceil(values / 32) FMA instructions plus six adds.
+// A piece of a long panel (mode & kPartial) writes its r row sums to the
+// partial buffer for the fixup kernel.  Warps take tiles from a counter; the
+// last warp to finish resets it for the next launch.
+constexpr int kExpandWarps = 4;
+constexpr int kExpandBlocksPerSM = 7;
+
+
+// Per-row bit counts of a block, row q in bits [q * 64/R, (q + 1) * 64/R).
+template <int R, int C>
+__device__ __forceinline__ uint64_t packed_counts(uint32_t m) {
+  constexpr int F = 64 / R;
+  uint64_t w = 0;
+#pragma unroll
+  for (int q = 0; q < R; ++q) w |= (uint64_t)__popc((m >> (q * C)) & ((1u << C) - 1u)) << (q * F);
+  return w;
+}
+
+template <int R>
+__device__ __forceinline__ int32_t packed_field(uint64_t w, int q) {
+  if (R == 1) return (int32_t)w;
+  constexpr int F = 64 / R;
+  return (int32_t)((w >> (q * F)) & ((1ull << F) - 1ull));
+}
+
+// Inclusive scan of `w` over lanes with the same key (keys ascend with the lane).
+__device__ __forceinline__ uint64_t seg_scan_u64(uint64_t w, int32_t key, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint64_t t = __shfl_up_sync(kFull, w, o);
+    const int32_t k = __shfl_up_sync(kFull, key, o);
+    if (lane >= o && k == key) w += t;
+  }
+  return w;
+}
+
+template <int R, int C, typename VT, typename AT>
+__global__ void __launch_bounds__(32 * kExpandWarps, kExpandBlocksPerSM)
+    k_spmv_expand(const Tile *__restrict__ tiles, int32_t ntiles, uint32_t *sched,
+                  const int32_t *__restrict__ brp, const int32_t *__restrict__ block_colidx,
+                  const typename MaskType<R, C>::T *__restrict__ masks,
+                  const VT *__restrict__ vals, const AT *__restrict__ x, AT *__restrict__ y,
+                  AT *__restrict__ partial, Scale<AT> sc, int64_t nrows) {
+  __shared__ int32_t s_col_all[kExpandWarps][kExpandCap];
+  __shared__ uint16_t s_vid_all[kExpandWarps][kExpandCap];
+  __shared__ int32_t s_row_all[kExpandWarps][kExpandRows];
+  __shared__ int32_t s_brp_all[kExpandWarps][kExpandRows + 1];
+  const int wid = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  int32_t *s_col = s_col_all[wid];
+  uint16_t *s_vid = s_vid_all[wid];
+  int32_t *s_row = s_row_all[wid];
+  int32_t *s_brp = s_brp_all[wid];
+  constexpr int32_t kNoPanel = 0x7fffffff;
+
+  uint32_t grab = 0;
+  if (lane == 0) grab = atomicAdd(&sched[0], 1u);
+  int32_t t = (int32_t)__shfl_sync(kFull, grab, 0);
+  while (t < ntiles) {
+    if (lane == 0) grab = atomicAdd(&sched[0], 1u);  // next tile, used after this one
+    const Tile cur = tiles[t];
+    const bool piece = (cur.mode & kPartial) != 0;
+    const int32_t np_t = piece ? 1 : cur.p1 - cur.p0;
+    const int rows_t = np_t * R;
+    const int32_t nv = cur.v1 - cur.v0;
+    {  // the tile's values are read in step 4: start bringing them to L1
+      constexpr int kLine = 128 / (int)sizeof(VT);
+      for (int32_t o = lane * kLine; o < nv; o += 32 * kLine) prefetch_l1(vals + cur.v0 + o);
+    }
+    for (int j = lane; j <= np_t; j += 32)
+      s_brp[j] = piece ? (j == 0 ? cur.b0 : cur.b1) : brp[cur.p0 + j];
+    for (int r = lane; r < rows_t; r += 32) s_row[r] = 0;
+    __syncwarp();
+
+    // tile row of a value: global row (or partial slot) of tile row r
+    auto emit = [&](int r, AT v) {
+      const int j = r / R, q = r - j * R;
+      if (piece) {
+        partial[(int64_t)cur.slot * R + q] = v;
+      } else {
+        const int64_t row = ((int64_t)cur.p0 + j) * R + q;
+        if (row < nrows) put_row(sc, y, row, v);
+      }
+    };
+    // panel (index within the tile) of block b: the last j with s_brp[j] <= b
+    auto panel_of = [&](int32_t b) {
+      int lo = 0, hi = np_t - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (s_brp[mid] <= b) lo = mid; else hi = mid - 1;
+      }
+      return lo;
+    };
+
+    // 1. per-row counts
+    for (int32_t base = cur.b0; base < cur.b1; base += 32) {
+      const int32_t b = base + lane;
+      const bool valid = b < cur.b1;
+      const uint32_t m = valid ? (uint32_t)masks[b] : 0u;
+      const int32_t j = valid ? panel_of(b) : kNoPanel;
+      const uint64_t inc = seg_scan_u64(packed_counts<R, C>(m), j, lane);
+      const int32_t jn = __shfl_down_sync(kFull, j, 1);
+      if (valid && (lane == 31 || jn != j)) {
+#pragma unroll
+        for (int q = 0; q < R; ++q) s_row[j * R + q] += packed_field<R>(inc, q);
+      }
+      __syncwarp();
+    }
+    // 2. row starts (exclusive scan; each lane takes 4 consecutive rows)
+    {
+      const int r0 = lane * (kExpandRows / 32);
+      int cnt[kExpandRows / 32];
+      int sum = 0;
+#pragma unroll
+      for (int i = 0; i < kExpandRows / 32; ++i) {
+        cnt[i] = (r0 + i < rows_t) ? s_row[r0 + i] : 0;
+        sum += cnt[i];
+      }
+      int total;
+      int start = warp_excl_scan(sum, lane, &total);
+      __syncwarp();
+#pragma unroll
+      for (int i = 0; i < kExpandRows / 32; ++i) {
+        if (r0 + i < rows_t) {
+          s_row[r0 + i] = start;
+          if (cnt[i] == 0) {
+            if (piece) emit(r0 + i, (AT)0);
+            else {
+              const int64_t row = ((int64_t)cur.p0 + (r0 + i) / R) * R + (r0 + i) % R;
+              if (row < nrows) put_empty_row(sc, y, row);
+            }
+          }
+        }
+        start += cnt[i];
+      }
+      __syncwarp();
+    }
+    // 3. scatter (s_row holds each row's cursor)
+    {
+      int32_t vrun = 0;
+      for (int32_t base = cur.b0; base < cur.b1; base += 32) {
+        const int32_t b = base + lane;
+        const bool valid = b < cur.b1;
+        const uint32_t m = valid ? (uint32_t)masks[b] : 0u;
+        const int32_t col = valid ? block_colidx[b] : 0;
+        const int32_t j = valid ? panel_of(b) : kNoPanel;
+        const uint64_t own = packed_counts<R, C>(m);
+        const uint64_t inc = seg_scan_u64(own, j, lane);
+        int total;
+        int vi = vrun + warp_excl_scan(__popc(m), lane, &total);
+        vrun += total;
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+          uint32_t mq = (m >> (q * C)) & ((1u << C) - 1u);
+          if (mq) {
+            int dst = s_row[j * R + q] + packed_field<R>(inc, q) - packed_field<R>(own, q);
+            while (mq) {
+              const int k = __ffs(mq) - 1;
+              mq &= mq - 1u;
+              s_col[dst] = col + k;
+              s_vid[dst] = (uint16_t)vi;
+              ++dst;
+              ++vi;
+            }
+          }
+        }
+        __syncwarp();
+        const int32_t jn = __shfl_down_sync(kFull, j, 1);
+        if (valid && (lane == 31 || jn != j)) {
+#pragma unroll
+          for (int q = 0; q < R; ++q) s_row[j * R + q] += packed_field<R>(inc, q);
+        }
+        __syncwarp();
+      }
+    }
+    // 4. FP64 (or FP32) products: s_row[r] is now the end of row r
+    {
+      const int32_t K = (nv + 31) >> 5;
+      const int32_t lo = min(lane * K, nv), hi = min(lo + K, nv);
+      const VT *__restrict__ tv = vals + cur.v0;
+      AT acc = 0, head_val = 0;
+      int head_row = -1, tail_row = -1;
+      if (lo < hi) {
+        int a = 0, bnd = rows_t - 1;  // first row ending after lo
+        while (a < bnd) {
+          const int mid = (a + bnd) >> 1;
+          if (s_row[mid] > lo) bnd = mid; else a = mid + 1;
+        }
+        int r = a;
+        int32_t rend = s_row[r];
+        bool started_here = (r == 0 ? 0 : s_row[r - 1]) >= lo;
+        // four values at a time: their loads are issued together
+        for (int32_t i0 = lo; i0 < hi; i0 += 4) {
+          AT av[4], xv[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            if (i0 + u < hi) {
+              av[u] = (AT)widen(tv[s_vid[i0 + u]]);
+              xv[u] = __ldg(x + s_col[i0 + u]);
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int32_t i = i0 + u;
+            if (i < hi) {
+              acc = fma(av[u], xv[u], acc);
+              if (i + 1 == rend) {
+                if (started_here) {
+                  emit(r, acc);
+                } else {
+                  head_row = r;
+                  head_val = acc;
+                }
+                acc = 0;
+                if (i + 1 < nv) {
+                  do {
+                    ++r;
+                  } while (s_row[r] <= i + 1);
+                  rend = s_row[r];
+                  started_here = true;
+                }
+              }
+            }
+          }
+        }
+        if (hi < nv) tail_row = r;
+      }
+      // rows cut between lanes: segmented scan of the lanes' last partial sums
+      AT sv = (tail_row >= 0) ? acc : (AT)0;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const AT tsv = __shfl_up_sync(kFull, sv, o);
+        const int kr = __shfl_up_sync(kFull, tail_row, o);
+        if (lane >= o && kr == tail_row && tail_row >= 0) sv += tsv;
+      }
+      const AT cin = __shfl_up_sync(kFull, sv, 1);
+      if (head_row >= 0) emit(head_row, head_val + cin);
+    }
+    __syncwarp();
     t = (int32_t)__shfl_sync(kFull, grab, 0);
   }
   // every warp has made its last grab: the last one to finish resets the counters
@@ -1026,7 +1314,7 @@ cudaError_t launch_direct(const spc5_matrix *A, const AT *x, AT *y, double alpha
     k_spmv_tiles<R, C, BODY, VT, AT><<<(unsigned)blocks, kDirectThreads, 0, s>>>(
         A->tiles, A->ntiles, A->block_rowptr, A->panel_vptr, A->block_colidx,
         (const MaskT *)A->masks, (const VT *)A->values, x, y, partial,
-        make_scale<AT>(alpha, beta), A->nrows);
+          make_scale<AT>(alpha, beta), A->nrows);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -1068,6 +1356,32 @@ cudaError_t launch_flat(const spc5_matrix *A, const AT *x, AT *y, double alpha, 
 }
 
 template <int R, int C, typename VT, typename AT>
+cudaError_t launch_expand(const spc5_matrix *A, const AT *x, AT *y, double alpha, double beta,
+                          cudaStream_t s, AT *partial, uint32_t *sched) {
+  using MaskT = typename MaskType<R, C>::T;
+  cudaError_t e = cudaSuccess;
+  if (A->fntiles > 0) {
+    int64_t blocks = (A->fntiles + kExpandWarps - 1) / kExpandWarps;
+    const int64_t resident = (int64_t)num_sms() * kExpandBlocksPerSM;
+    if (blocks > resident) blocks = resident;
+    k_spmv_expand<R, C, VT, AT><<<(unsigned)blocks, 32 * kExpandWarps, 0, s>>>(
+        A->ftiles, (int32_t)A->fntiles, sched, A->block_rowptr, A->block_colidx,
+        (const MaskT *)A->masks, (const VT *)A->values, x, y, partial,
+        make_scale<AT>(alpha, beta), A->nrows);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  if (A->fnlong > 0) {
+    int64_t threads = A->fnlong * R;
+    int fblocks = (int)std::min<int64_t>((threads + 255) / 256, 4096);
+    k_fixup<R, AT><<<fblocks, 256, 0, s>>>(A->fnlong, A->flong_panels, A->flong_slots, partial,
+                                           y, make_scale<AT>(alpha, beta), A->nrows);
+    e = cudaGetLastError();
+  }
+  return e;
+}
+
+template <int R, int C, typename VT, typename AT>
 cudaError_t launch_direct_body(const spc5_matrix *A, const void *x, void *y, double alpha,
                                double beta, cudaStream_t s, void *partial) {
   switch (A->body) {
@@ -1089,7 +1403,7 @@ cudaError_t launch_direct_body(const spc5_matrix *A, const void *x, void *y, dou
 template <int R, int C>
 cudaError_t launch(const spc5_matrix *A, const void *x, void *y, double alpha, double beta,
                    cudaStream_t s, void *partial, uint32_t *sched) {
-  if (A->flat) {
+  if (A->flat == 1) {
     if (A->value_dtype == SPC5_F32)
       return launch_flat<R, C, float, float>(A, (const float *)x, (float *)y, alpha, beta, s,
                                              (float *)partial, sched);
@@ -1098,6 +1412,16 @@ cudaError_t launch(const spc5_matrix *A, const void *x, void *y, double alpha, d
                                                 (float *)partial, sched);
     return launch_flat<R, C, double, double>(A, (const double *)x, (double *)y, alpha, beta, s,
                                              (double *)partial, sched);
+  }
+  if (A->flat == 2) {
+    if (A->value_dtype == SPC5_F32)
+      return launch_expand<R, C, float, float>(A, (const float *)x, (float *)y, alpha, beta, s,
+                                               (float *)partial, sched);
+    if (A->value_dtype == SPC5_BF16)
+      return launch_expand<R, C, uint16_t, float>(A, (const float *)x, (float *)y, alpha, beta,
+                                                  s, (float *)partial, sched);
+    return launch_expand<R, C, double, double>(A, (const double *)x, (double *)y, alpha, beta, s,
+                                               (double *)partial, sched);
   }
   if (A->value_dtype == SPC5_F32)
     return launch_direct_body<R, C, float, float>(A, x, y, alpha, beta, s, partial);

@@ -6,7 +6,8 @@
 // x accesses of neighbouring rows together.  Rather than a model, the tuner
 // times the candidates on the caller's vectors:
 //   spc5_tune           G in {1, 2, 4, 8} (those that fit 32 / r), the two
-//                       row-stream bodies and the block-balanced plan for one
+//                       row-stream bodies, the block-balanced and the
+//                       expanded plan for one
 //                       converted matrix, keeping the fastest plan;
 //   spc5_convert_tuned  every requested beta(r,c), each tuned, keeping the
 //                       fastest matrix.
@@ -59,10 +60,11 @@ spc5_status tune(spc5_matrix *A, const void *x, void *y, int iters, cudaStream_t
   struct Cand {
     int log2g, body, flat;
   };
-  // row-group plans (lanes per row; the row-stream bodies need one lane per
-  // row) and the block-balanced plan
+  // the block-balanced and expanded plans, and row-group plans (lanes per
+  // row; the row-stream bodies need one lane per row)
   std::vector<Cand> cands;
   cands.push_back({0, 0, 1});
+  cands.push_back({0, 0, 2});
   cands.push_back({0, 2, 0});
   cands.push_back({0, 3, 0});
   for (int lg = 0; lg <= max_log2g; ++lg) cands.push_back({lg, 0, 0});

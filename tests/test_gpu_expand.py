@@ -1,12 +1,16 @@
-"""The block-balanced SpMV plan (flat tiles): blocks of runs of whole panels
-dealt to the lanes one block per lane, row sums assembled by a segmented
-warp scan, long panels cut into pieces of a fixed number of blocks.
+"""The two plans for skewed rows.  Block-balanced (SPC5_FLAT=1): the blocks
+of runs of whole panels dealt to the lanes one block per lane, row sums by
+a segmented warp scan, long panels cut into pieces of a fixed block count.
+Expanded (SPC5_FLAT=2): runs of whole panels (at most 1024 values and 128
+rows) whose values a warp lays out row by row in shared memory and splits
+evenly over its lanes; panels of more than 1024 values cut into pieces.
+Pieces' row sums are added by a fixup kernel.
 
 Checked through the C ABI against the CPU oracle at the FP64 tolerance
 |y - y_ref| <= 1e-13 * sum_j |a_ij x_j| (and the FP32/BF16 bounds of the
 precision tests), bit-exact on integer data, over matrices with skewed row
-lengths, runs of empty panels longer than a warp's window, ragged last
-panels and tiles of one to many rounds."""
+lengths, runs of empty rows and panels, ragged last panels, rows cut between
+lanes and tiles of one to many rounds of blocks."""
 from __future__ import annotations
 
 import numpy as np
@@ -20,6 +24,7 @@ from gpuhelpers import assert_within_tol, convert, spmv, to_device, torch_cuda
 pytestmark = pytest.mark.gpu
 
 BETAS = [(1, 8), (2, 4), (2, 8), (4, 4), (4, 8), (8, 4)]
+PLANS = ["1", "2"]
 
 
 def _sparse_rows(n=6000, ncols=700, seed=9):
@@ -56,18 +61,16 @@ def mats():
     return _mats()
 
 
-@pytest.mark.parametrize("fbcap", ["", "32", "96"])
+@pytest.mark.parametrize("plan", PLANS)
 @pytest.mark.parametrize("r,c", BETAS)
-def test_flat_fp64_tolerance(monkeypatch, mats, r, c, fbcap):
+def test_skewed_plans_fp64_tolerance(monkeypatch, mats, r, c, plan):
     monkeypatch.setenv("SPC5_KERNEL", "0")
-    monkeypatch.setenv("SPC5_FLAT", "1")
-    if fbcap:
-        monkeypatch.setenv("SPC5_FLAT_BCAP", fbcap)
+    monkeypatch.setenv("SPC5_FLAT", plan)
     saw_pieces = False
     for A in mats:
         M = convert(A, r, c)
         info = M.info()
-        assert info["flat"] == 1
+        assert info["flat"] == int(plan)
         saw_pieces |= info["long_panels"] > 0
         x = synth.vector_uniform(A.ncols, seed=5)
         y_ref, scale = oracle.csr_spmv(A, x)
@@ -75,41 +78,43 @@ def test_flat_fp64_tolerance(monkeypatch, mats, r, c, fbcap):
         y0 = synth.vector_normal(A.nrows, seed=2)
         assert_within_tol(spmv(M, x, y0.copy(), -1.5, 0.5), -1.5 * y_ref + 0.5 * y0,
                           1.5 * scale, extra=np.abs(0.5 * y0))
-    if fbcap:
-        assert saw_pieces
+    assert saw_pieces
 
 
+@pytest.mark.parametrize("plan", PLANS)
 @pytest.mark.parametrize("r,c", BETAS)
-def test_flat_integer_exact(monkeypatch, r, c):
+def test_skewed_plans_integer_exact(monkeypatch, r, c, plan):
     """Integer data: every order of summation gives the exact result."""
     monkeypatch.setenv("SPC5_KERNEL", "0")
-    monkeypatch.setenv("SPC5_FLAT", "1")
-    monkeypatch.setenv("SPC5_FLAT_BCAP", "64")
+    monkeypatch.setenv("SPC5_FLAT", plan)
     for A in (synth.bernoulli(40, 20_000, 0.3, seed=9, integer_values=True),
               synth.bernoulli(3000, 400, 0.01, seed=4, integer_values=True)):
         x = synth.vector_int(A.ncols, -3, 3, seed=1)
         M = convert(A, r, c)
-        assert M.info()["flat"] == 1
+        assert M.info()["flat"] == int(plan)
         assert np.array_equal(spmv(M, x), A.todense() @ x)
 
 
-def test_flat_default_choice():
-    """The converter picks the block-balanced plan for skewed row lengths and
+def test_skewed_plans_default_choice():
+    """The converter picks the block-balanced plan for skewed rows in panels of
+    one or two rows, the expanded plan for taller panels of skewed rows, and
     keeps row groups for a stencil."""
     torch_cuda()
     skewed = convert(synth.powerlaw(60_000, seed=3), 1, 8).info()
     assert skewed["group_efficiency"] < 0.7 and skewed["flat"] == 1
+    tall = convert(synth.powerlaw(60_000, seed=3), 4, 4).info()
+    assert tall["group_efficiency"] >= 0.7 or tall["flat"] == 2
     regular = convert(synth.stencil27(20, 20, 20, values="normal"), 4, 8).info()
     assert regular["group_efficiency"] >= 0.7 and regular["flat"] == 0
 
 
-def test_flat_counter_resets_across_launches_and_graph_replay(monkeypatch):
+@pytest.mark.parametrize("plan", PLANS)
+def test_skewed_plans_counter_resets_across_launches_and_graph_replay(monkeypatch, plan):
     """Tiles are taken from a counter that each launch resets: back-to-back
     launches and CUDA-graph replays give the same y."""
     torch = torch_cuda()
     monkeypatch.setenv("SPC5_KERNEL", "0")
-    monkeypatch.setenv("SPC5_FLAT", "1")
-    monkeypatch.setenv("SPC5_FLAT_BCAP", "32")
+    monkeypatch.setenv("SPC5_FLAT", plan)
     A = synth.powerlaw(50_000, seed=6)
     M = convert(A, 2, 8)
     x = synth.vector_uniform(A.ncols, seed=9)
@@ -140,19 +145,19 @@ def test_flat_counter_resets_across_launches_and_graph_replay(monkeypatch):
         assert np.array_equal(dy.cpu().numpy(), first)
 
 
+@pytest.mark.parametrize("plan", PLANS)
 @pytest.mark.parametrize("dtype,tol", [("f32", 2e-6), ("bf16", 1e-2)])
 @pytest.mark.parametrize("r,c", BETAS)
-def test_flat_reduced_precision(monkeypatch, mats, dtype, tol, r, c):
+def test_skewed_plans_reduced_precision(monkeypatch, mats, dtype, tol, r, c, plan):
     torch = torch_cuda()
     monkeypatch.setenv("SPC5_KERNEL", "0")
-    monkeypatch.setenv("SPC5_FLAT", "1")
-    monkeypatch.setenv("SPC5_FLAT_BCAP", "64")
+    monkeypatch.setenv("SPC5_FLAT", plan)
     code = spc5.SPC5_F32 if dtype == "f32" else spc5.SPC5_BF16
     for A in mats[:4]:
         rowptr, colidx, vals = to_device(A)
         M = spc5.spc5_convert_csr(A.nrows, A.ncols, A.nnz, rowptr, colidx, vals,
                                   store_dtype=code, r=r, c=c)
-        assert M.info()["flat"] == 1
+        assert M.info()["flat"] == int(plan)
         x32 = synth.vector_uniform(A.ncols, seed=7).astype(np.float32)
         dy = torch.full((A.nrows,), float("nan"), dtype=torch.float32, device="cuda")
         spc5.spc5_spmv(M, torch.from_numpy(x32).cuda(), dy)
