@@ -246,7 +246,7 @@ def build_cases(names, torch, spc5, synth, log, betas, tune=True):
 PRECISION_TOL = {"f32": 2e-6, "bf16": 1e-2}  # |y - y_fp64| <= tol * sum_j |a_ij x_j|
 
 
-def precision_section(hosts, torch, spc5, stream, hbm, case_rows, log, reps=10):
+def precision_section(hosts, torch, spc5, stream, hbm, case_rows, log, reps=10, tune=True):
     """FP32 and BF16 value storage (FP32 x, y, accumulation) on the 27-point
     and FEM matrices, every beta: time per SpMV, HBM fraction, speed-up over
     the FP64 case of the main step, and the largest error relative to the
@@ -272,16 +272,20 @@ def precision_section(hosts, torch, spc5, stream, hbm, case_rows, log, reps=10):
         spc5.spc5_spmv(Mabs, xabs, sc, 1.0, 0.0, stream)
         del M64, Mabs
         y32 = torch.empty(A.nrows, dtype=torch.float32, device="cuda")
+        flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device="cuda")
         for r, c in BETAS:
             for dt, code in (("f32", spc5.SPC5_F32), ("bf16", spc5.SPC5_BF16)):
                 M = spc5.spc5_convert_csr(A.nrows, A.ncols, A.nnz, *dev, store_dtype=code, r=r,
                                           c=c)
+                if tune:
+                    spc5.spc5_tune(M, x32, y32, iters=3)
                 info = M.info()
                 for _ in range(3):
                     spc5.spc5_spmv(M, x32, y32, 1.0, 0.0, stream)
                 evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                        for _ in range(reps)]
                 for e0, e1 in evs:
+                    flush.zero_()  # the reduced-precision matrices can fit in L2
                     e0.record(stream)
                     spc5.spc5_spmv(M, x32, y32, 1.0, 0.0, stream)
                     e1.record(stream)
@@ -300,9 +304,11 @@ def precision_section(hosts, torch, spc5, stream, hbm, case_rows, log, reps=10):
                              "gbs": round(b / (us * 1e-6) / 1e9, 1),
                              "frac": round(b / (us * 1e-6) / 1e9 / hbm, 3),
                              "speedup_vs_fp64": round(ref / us, 2) if ref else None,
-                             "tol": PRECISION_TOL[dt], "max_err_over_tol": round(ratio, 4)})
+                             "tol": PRECISION_TOL[dt], "max_err_over_tol": round(ratio, 4),
+                             "plan": ({1: "blocks", 2: "expanded"}.get(info["flat"])
+                                      or f"rows/G{info['lanes_per_row']}")})
                 del M
-        del dev, dabs
+        del dev, dabs, flush
         torch.cuda.synchronize()
         log(f"precision rows for {name} done")
     return rows
@@ -600,7 +606,8 @@ def run_native(args):
         result["clocks"] = clocks
 
     if not args.no_precision and rank == 0:
-        prec = precision_section(hosts, torch, spc5, stream, hbm, case_rows, log)
+        prec = precision_section(hosts, torch, spc5, stream, hbm, case_rows, log,
+                                 tune=not args.no_tune)
         result["precision"] = {
             "note": "FP32/BF16 value storage, FP32 x/y/accumulation; error vs the FP64 product "
                     "of the same matrix, relative to tol * sum_j |a_ij x_j|",

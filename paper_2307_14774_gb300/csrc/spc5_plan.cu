@@ -657,10 +657,11 @@ spc5_status plan_tiles(spc5_matrix *A, const uint32_t *mask32, const int32_t *bo
   A->consumers = consumers;
   A->stage_bytes = stage;
   // direct kernel bodies: 0 per-block set-bit loop, 1 per-block predicated
-  // loop over the c bits, 2 row stream across blocks, 3 queued row stream
-  // (2 and 3 on row-group tiles with one lane per row; other tiles use body 0)
+  // loop over the c bits, 2 row stream across blocks, 3 queued row stream,
+  // 4 four-block rounds (2 to 4 on row-group tiles with one lane per row;
+  // other tiles use body 0)
   A->body = staged ? body
-                   : std::min(std::max(opt.body >= 0 ? opt.body : env_int("SPC5_BODY", 0), 0), 3);
+                   : std::min(std::max(opt.body >= 0 ? opt.body : env_int("SPC5_BODY", 0), 0), 4);
 
   if (np == 0) return SPC5_OK;
   PlanParams P{np, nb, gp, vcap, bcap, vcap - 32, log2g, log2g_segment,

@@ -322,8 +322,68 @@ __device__ __forceinline__ AT row_queue(const MaskT *__restrict__ masks,
   return acc;
 }
 
+// Four-block rounds (one lane per row): all lanes of the warp take their
+// panel's next four blocks together, pack their row's bits of the four blocks
+// into one word, and loop as many times as the largest bit count in the warp
+// (one FMA per trip, predicated on the lane having a bit left); each trip
+// selects its block's column and value index with branch-free selects.  The
+// warp never diverges, the block traversal costs a few instructions per four
+// blocks, and summing a row's bits over four blocks evens out the lanes'
+// trip counts (the FMA instructions' idle lanes).
+template <int R, int C, typename VT, typename AT, typename MaskT>
+__device__ __forceinline__ AT row_rounds4(const MaskT *__restrict__ masks,
+                                          const int32_t *__restrict__ block_colidx,
+                                          const VT *__restrict__ vals, const AT *__restrict__ x,
+                                          int32_t bl, int32_t nbp, int32_t v, int q) {
+  constexpr int LOG2C = C == 8 ? 3 : 2;
+  const int qc = q * C;
+  const uint32_t row_low = (1u << qc) - 1u;
+  const uint32_t cmask = (1u << C) - 1u;
+  AT acc = 0;
+  const int32_t maxnb = __reduce_max_sync(kFull, nbp);
+  for (int32_t b = 0; b < maxnb; b += 4) {
+    uint32_t m[4];
+    int32_t cc[4], o[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const bool ok = b + i < nbp;
+      m[i] = ok ? (uint32_t)masks[bl + b + i] : 0u;
+      cc[i] = ok ? block_colidx[bl + b + i] : 0;
+    }
+    uint32_t w = 0u;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      o[i] = v + __popc(m[i] & row_low);
+      v += __popc(m[i]);
+      w |= ((m[i] >> qc) & cmask) << (i * C);
+    }
+    const int trips = __reduce_max_sync(kFull, __popc(w));
+    int slot = -1;
+    int32_t off = 0, col = 0;
+    for (int it = 0; it < trips; ++it) {
+      if (w) {
+        const int k = __ffs(w) - 1;
+        const int i = k >> LOG2C;
+        const bool fresh = i != slot;
+        off = fresh ? sel4(i, o[0], o[1], o[2], o[3]) : off;
+        col = fresh ? sel4(i, cc[0], cc[1], cc[2], cc[3]) : col;
+        slot = i;
+        acc = fma((AT)widen(vals[off]), __ldg(x + col + (k & (C - 1))), acc);
+        ++off;
+        w &= w - 1u;
+      }
+    }
+  }
+  return acc;
+}
+
+template <int BODY>
+struct TileBlocksPerSM {  // the four-block body holds more registers
+  static constexpr int v = BODY == 4 ? 5 : kDirectBlocksPerSM;
+};
+
 template <int R, int C, int BODY, typename VT, typename AT>
-__global__ void __launch_bounds__(kDirectThreads, kDirectBlocksPerSM)
+__global__ void __launch_bounds__(kDirectThreads, TileBlocksPerSM<BODY>::v)
     k_spmv_tiles(const Tile *__restrict__ tiles, int64_t ntiles,
                  const int32_t *__restrict__ block_rowptr, const int32_t *__restrict__ panel_vptr,
                  const int32_t *__restrict__ block_colidx,
@@ -341,12 +401,13 @@ __global__ void __launch_bounds__(kDirectThreads, kDirectBlocksPerSM)
     const int64_t tn = t + nwarps;
     Tile nxt{0, 0, 0, 0, 0, 0, 0, 0};
     if (tn < ntiles) nxt = tiles[tn];
-    {  // start bringing the tile's values and block columns to L2
+    {  // start bringing the first 2 KB of the tile's values and 1 KB of its
+       // block columns to L2: the tile's first rounds wait on them (more
+       // would evict x from L2 on large tiles)
       constexpr int kLine = 128 / (int)sizeof(VT);
-      for (int32_t o = lane * kLine; o < cur.v1 - cur.v0; o += 32 * kLine)
-        prefetch_l2(vals + cur.v0 + o);
-      for (int32_t o = lane * 32; o < cur.b1 - cur.b0; o += 32 * 32)
-        prefetch_l2(block_colidx + cur.b0 + o);
+      if (lane < 16 && lane * kLine < cur.v1 - cur.v0) prefetch_l2(vals + cur.v0 + lane * kLine);
+      if (lane >= 16 && lane < 24 && (lane - 16) * 32 < cur.b1 - cur.b0)
+        prefetch_l2(block_colidx + cur.b0 + (lane - 16) * 32);
     }
     const bool segment = (cur.mode & kSegment) != 0;
     const int log2G = cur.mode & 15;
@@ -375,6 +436,8 @@ __global__ void __launch_bounds__(kDirectThreads, kDirectBlocksPerSM)
       acc = row_stream<R, C>(masks, block_colidx, vals, x, bl, nbp, v, q);
     } else if (BODY == 3 && G == 1) {
       acc = row_queue<R, C>(masks, block_colidx, vals, x, bl, nbp, v, q);
+    } else if (BODY == 4 && G == 1) {
+      acc = row_rounds4<R, C>(masks, block_colidx, vals, x, bl, nbp, v, q);
     } else {
     constexpr bool UNROLL = BODY == 1;
     const int32_t maxnb = __reduce_max_sync(kFull, nbp);
@@ -1309,7 +1372,7 @@ cudaError_t launch_direct(const spc5_matrix *A, const AT *x, AT *y, double alpha
   if (A->ntiles > 0) {
     const int warps_per_block = kDirectThreads / 32;
     int64_t blocks = (A->ntiles + warps_per_block - 1) / warps_per_block;
-    const int64_t resident = (int64_t)num_sms() * kDirectBlocksPerSM;
+    const int64_t resident = (int64_t)num_sms() * TileBlocksPerSM<BODY>::v;
     if (blocks > resident) blocks = resident;
     k_spmv_tiles<R, C, BODY, VT, AT><<<(unsigned)blocks, kDirectThreads, 0, s>>>(
         A->tiles, A->ntiles, A->block_rowptr, A->panel_vptr, A->block_colidx,
@@ -1393,6 +1456,9 @@ cudaError_t launch_direct_body(const spc5_matrix *A, const void *x, void *y, dou
                                             (AT *)partial);
     case 3:
       return launch_direct<R, C, 3, VT, AT>(A, (const AT *)x, (AT *)y, alpha, beta, s,
+                                            (AT *)partial);
+    case 4:
+      return launch_direct<R, C, 4, VT, AT>(A, (const AT *)x, (AT *)y, alpha, beta, s,
                                             (AT *)partial);
     default:
       return launch_direct<R, C, 0, VT, AT>(A, (const AT *)x, (AT *)y, alpha, beta, s,

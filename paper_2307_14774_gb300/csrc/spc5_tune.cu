@@ -5,8 +5,8 @@
 // lanes per row shorten each warp's serial block loop, fewer lanes keep the
 // x accesses of neighbouring rows together.  Rather than a model, the tuner
 // times the candidates on the caller's vectors:
-//   spc5_tune           G in {1, 2, 4, 8} (those that fit 32 / r), the two
-//                       row-stream bodies, the block-balanced and the
+//   spc5_tune           G in {1, 2, 4, 8} (those that fit 32 / r), the
+//                       one-lane-per-row bodies, the block-balanced and the
 //                       expanded plan for one
 //                       converted matrix, keeping the fastest plan;
 //   spc5_convert_tuned  every requested beta(r,c), each tuned, keeping the
@@ -61,12 +61,13 @@ spc5_status tune(spc5_matrix *A, const void *x, void *y, int iters, cudaStream_t
     int log2g, body, flat;
   };
   // the block-balanced and expanded plans, and row-group plans (lanes per
-  // row; the row-stream bodies need one lane per row)
+  // row; bodies 2 to 4 need one lane per row)
   std::vector<Cand> cands;
   cands.push_back({0, 0, 1});
   cands.push_back({0, 0, 2});
   cands.push_back({0, 2, 0});
   cands.push_back({0, 3, 0});
+  cands.push_back({0, 4, 0});
   for (int lg = 0; lg <= max_log2g; ++lg) cands.push_back({lg, 0, 0});
   double best = -1.0, best_rows = -1.0;
   size_t best_i = 0, best_rows_i = 1;

@@ -172,8 +172,8 @@ def test_invalid_csr_is_rejected_on_device():
 @pytest.mark.parametrize("log2g", [0, 1, 2, 3])
 def test_direct_kernel_lane_mappings(monkeypatch, log2g):
     """The direct tile kernel with every lanes-per-row mapping and every row
-    body (set-bit loop, predicated loop, row stream, queued row stream), with
-    and without long-panel pieces."""
+    body (set-bit loop, predicated loop, row stream, queued row stream,
+    four-block rounds), with and without long-panel pieces."""
     monkeypatch.setenv("SPC5_KERNEL", "0")
     monkeypatch.setenv("SPC5_FLAT", "0")
     monkeypatch.setenv("SPC5_LOG2G_GROUP", str(log2g))
@@ -181,7 +181,7 @@ def test_direct_kernel_lane_mappings(monkeypatch, log2g):
     x = synth.vector_uniform(A.ncols, seed=4)
     y_ref, scale = oracle.csr_spmv(A, x)
     for r, c in [(1, 8), (4, 4), (8, 4)]:
-        for body in ("0", "1", "2", "3"):
+        for body in ("0", "1", "2", "3", "4"):
             for vcap in ("", "2048"):
                 monkeypatch.setenv("SPC5_BODY", body)
                 if vcap:
