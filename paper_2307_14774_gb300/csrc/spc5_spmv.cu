@@ -485,24 +485,30 @@ __global__ void __launch_bounds__(kDirectThreads, TileBlocksPerSM<BODY>::v)
 // Block-balanced kernel for matrices whose panels hold very different
 // numbers of blocks (power-law rows): with lanes owning rows, a warp waits
 // for its longest row while the other lanes idle.  Here the blocks of a tile
-// (consecutive whole panels) are dealt to the lanes one block per lane per
-// round, so every lane has a block whatever the row lengths:
-//   - the value offset of a lane's block is the running offset plus the
-//     exclusive warp scan of the blocks' popcounts (Algorithm 1's idxVal);
-//   - a lane forms its block's r row sums (one FMA per set bit, x through
-//     L1/L2);
+// (consecutive whole panels) are dealt to the lanes four consecutive blocks
+// per lane per round, so every lane has work whatever the row lengths:
+//   - the value offset of a lane's blocks is the running offset plus the
+//     exclusive warp scan of the lanes' popcounts (Algorithm 1's idxVal);
+//   - a lane accumulates its blocks' r row sums with one FMA per set bit
+//     (x through L1/L2);
 //   - the panels ending inside the round are found from block_rowptr (a
-//     window of up to 32 panels per step, marked in a 32-bit word by a warp
-//     OR-reduction, their ids passed to the lanes through shared memory);
-//   - a segmented inclusive scan over the lanes adds the block sums of each
-//     panel; the lane holding a panel's last block writes the panel's r rows
-//     of y (one write per row, as in Section 3.2), and the panel still open
-//     at the end of the round carries its sums into the next round.
+//     window of up to 32 panels per step, marked in a 128-bit mask by warp
+//     OR-reductions, their ids passed to the lanes through shared memory);
+//   - a lane writes the rows of the panels that start and end among its own
+//     blocks (one write per row, as in Section 3.2); the partial sums of
+//     panels cut between lanes are completed by a segmented warp scan of the
+//     lanes' last partial sums, and the panel still open at the end of the
+//     round carries its sums into the next round.
+// On GB300 every FP64 instruction costs a 16-cycle slot of the FP64 pipe
+// whatever its active lanes: the scan's adds are paid once per 128 blocks.
 // A piece of a long panel (mode & kPartial) holds one panel only: the lanes
 // keep private row sums over all rounds, reduce them with shuffles at the
 // end and write them to the partial buffer for the fixup kernel.
 // Warps take tiles from a counter (dynamic scheduling); the last warp to
 // finish resets the counter for the next launch.
+constexpr int kFlatKB = 4;                // blocks per lane per round
+constexpr int kFlatRound = 32 * kFlatKB;  // blocks per round
+
 __device__ __forceinline__ int warp_excl_scan(int v, int lane, int *total) {
   int incl = v;
 #pragma unroll
@@ -544,8 +550,8 @@ __device__ __forceinline__ void block_rows(AT (&s)[R], uint32_t m, const VT *__r
 }
 
 template <int R>
-struct FlatBlocksPerSM {
-  static constexpr int v = R >= 4 ? 4 : 6;
+struct FlatBlocksPerSM {  // registers grow with the r row sums a lane keeps
+  static constexpr int v = R == 1 ? 6 : (R == 2 ? 5 : (R == 4 ? 4 : 3));
 };
 
 template <int R, int C, typename VT, typename AT>
@@ -555,8 +561,8 @@ __global__ void __launch_bounds__(kDirectThreads, FlatBlocksPerSM<R>::v)
                 const typename MaskType<R, C>::T *__restrict__ masks,
                 const VT *__restrict__ vals, const AT *__restrict__ x, AT *__restrict__ y,
                 AT *__restrict__ partial, Scale<AT> sc, int64_t nrows) {
-  __shared__ int32_t s_pid[kDirectThreads];
-  int32_t *pid = s_pid + (threadIdx.x & ~31);
+  __shared__ int32_t s_pid[kDirectThreads / 32][kFlatRound];
+  int32_t *pid = s_pid[threadIdx.x >> 5];
   const int lane = threadIdx.x & 31;
   uint32_t grab = 0;
   if (lane == 0) grab = atomicAdd(&sched[0], 1u);
@@ -565,26 +571,30 @@ __global__ void __launch_bounds__(kDirectThreads, FlatBlocksPerSM<R>::v)
     if (lane == 0) grab = atomicAdd(&sched[0], 1u);  // next tile, used after this one
     const Tile cur = tiles[t];
     int32_t v = cur.v0;
-    uint32_t m_next = 0u;
-    int32_t c_next = 0;
-    if (cur.b0 + lane < cur.b1) {
-      m_next = (uint32_t)masks[cur.b0 + lane];
-      c_next = block_colidx[cur.b0 + lane];
-    }
     if (cur.mode & kPartial) {
       AT s[R];
 #pragma unroll
       for (int q = 0; q < R; ++q) s[q] = 0;
-      for (int32_t base = cur.b0; base < cur.b1; base += 32) {
-        const uint32_t m = m_next;
-        const int32_t col = c_next;
-        const int32_t bn = base + 32 + lane;
-        m_next = bn < cur.b1 ? (uint32_t)masks[bn] : 0u;
-        c_next = bn < cur.b1 ? block_colidx[bn] : 0;
+      for (int32_t base = cur.b0; base < cur.b1; base += kFlatRound) {
+        uint32_t m[kFlatKB];
+        int32_t cb[kFlatKB];
+        int cnt = 0;
+#pragma unroll
+        for (int i = 0; i < kFlatKB; ++i) {
+          const int32_t b = base + kFlatKB * lane + i;
+          const bool ok = b < cur.b1;
+          m[i] = ok ? (uint32_t)masks[b] : 0u;
+          cb[i] = ok ? block_colidx[b] : 0;
+          cnt += __popc(m[i]);
+        }
         int total;
-        const int excl = warp_excl_scan(__popc(m), lane, &total);
-        block_rows<R, C>(s, m, vals + v + excl, x + col);
+        int32_t off = v + warp_excl_scan(cnt, lane, &total);
         v += total;
+#pragma unroll
+        for (int i = 0; i < kFlatKB; ++i) {
+          block_rows<R, C>(s, m[i], vals + off, x + cb[i]);
+          off += __popc(m[i]);
+        }
       }
 #pragma unroll
       for (int q = 0; q < R; ++q) {
@@ -602,32 +612,41 @@ __global__ void __launch_bounds__(kDirectThreads, FlatBlocksPerSM<R>::v)
           }
         }
       }
-      AT carry = 0;  // lane q < R: row q's sum of the panel still open
+      AT carry = 0;       // lane q < R: row q's sum of the panel still open
+      bool open = false;  // a panel continues from the previous round
       int32_t pcur = cur.p0;
-      for (int32_t base = cur.b0; base < cur.b1; base += 32) {
-        const int32_t lim = (base + 32 < cur.b1) ? base + 32 : cur.b1;
-        const uint32_t m = m_next;
-        const int32_t col = c_next;
-        const int32_t bn = base + 32 + lane;
-        m_next = bn < cur.b1 ? (uint32_t)masks[bn] : 0u;
-        c_next = bn < cur.b1 ? block_colidx[bn] : 0;
-        int total;
-        const int excl = warp_excl_scan(__popc(m), lane, &total);
-        AT s[R];
+      for (int32_t base = cur.b0; base < cur.b1; base += kFlatRound) {
+        const int32_t lim = (base + kFlatRound < cur.b1) ? base + kFlatRound : cur.b1;
+        uint32_t m[kFlatKB];
+        int32_t cb[kFlatKB];
+        int cnt = 0;
 #pragma unroll
-        for (int q = 0; q < R; ++q) s[q] = 0;
-        block_rows<R, C>(s, m, vals + v + excl, x + col);
+        for (int i = 0; i < kFlatKB; ++i) {
+          const int32_t b = base + kFlatKB * lane + i;
+          const bool ok = b < lim;
+          m[i] = ok ? (uint32_t)masks[b] : 0u;
+          cb[i] = ok ? block_colidx[b] : 0;
+          cnt += __popc(m[i]);
+        }
+        int total;
+        int32_t off = v + warp_excl_scan(cnt, lane, &total);
         v += total;
         // panels whose last block lies in [base, lim): bit (end - 1 - base)
-        uint32_t ends = 0u;
+        uint32_t e0 = 0u, e1 = 0u, e2 = 0u, e3 = 0u;
         for (int32_t w = pcur;; w += 32) {
           const int32_t p = w + lane;
           const bool in = p < cur.p1;
           const int32_t st = in ? brp[p] : 0;
           const int32_t en = in ? brp[p + 1] : 0;
           const bool mark = in && en > st && en > base && en <= lim;
-          if (mark) pid[en - 1 - base] = p;
-          ends |= __reduce_or_sync(kFull, mark ? (1u << (en - 1 - base)) : 0u);
+          const int pos = mark ? en - 1 - base : 0;
+          if (mark) pid[pos] = p;
+          const uint32_t bit = mark ? (1u << (pos & 31)) : 0u;
+          const int wd = pos >> 5;
+          e0 |= __reduce_or_sync(kFull, wd == 0 ? bit : 0u);
+          e1 |= __reduce_or_sync(kFull, wd == 1 ? bit : 0u);
+          e2 |= __reduce_or_sync(kFull, wd == 2 ? bit : 0u);
+          e3 |= __reduce_or_sync(kFull, wd == 3 ? bit : 0u);
           const unsigned beyond = __ballot_sync(kFull, !in || en > lim);
           if (beyond) {
             pcur = w + __ffs(beyond) - 1;
@@ -635,38 +654,81 @@ __global__ void __launch_bounds__(kDirectThreads, FlatBlocksPerSM<R>::v)
           }
         }
         __syncwarp();
-        // segmented inclusive scan: lane adds lane - o when no panel ends in [lane - o, lane)
+        auto endbit = [&](int pos) -> bool {
+          const int wd = pos >> 5;
+          const uint32_t e = wd == 0 ? e0 : (wd == 1 ? e1 : (wd == 2 ? e2 : e3));
+          return (e >> (pos & 31)) & 1u;
+        };
+        uint32_t ef = 0u;  // the lane's blocks that end a panel
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const bool same = lane >= o && ((ends >> (lane - o)) & ((1u << o) - 1u)) == 0u;
+        for (int i = 0; i < kFlatKB; ++i) ef |= (endbit(kFlatKB * lane + i) ? 1u : 0u) << i;
+        // does the lane's first block start a panel?
+        bool fresh = (lane == 0) ? !open : endbit(kFlatKB * lane - 1);
+        AT acc[R], head[R];
 #pragma unroll
-          for (int q = 0; q < R; ++q) {
-            const AT tq = __shfl_up_sync(kFull, s[q], o);
-            if (same) s[q] += tq;
+        for (int q = 0; q < R; ++q) acc[q] = head[q] = 0;
+        bool has_head = false;
+        int32_t head_pid = 0;
+#pragma unroll
+        for (int i = 0; i < kFlatKB; ++i) {
+          block_rows<R, C>(acc, m[i], vals + off, x + cb[i]);
+          off += __popc(m[i]);
+          if ((ef >> i) & 1u) {
+            const int64_t p = pid[kFlatKB * lane + i];
+            if (fresh) {
+#pragma unroll
+              for (int q = 0; q < R; ++q) {
+                const int64_t row = p * R + q;
+                if (row < nrows) put_row(sc, y, row, acc[q]);
+              }
+            } else {
+#pragma unroll
+              for (int q = 0; q < R; ++q) head[q] = acc[q];
+              has_head = true;
+              head_pid = (int32_t)p;
+            }
+#pragma unroll
+            for (int q = 0; q < R; ++q) acc[q] = 0;
+            fresh = true;
           }
         }
-        const int last = lim - 1 - base;
-        const int first_end = ends ? __ffs(ends) - 1 : last;
+        // lane 0's partial continues the open panel when it ends no panel
 #pragma unroll
         for (int q = 0; q < R; ++q) {
           const AT cq = __shfl_sync(kFull, carry, q);
-          if (lane == first_end) s[q] += cq;
+          if (lane == 0 && ef == 0u) acc[q] += cq;
         }
-        if ((ends >> lane) & 1u) {
-          const int64_t p = pid[lane];
+        // segmented scan of the lanes' last partial sums: lane adds lane - o
+        // when no lane in (lane - o, lane] ends a panel
+        const uint32_t endl = __ballot_sync(kFull, ef != 0u);
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const bool same =
+              lane >= o && ((endl >> (lane - o + 1)) & ((1u << o) - 1u)) == 0u;
 #pragma unroll
           for (int q = 0; q < R; ++q) {
-            const int64_t row = p * R + q;
-            if (row < nrows) put_row(sc, y, row, s[q]);
+            const AT tq = __shfl_up_sync(kFull, acc[q], o);
+            if (same) acc[q] += tq;
           }
         }
-        // the segment after the last end stays open (its sums include the
-        // carry when it is also the first segment)
-        const bool open = ((ends >> last) & 1u) == 0u;
+        // panels cut between lanes: the head plus the scanned partial before it
 #pragma unroll
         for (int q = 0; q < R; ++q) {
-          const AT sq = __shfl_sync(kFull, s[q], last);
-          if (lane == q) carry = open ? sq : (AT)0;
+          const AT cin = __shfl_up_sync(kFull, acc[q], 1);
+          const AT cq = __shfl_sync(kFull, carry, q);
+          if (has_head) {
+            const int64_t row = (int64_t)head_pid * R + q;
+            if (row < nrows) put_row(sc, y, row, head[q] + (lane == 0 ? cq : cin));
+          }
+        }
+        // the panel open at the end of the round
+        const int lastpos = lim - 1 - base;
+        open = !endbit(lastpos);
+        const int ll = lastpos / kFlatKB;
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+          const AT sl = __shfl_sync(kFull, acc[q], ll);
+          if (lane == q) carry = open ? sl : (AT)0;
         }
         __syncwarp();
       }
