@@ -203,11 +203,10 @@ __device__ __forceinline__ void put_empty_row(const Scale<AT> &sc, AT *y, int64_
 // its row's values across the panel's blocks, one FMA per loop trip, so a
 // warp issues as many FP64 FMAs as its longest row has values (plus one trip
 // for every block in which a row has no value), instead of the sum over
-// blocks of the largest per-block bit count.  Entering the next block is
-// written without branches (the new block's row bits, value offset and start
-// column are computed by every lane and selected where the current row bits
-// are used up), so the warp does not serialise lanes that change blocks at
-// different trips; the block after next is prefetched one block ahead.
+// blocks of the largest per-block bit count.  A lane enters its panel's next
+// block when its row bits in the current one are used up; the metadata of
+// the block after it is loaded, and its values prefetched to L1, one block
+// ahead.
 template <int R, int C, typename VT, typename AT, typename MaskT>
 __device__ __forceinline__ AT row_stream(const MaskT *__restrict__ masks,
                                          const int32_t *__restrict__ block_colidx,
@@ -239,6 +238,7 @@ __device__ __forceinline__ AT row_stream(const MaskT *__restrict__ masks,
       if (b < nbp) {
         m1 = (uint32_t)masks[bl + b];
         c1 = block_colidx[bl + b];
+        prefetch_l1(vals + v);  // the next block's values, needed a few trips later
       }
     }
     if (mq) {
