@@ -74,6 +74,7 @@ void free_matrix(spc5_matrix *A) {
   cudaFree(A->flong_slots);
   cudaFree(A->fpartial);
   cudaFree(A->fsched);
+  cudaFree(A->frowoff);
   cudaFree(A->dev_error);
   delete A;
 }

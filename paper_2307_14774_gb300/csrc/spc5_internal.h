@@ -87,6 +87,7 @@ struct spc5_matrix {
   int32_t *flong_slots = nullptr;
   int64_t fnlong = 0, fnpieces = 0;
   double *fpartial = nullptr;       // fnpieces * r partial row sums
+  uint16_t *frowoff = nullptr;      // expanded plan: (npanels + fnpieces) * r row starts
   uint32_t *fsched = nullptr;       // [2]: next tile, finished warps (reset by the kernel)
 
   // staging for host vectors in spc5_spmv
@@ -143,6 +144,10 @@ spc5_status spmv_device_scratch(const spc5_matrix *A, const void *x, void *y, do
 
 // Pieces of split panels in the plan the SpMV uses.
 int64_t spmv_pieces(const spc5_matrix *A);
+
+// Row starts of the expanded plan's tiles (A->frowoff, allocated), computed
+// on the GPU once the tiles are written.
+spc5_status expand_row_starts(spc5_matrix *A, cudaStream_t stream);
 
 // Number of kernel launches one spmv_device call makes.
 int spmv_launches(const spc5_matrix *A);

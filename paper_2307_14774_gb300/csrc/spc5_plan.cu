@@ -563,7 +563,11 @@ spc5_status plan_flat(spc5_matrix *A, const int32_t *boff, cudaStream_t s,
                                                           boff, A->ftiles);
   }
   CK(cudaGetLastError(), "expanded plan kernels");
-  return SPC5_OK;
+  const int64_t nro = (np + A->fnpieces) * A->r;
+  CK(cudaMalloc((void **)&A->frowoff, (size_t)std::max<int64_t>(nro, 1) * sizeof(uint16_t)),
+     "alloc expanded row starts");
+  A->device_bytes += nro * (int64_t)sizeof(uint16_t);
+  return expand_row_starts(A, s);
 }
 
 void free_flat(spc5_matrix *A) {
@@ -574,6 +578,11 @@ void free_flat(spc5_matrix *A) {
   cudaFree(A->fsched);
   A->device_bytes -= A->fntiles * (int64_t)sizeof(Tile) + A->fnlong * 12 +
                      A->fnpieces * A->r * (int64_t)sizeof(double) + 8;
+  if (A->frowoff) {
+    cudaFree(A->frowoff);
+    A->device_bytes -= (A->npanels + A->fnpieces) * A->r * (int64_t)sizeof(uint16_t);
+    A->frowoff = nullptr;
+  }
   A->ftiles = nullptr;
   A->flong_panels = nullptr;
   A->flong_slots = nullptr;

@@ -752,23 +752,19 @@ __global__ void __launch_bounds__(kDirectThreads, FlatBlocksPerSM<R>::v)
 // use it; with lanes owning rows, lanes idle whenever rows (or a row's bits
 // in a block) have uneven lengths, and power-law rows leave most lanes idle.
 // This kernel separates the integer work from the FP64 work:
-//   1. counting: the tile's blocks are dealt to the lanes (one block per lane
-//      per round); a lane finds its block's panel by a binary search in the
-//      tile's block_rowptr (staged in shared memory) and packs its block's
-//      per-row bit counts into one 64-bit word (64/r bits per row); a
-//      segmented warp scan of the packed words by panel gives, at the last
-//      lane of each panel, the round's per-row counts, added to the row
-//      counters in shared memory;
-//   2. an exclusive scan of the row counters gives each row's start in a
-//      row-major layout of the tile's values; rows without values get
-//      y = beta y here;
-//   3. scatter: the same rounds again; a value's destination is its row's
-//      cursor plus the exclusive part of the scan plus its rank among the
-//      row's bits in the block, and its value index is the running value
-//      offset (Algorithm 1's idxVal) plus an exclusive warp scan of the
-//      blocks' popcounts; the column x index and the value index are written
-//      to shared memory;
-//   4. FP64: the tile's values, now row by row, are split into 32 equal runs,
+//   1. each tile's row starts in a row-major layout of its values were
+//      computed when the plan was built (k_ex_row_starts: per-row counts
+//      from a segmented warp scan of packed per-row bit counts, then an
+//      exclusive scan); rows without values get y = beta y here;
+//   2. scatter: the tile's blocks are dealt to the lanes one per lane per
+//      round; a lane finds its block's panel by a binary search in the
+//      tile's block_rowptr (staged in shared memory), and a value's
+//      destination is its row's cursor plus its rank among the row's values
+//      of the round (the same packed segmented scan) plus its rank among the
+//      row's bits in the block; its value index is the running value offset
+//      (Algorithm 1's idxVal) plus an exclusive warp scan of the blocks'
+//      popcounts; the column index and the value index go to shared memory;
+//   3. FP64: the tile's values, now row by row, are split into 32 equal runs,
 //      one per lane; a lane multiplies its run's values by x with one FMA per
 //      value (all lanes busy), writes the rows that start and end inside its
 //      run (one write per row, Section 3.2), and a segmented warp scan of the
@@ -809,13 +805,96 @@ __device__ __forceinline__ uint64_t seg_scan_u64(uint64_t w, int32_t key, int la
   return w;
 }
 
+// Per-row value counts of an expanded tile's blocks [b0, b1) (panels
+// [0, np_t) of the tile, block_rowptr slice in s_brp) added to s_row[j*R+q]:
+// blocks are dealt to the lanes one per lane per round; a lane finds its
+// block's panel by a binary search in s_brp and packs the block's per-row bit
+// counts into one 64-bit word; a segmented warp scan of the packed words by
+// panel gives, at the last lane of each panel in the round, the round's
+// per-row counts.
+template <int R, int C>
+__device__ __forceinline__ void ex_count_rows(int lane, int32_t b0, int32_t b1, int32_t np_t,
+                                              const int32_t *s_brp, int32_t *s_row,
+                                              const typename MaskType<R, C>::T *__restrict__ masks) {
+  constexpr int32_t kNoPanel = 0x7fffffff;
+  for (int32_t base = b0; base < b1; base += 32) {
+    const int32_t b = base + lane;
+    const bool valid = b < b1;
+    const uint32_t m = valid ? (uint32_t)masks[b] : 0u;
+    int32_t j = kNoPanel;
+    if (valid) {
+      int lo = 0, hi = np_t - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (s_brp[mid] <= b) lo = mid; else hi = mid - 1;
+      }
+      j = lo;
+    }
+    const uint64_t inc = seg_scan_u64(packed_counts<R, C>(m), j, lane);
+    const int32_t jn = __shfl_down_sync(kFull, j, 1);
+    if (valid && (lane == 31 || jn != j)) {
+#pragma unroll
+      for (int q = 0; q < R; ++q) s_row[j * R + q] += packed_field<R>(inc, q);
+    }
+    __syncwarp();
+  }
+}
+
+// Row starts of every expanded tile, computed once when the plan is built:
+// rowoff[base + r] = index of tile row r's first value in the tile's
+// row-major layout, base = p0 * r for a tile of whole panels and
+// (npanels + slot) * r for a piece of a long panel.  One warp per tile.
+template <int R, int C>
+__global__ void __launch_bounds__(32 * kExpandWarps)
+    k_ex_row_starts(const Tile *__restrict__ tiles, int32_t ntiles, int64_t npanels,
+                    const int32_t *__restrict__ brp,
+                    const typename MaskType<R, C>::T *__restrict__ masks, uint16_t *rowoff) {
+  __shared__ int32_t s_row_all[kExpandWarps][kExpandRows];
+  __shared__ int32_t s_brp_all[kExpandWarps][kExpandRows + 1];
+  const int wid = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  int32_t *s_row = s_row_all[wid];
+  int32_t *s_brp = s_brp_all[wid];
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < ntiles;
+       t += nwarps) {
+    const Tile cur = tiles[t];
+    const bool piece = (cur.mode & kPartial) != 0;
+    const int32_t np_t = piece ? 1 : cur.p1 - cur.p0;
+    const int rows_t = np_t * R;
+    for (int j = lane; j <= np_t; j += 32)
+      s_brp[j] = piece ? (j == 0 ? cur.b0 : cur.b1) : brp[cur.p0 + j];
+    for (int r = lane; r < rows_t; r += 32) s_row[r] = 0;
+    __syncwarp();
+    ex_count_rows<R, C>(lane, cur.b0, cur.b1, np_t, s_brp, s_row, masks);
+    const int r0 = lane * (kExpandRows / 32);
+    int cnt[kExpandRows / 32];
+    int sum = 0;
+#pragma unroll
+    for (int i = 0; i < kExpandRows / 32; ++i) {
+      cnt[i] = (r0 + i < rows_t) ? s_row[r0 + i] : 0;
+      sum += cnt[i];
+    }
+    int total;
+    int start = warp_excl_scan(sum, lane, &total);
+    const int64_t base = piece ? (npanels + cur.slot) * R : (int64_t)cur.p0 * R;
+#pragma unroll
+    for (int i = 0; i < kExpandRows / 32; ++i) {
+      if (r0 + i < rows_t) rowoff[base + r0 + i] = (uint16_t)start;
+      start += cnt[i];
+    }
+    __syncwarp();
+  }
+}
+
 template <int R, int C, typename VT, typename AT>
 __global__ void __launch_bounds__(32 * kExpandWarps, kExpandBlocksPerSM)
     k_spmv_expand(const Tile *__restrict__ tiles, int32_t ntiles, uint32_t *sched,
                   const int32_t *__restrict__ brp, const int32_t *__restrict__ block_colidx,
                   const typename MaskType<R, C>::T *__restrict__ masks,
                   const VT *__restrict__ vals, const AT *__restrict__ x, AT *__restrict__ y,
-                  AT *__restrict__ partial, Scale<AT> sc, int64_t nrows) {
+                  AT *__restrict__ partial, Scale<AT> sc, int64_t nrows,
+                  const uint16_t *__restrict__ rowoff, int64_t npanels) {
   __shared__ int32_t s_col_all[kExpandWarps][kExpandCap];
   __shared__ uint16_t s_vid_all[kExpandWarps][kExpandCap];
   __shared__ int32_t s_row_all[kExpandWarps][kExpandRows];
@@ -838,13 +917,15 @@ __global__ void __launch_bounds__(32 * kExpandWarps, kExpandBlocksPerSM)
     const int32_t np_t = piece ? 1 : cur.p1 - cur.p0;
     const int rows_t = np_t * R;
     const int32_t nv = cur.v1 - cur.v0;
-    {  // the tile's values are read in step 4: start bringing them to L1
+    {  // the tile's values are read in step 3: start bringing them to L1
       constexpr int kLine = 128 / (int)sizeof(VT);
       for (int32_t o = lane * kLine; o < nv; o += 32 * kLine) prefetch_l1(vals + cur.v0 + o);
     }
+    // tile rows' starts (computed when the plan was built)
+    const int64_t rbase = piece ? (npanels + cur.slot) * R : (int64_t)cur.p0 * R;
     for (int j = lane; j <= np_t; j += 32)
       s_brp[j] = piece ? (j == 0 ? cur.b0 : cur.b1) : brp[cur.p0 + j];
-    for (int r = lane; r < rows_t; r += 32) s_row[r] = 0;
+    for (int r = lane; r < rows_t; r += 32) s_row[r] = rowoff[rbase + r];
     __syncwarp();
 
     // tile row of a value: global row (or partial slot) of tile row r
@@ -867,50 +948,19 @@ __global__ void __launch_bounds__(32 * kExpandWarps, kExpandBlocksPerSM)
       return lo;
     };
 
-    // 1. per-row counts
-    for (int32_t base = cur.b0; base < cur.b1; base += 32) {
-      const int32_t b = base + lane;
-      const bool valid = b < cur.b1;
-      const uint32_t m = valid ? (uint32_t)masks[b] : 0u;
-      const int32_t j = valid ? panel_of(b) : kNoPanel;
-      const uint64_t inc = seg_scan_u64(packed_counts<R, C>(m), j, lane);
-      const int32_t jn = __shfl_down_sync(kFull, j, 1);
-      if (valid && (lane == 31 || jn != j)) {
-#pragma unroll
-        for (int q = 0; q < R; ++q) s_row[j * R + q] += packed_field<R>(inc, q);
-      }
-      __syncwarp();
-    }
-    // 2. row starts (exclusive scan; each lane takes 4 consecutive rows)
-    {
-      const int r0 = lane * (kExpandRows / 32);
-      int cnt[kExpandRows / 32];
-      int sum = 0;
-#pragma unroll
-      for (int i = 0; i < kExpandRows / 32; ++i) {
-        cnt[i] = (r0 + i < rows_t) ? s_row[r0 + i] : 0;
-        sum += cnt[i];
-      }
-      int total;
-      int start = warp_excl_scan(sum, lane, &total);
-      __syncwarp();
-#pragma unroll
-      for (int i = 0; i < kExpandRows / 32; ++i) {
-        if (r0 + i < rows_t) {
-          s_row[r0 + i] = start;
-          if (cnt[i] == 0) {
-            if (piece) emit(r0 + i, (AT)0);
-            else {
-              const int64_t row = ((int64_t)cur.p0 + (r0 + i) / R) * R + (r0 + i) % R;
-              if (row < nrows) put_empty_row(sc, y, row);
-            }
-          }
+    // rows without values
+    for (int r = lane; r < rows_t; r += 32) {
+      const int32_t next = (r + 1 < rows_t) ? s_row[r + 1] : nv;
+      if (next == s_row[r]) {
+        if (piece) emit(r, (AT)0);
+        else {
+          const int64_t row = ((int64_t)cur.p0 + r / R) * R + r % R;
+          if (row < nrows) put_empty_row(sc, y, row);
         }
-        start += cnt[i];
       }
-      __syncwarp();
     }
-    // 3. scatter (s_row holds each row's cursor)
+    __syncwarp();
+    // 2. scatter (s_row holds each row's cursor)
     {
       int32_t vrun = 0;
       for (int32_t base = cur.b0; base < cur.b1; base += 32) {
@@ -948,9 +998,10 @@ __global__ void __launch_bounds__(32 * kExpandWarps, kExpandBlocksPerSM)
         __syncwarp();
       }
     }
-    // 4. FP64 (or FP32) products: s_row[r] is now the end of row r
+    // 3. FP64 (or FP32) products: s_row[r] is now the end of row r
     {
-      const int32_t K = (nv + 31) >> 5;
+      // an odd run length keeps the lanes' shared-memory reads on distinct banks
+      const int32_t K = ((nv + 31) >> 5) | 1;
       const int32_t lo = min(lane * K, nv), hi = min(lo + K, nv);
       const VT *__restrict__ tv = vals + cur.v0;
       AT acc = 0, head_val = 0;
@@ -1492,7 +1543,7 @@ cudaError_t launch_expand(const spc5_matrix *A, const AT *x, AT *y, double alpha
     k_spmv_expand<R, C, VT, AT><<<(unsigned)blocks, 32 * kExpandWarps, 0, s>>>(
         A->ftiles, (int32_t)A->fntiles, sched, A->block_rowptr, A->block_colidx,
         (const MaskT *)A->masks, (const VT *)A->values, x, y, partial,
-        make_scale<AT>(alpha, beta), A->nrows);
+        make_scale<AT>(alpha, beta), A->nrows, A->frowoff, A->npanels);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -1504,6 +1555,18 @@ cudaError_t launch_expand(const spc5_matrix *A, const AT *x, AT *y, double alpha
     e = cudaGetLastError();
   }
   return e;
+}
+
+template <int R, int C>
+cudaError_t launch_row_starts(spc5_matrix *A, cudaStream_t s) {
+  using MaskT = typename MaskType<R, C>::T;
+  if (A->fntiles == 0) return cudaSuccess;
+  int64_t blocks = (A->fntiles + kExpandWarps - 1) / kExpandWarps;
+  if (blocks > 65536) blocks = 65536;
+  k_ex_row_starts<R, C><<<(unsigned)blocks, 32 * kExpandWarps, 0, s>>>(
+      A->ftiles, (int32_t)A->fntiles, A->npanels, A->block_rowptr, (const MaskT *)A->masks,
+      A->frowoff);
+  return cudaGetLastError();
 }
 
 template <int R, int C, typename VT, typename AT>
@@ -1576,6 +1639,22 @@ int spmv_launches(const spc5_matrix *A) {
 }
 
 int64_t spmv_pieces(const spc5_matrix *A) { return A->flat ? A->fnpieces : A->npieces; }
+
+spc5_status expand_row_starts(spc5_matrix *A, cudaStream_t s) {
+  cudaError_t e;
+  switch (A->r * 100 + A->c) {
+    case 108: e = launch_row_starts<1, 8>(A, s); break;
+    case 204: e = launch_row_starts<2, 4>(A, s); break;
+    case 208: e = launch_row_starts<2, 8>(A, s); break;
+    case 404: e = launch_row_starts<4, 4>(A, s); break;
+    case 408: e = launch_row_starts<4, 8>(A, s); break;
+    case 804: e = launch_row_starts<8, 4>(A, s); break;
+    default:
+      set_error("unsupported block shape");
+      return SPC5_EUNSUPPORTED_RC;
+  }
+  return cuda_check(e, "expanded tiles' row starts");
+}
 
 spc5_status spmv_device_scratch(const spc5_matrix *A, const void *x, void *y, double alpha,
                                 double beta, cudaStream_t s, void *partial, uint32_t *sched) {
