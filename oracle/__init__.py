@@ -75,7 +75,12 @@ def _bind(lib):
     lib.oracle_quantize.argtypes = [i64, f64p, ci, opt]
     lib.oracle_csr_transpose.argtypes = [i64, i64, i32p, i32p, f64p, i32p, i32p, f64p]
     lib.oracle_values_grad.argtypes = [i64, i32p, i32p, f64p, f64p, f64p]
-    for f in (lib.oracle_quantize, lib.oracle_csr_transpose, lib.oracle_values_grad, lib.oracle_check_csr, lib.oracle_csr_spmv, lib.oracle_csr_spmv_plain,
+    lib.oracle_hybrid_split.argtypes = [i64, ci, ci, i64p, i32p, u64p, f64p, i64p, i32p, u64p,
+                                        f64p, ctypes.POINTER(ctypes.c_int64), i32p, i32p, f64p,
+                                        ctypes.POINTER(ctypes.c_int64)]
+    for f in (lib.oracle_quantize, lib.oracle_csr_transpose, lib.oracle_values_grad,
+              lib.oracle_hybrid_split, lib.oracle_check_csr, lib.oracle_csr_spmv,
+              lib.oracle_csr_spmv_plain,
               lib.oracle_spc5_convert, lib.oracle_spc5_spmv, lib.oracle_spc5_to_csr,
               lib.oracle_pack_masks):
         f.restype = ci
@@ -233,6 +238,32 @@ class Oracle:
                                            _arr(x, np.float64), out))
         return out
 
+    def hybrid_split(self, S: SPC5):
+        """beta(r,c) -> (block part: SPC5 of the blocks holding two or more
+        values, scalars: CSR namespace of the single-value blocks)."""
+        from types import SimpleNamespace
+        nb, nnz = S.nblocks, S.nnz
+        brp = np.zeros(S.npanels + 1, np.int64)
+        bcol = np.zeros(max(nb, 1), np.int32)
+        masks = np.zeros((max(nb, 1), S.r), np.uint64)
+        vals = np.zeros(max(nnz, 1), np.float64)
+        srp = np.zeros(S.nrows + 1, np.int32)
+        scol = np.zeros(max(nnz, 1), np.int32)
+        svals = np.zeros(max(nnz, 1), np.float64)
+        nbb, ns = ctypes.c_int64(0), ctypes.c_int64(0)
+        _check(self.lib.oracle_hybrid_split(S.nrows, S.r, S.c, _arr(S.block_rowptr, np.int64),
+                                            _arr(S.block_colidx, np.int32),
+                                            _arr(S.block_masks.reshape(-1), np.uint64),
+                                            _arr(S.values, np.float64), brp, bcol,
+                                            masks.reshape(-1), vals, ctypes.byref(nbb), srp,
+                                            scol, svals, ctypes.byref(ns)))
+        nbb, ns = nbb.value, ns.value
+        blocks = SPC5(S.nrows, S.ncols, S.r, S.c, brp, bcol[:nbb], masks[:nbb],
+                      vals[:nnz - ns], self.lib)
+        scalars = SimpleNamespace(nrows=S.nrows, ncols=S.ncols, rowptr=srp, colidx=scol[:ns],
+                                  vals=svals[:ns])
+        return blocks, scalars
+
     def to_csr(self, S: SPC5):
         """beta(r,c) -> (rowptr, colidx, vals)."""
         nnz = S.nnz
@@ -275,6 +306,10 @@ def convert(A, r: int, c: int) -> SPC5:
 
 def spc5_spmv(S: SPC5, x) -> np.ndarray:
     return _default().spc5_spmv(S, x)
+
+
+def hybrid_split(S: SPC5):
+    return _default().hybrid_split(S)
 
 
 def to_csr(S: SPC5):

@@ -18,6 +18,8 @@
  *                       nearest even (the reduced-precision value forms)
  *   oracle_csr_transpose  A^T in CSR (for dx = A^T g, the input gradient)
  *   oracle_values_grad  dvals[e] = g[row(e)] * x[col(e)] (value gradient)
+ *   oracle_hybrid_split beta(r,c) -> blocks of two or more values plus the
+ *                       single-value blocks as scalar (CSR) entries
  *
  * Readings of the paper taken here (each one is also listed in the design
  * notes):
@@ -366,5 +368,89 @@ int oracle_values_grad(int64_t nrows, const int32_t *rowptr, const int32_t *coli
                        const double *g, const double *x, double *dvals) {
   for (int64_t i = 0; i < nrows; ++i)
     for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) dvals[e] = g[i] * x[colidx[e]];
+  return ORACLE_OK;
+}
+
+/*
+ * Hybrid form (the paper's closing remarks: a block holding a single value
+ * costs SPC5 a block's metadata and a mask test for one product, and the
+ * paper measures SPC5 slower than CSR below about two values per block; it
+ * proposes mixing the block format with a scalar one).  Reading taken here:
+ * a block whose r masks hold exactly one set bit becomes a scalar entry
+ * (its row, column idxCol + k, its value); every other block stays a block.
+ *
+ * Outputs:
+ *   block part  brp_b[npanels+1], bcol_b[*nb_b], masks_b[*nb_b * r],
+ *               vals_b[nnz - *ns]: the kept blocks in storage order, their
+ *               values in Algorithm 1's order (a beta(r,c) matrix of its own);
+ *   scalars     s_rowptr[nrows+1], s_colidx[*ns], s_vals[*ns]: CSR by row,
+ *               each row's scalars in ascending column order (blocks of a
+ *               panel are ascending and disjoint).
+ * Arrays must be sized for the worst case (nblocks blocks, nnz values).
+ */
+int oracle_hybrid_split(int64_t nrows, int r, int c, const int64_t *block_rowptr,
+                        const int32_t *block_colidx, const uint64_t *block_masks,
+                        const double *values, int64_t *brp_b, int32_t *bcol_b,
+                        uint64_t *masks_b, double *vals_b, int64_t *nb_b, int32_t *s_rowptr,
+                        int32_t *s_colidx, double *s_vals, int64_t *ns) {
+  if (r < 1 || r > 64 || c < 1 || c > 64) return ORACLE_EINVAL;
+  int64_t npanels = (nrows + r - 1) / r;
+  /* pass 1: scalars per row */
+  for (int64_t i = 0; i <= nrows; ++i) s_rowptr[i] = 0;
+  for (int64_t p = 0; p < npanels; ++p)
+    for (int64_t b = block_rowptr[p]; b < block_rowptr[p + 1]; ++b) {
+      int bits = 0, qs = 0;
+      for (int q = 0; q < r; ++q) {
+        uint64_t m = block_masks[b * r + q];
+        for (int k = 0; k < c; ++k)
+          if ((1ULL << k) & m) {
+            ++bits;
+            qs = q;
+          }
+      }
+      if (bits == 1) {
+        if (p * r + qs >= nrows) return ORACLE_EINVAL;
+        s_rowptr[p * r + qs + 1]++;
+      }
+    }
+  for (int64_t i = 0; i < nrows; ++i) s_rowptr[i + 1] += s_rowptr[i];
+  int64_t *next = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nrows > 0 ? nrows : 1));
+  if (!next) return ORACLE_EINVAL;
+  for (int64_t i = 0; i < nrows; ++i) next[i] = s_rowptr[i];
+  /* pass 2: walk the blocks with Algorithm 1's running idxVal */
+  int64_t idxVal = 0, kept = 0, keptVal = 0;
+  for (int64_t p = 0; p < npanels; ++p) {
+    brp_b[p] = kept;
+    for (int64_t b = block_rowptr[p]; b < block_rowptr[p + 1]; ++b) {
+      int bits = 0;
+      for (int q = 0; q < r; ++q) {
+        uint64_t m = block_masks[b * r + q];
+        for (int k = 0; k < c; ++k)
+          if ((1ULL << k) & m) ++bits;
+      }
+      if (bits == 1) {
+        for (int q = 0; q < r; ++q) {
+          uint64_t m = block_masks[b * r + q];
+          for (int k = 0; k < c; ++k)
+            if ((1ULL << k) & m) {
+              int64_t row = p * r + q;
+              s_colidx[next[row]] = (int32_t)(block_colidx[b] + k);
+              s_vals[next[row]] = values[idxVal];
+              ++next[row];
+            }
+        }
+        idxVal += 1;
+      } else {
+        bcol_b[kept] = block_colidx[b];
+        for (int q = 0; q < r; ++q) masks_b[kept * r + q] = block_masks[b * r + q];
+        for (int i = 0; i < bits; ++i) vals_b[keptVal++] = values[idxVal++];
+        ++kept;
+      }
+    }
+  }
+  brp_b[npanels] = kept;
+  *nb_b = kept;
+  *ns = nrows > 0 ? s_rowptr[nrows] : 0;
+  free(next);
   return ORACLE_OK;
 }

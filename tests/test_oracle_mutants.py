@@ -47,6 +47,13 @@ MUTANTS = [
     ("bf16_double_rounding", "bf16_from_f32_rne(round_to_odd_f32(in[i]))",
      "bf16_from_f32_rne((float)in[i])"),
     ("bf16_truncate", "b += 0x7FFFu + lsb;", "b += 0u * lsb;"),
+    ("hybrid_scalar_row", "s_rowptr[p * r + qs + 1]++;", "s_rowptr[p * r + 1]++;"),
+    ("hybrid_scalar_value", "s_vals[next[row]] = values[idxVal];",
+     "s_vals[next[row]] = values[idxVal > 0 ? idxVal - 1 : 0];"),
+    ("hybrid_value_skip", "        idxVal += 1;\n      } else {",
+     "        idxVal += 2;\n      } else {"),
+    ("hybrid_keep_mask_row", "masks_b[kept * r + q] = block_masks[b * r + q];",
+     "masks_b[kept * r + q] = block_masks[b * r];"),
 ]
 
 
@@ -151,8 +158,27 @@ def _pins(O: oracle.Oracle) -> list[str]:
         return np.array_equal(O.quantize(v, "f32").view(np.uint32),
                               v.astype(np.float32).view(np.uint32))
 
+    def hybrid():
+        from test_oracle_hybrid import _expected
+        for A in small + [synth.stencil27(7, 6, 5)]:
+            for r, c in ((1, 8), (2, 4), (4, 8), (3, 5)):
+                S = O.convert(A, r, c)
+                B, Sc = O.hybrid_split(S)
+                keep, scalars, vals_keep = _expected(S)
+                scalars.sort(key=lambda t: (t[0], t[1]))
+                if not (np.array_equal(B.block_colidx, S.block_colidx[keep])
+                        and np.array_equal(B.block_masks, S.block_masks[keep])
+                        and np.array_equal(B.values, vals_keep)
+                        and np.array_equal(Sc.colidx, [t[1] for t in scalars])
+                        and np.array_equal(Sc.vals, [t[2] for t in scalars])
+                        and np.array_equal(np.diff(Sc.rowptr), np.bincount(
+                            [t[0] for t in scalars], minlength=A.nrows))):
+                    return False
+        return True
+
     pin("closed_form", closed_form)
     pin("quantize_exact", quantize_exact)
+    pin("hybrid", hybrid)
     return failed
 
 
