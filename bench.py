@@ -65,6 +65,7 @@ def parse_args():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-cg", action="store_true")
     ap.add_argument("--no-grad", action="store_true")
+    ap.add_argument("--no-hybrid", action="store_true")
     ap.add_argument("--no-tune", action="store_true",
                     help="keep the planner's default mapping instead of autotuning it")
     ap.add_argument("--cases-out", default=None, help="write the per-case table here")
@@ -311,6 +312,55 @@ def precision_section(hosts, torch, spc5, stream, hbm, case_rows, log, reps=10, 
         del dev, dabs, flush
         torch.cuda.synchronize()
         log(f"precision rows for {name} done")
+    return rows
+
+
+def hybrid_section(hosts, torch, spc5, stream, hbm, case_rows, log, reps=10, tune=True):
+    """Hybrid form (single-value blocks as scalar CSR entries) of the
+    power-law and uniform matrices, every beta, FP64: time per SpMV (tuned
+    like the main step), the share of entries stored as scalars, and the
+    speed-up over the plain beta(r,c) case of the main step."""
+    base_us = {(r["matrix"], r["beta"]): r["us"] for r in case_rows}
+    rows = []
+    for name in ("powerlaw", "uniform"):
+        if name not in hosts:
+            continue
+        A, x = hosts[name]
+        dev = [torch.from_numpy(a).cuda() for a in (A.rowptr, A.colidx, A.vals)]
+        dx = torch.from_numpy(x).cuda()
+        dy = torch.empty(A.nrows, dtype=torch.float64, device="cuda")
+        for r, c in BETAS:
+            M = spc5.spc5_convert_hybrid(A.nrows, A.ncols, A.nnz, *dev, r=r, c=c)
+            if tune:
+                spc5.spc5_tune(M, dx, dy, iters=3)
+            info = M.info()
+            for _ in range(3):
+                spc5.spc5_spmv(M, dx, dy, 1.0, 0.0, stream)
+            evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                   for _ in range(reps)]
+            for e0, e1 in evs:
+                e0.record(stream)
+                spc5.spc5_spmv(M, dx, dy, 1.0, 0.0, stream)
+                e1.record(stream)
+            torch.cuda.synchronize()
+            us = statistics.median(e0.elapsed_time(e1) for e0, e1 in evs) * 1e3
+            ns = info["nscalars"]
+            nb, npan = info["nblocks"], info["npanels"]
+            b = (8 * A.nnz + 4 * nb + info["mask_bytes"] * nb + 8 * (npan + 1) + 4 * ns
+                 + 4 * (A.nrows + 1) + 8 * A.ncols + 8 * A.nrows)
+            ref = base_us.get((name, f"{r}x{c}"))
+            rows.append({"matrix": name, "beta": f"{r}x{c}", "us": round(us, 2),
+                         "gflops": round(2.0 * A.nnz / (us * 1e-6) / 1e9, 1),
+                         "gbs": round(b / (us * 1e-6) / 1e9, 1),
+                         "frac": round(b / (us * 1e-6) / 1e9 / hbm, 3),
+                         "scalar_share": round(ns / A.nnz, 3),
+                         "speedup_vs_blocks": round(ref / us, 2) if ref else None,
+                         "plan": ({1: "blocks", 2: "expanded"}.get(info["flat"])
+                                  or f"rows/G{info['lanes_per_row']}")})
+            del M
+        del dev
+        torch.cuda.synchronize()
+        log(f"hybrid rows for {name} done")
     return rows
 
 
@@ -625,6 +675,12 @@ def run_native(args):
         result["ircg"] = cg_section(torch, spc5, synth, stream, log)
     if not args.no_grad and rank == 0:
         result["autograd"] = grad_section(torch, spc5, synth, log)
+    if not args.no_hybrid and rank == 0:
+        result["hybrid"] = {
+            "note": "single-value blocks stored as scalar CSR entries (FP64); algorithmic bytes "
+                    "add 4 bytes per scalar column and the scalar row pointer",
+            "rows": hybrid_section(hosts, torch, spc5, stream, hbm, case_rows, log,
+                                   tune=not args.no_tune)}
 
     # end to end through the C-ABI with host vectors: every step copies x from
     # pinned host memory and reads y back

@@ -85,6 +85,9 @@ typedef struct {
                               2 each tile's values split evenly over the lanes (expanded) */
   double group_efficiency; /* busy share of the row-group plan's block slots; below 0.7 the
                               converter picks plan 1 for r*c <= 16 and plan 2 for r*c = 32 */
+  int32_t hybrid;          /* 1 for a matrix from spc5_convert_hybrid */
+  int64_t nscalars;        /* hybrid: single-value blocks stored as scalars (nnz counts them;
+                              nblocks and filling describe the remaining blocks) */
 } spc5_info;
 
 /*
@@ -116,6 +119,36 @@ spc5_status spc5_convert_csr(int64_t nrows, int64_t ncols, int64_t nnz, const in
                              const int32_t *colidx, const void *vals, spc5_dtype vals_dtype,
                              spc5_dtype store_dtype, int r, int c, void *stream,
                              spc5_matrix **out);
+
+/*
+ * spc5_convert_hybrid -- the hybrid form the paper proposes for low-filling
+ * matrices (closing remarks: SPC5 is slower than CSR below about two values
+ * per block, so mix the block format with a scalar one).  Converts like
+ * spc5_convert_csr, then moves every block whose r masks hold exactly one
+ * set bit to a CSR of scalars (row, column, value; each row's columns
+ * ascending); the other blocks stay a beta(r,c) matrix with values in
+ * Algorithm 1's order.  A single-value block's bit is its block's first
+ * column, so a scalar's column is its block's start column.
+ *
+ * spc5_spmv, spc5_spmv_noalloc, spc5_tune, spc5_ircg, spc5_matrix_info,
+ * spc5_export (the block part) and spc5_export_hybrid (the scalars) take the
+ * handle; the transposed product, the value gradient, spc5_set_values and
+ * the batched product give SPC5_EUNSUPPORTED.  Same arguments, ownership
+ * and errors as spc5_convert_csr.
+ */
+spc5_status spc5_convert_hybrid(int64_t nrows, int64_t ncols, int64_t nnz, const int32_t *rowptr,
+                                const int32_t *colidx, const void *vals, spc5_dtype vals_dtype,
+                                spc5_dtype store_dtype, int r, int c, void *stream,
+                                spc5_matrix **out);
+
+/*
+ * spc5_export_hybrid -- device pointers to a hybrid matrix's scalars, owned
+ * by the handle: s_rowptr[nrows + 1] (int32), s_colidx[nscalars] (int32),
+ * s_vals[nscalars] in the storage type.  SPC5_EINVAL if A is not hybrid.
+ * Any output pointer may be NULL.
+ */
+spc5_status spc5_export_hybrid(const spc5_matrix *A, const int32_t **s_rowptr,
+                               const int32_t **s_colidx, const void **s_vals);
 
 /* Fill *info with the matrix description (host-only, no device work). */
 spc5_status spc5_matrix_info(const spc5_matrix *A, spc5_info *info);

@@ -75,6 +75,13 @@ void free_matrix(spc5_matrix *A) {
   cudaFree(A->fpartial);
   cudaFree(A->fsched);
   cudaFree(A->frowoff);
+  cudaFree(A->s_rowptr);
+  cudaFree(A->s_colidx);
+  cudaFree(A->s_vals);
+  cudaFree(A->stiles);
+  cudaFree(A->slong_rows);
+  cudaFree(A->slong_slots);
+  cudaFree(A->spartial);
   cudaFree(A->dev_error);
   delete A;
 }
@@ -176,6 +183,36 @@ spc5_status spc5_convert_csr(int64_t nrows, int64_t ncols, int64_t nnz, const in
   return SPC5_OK;
 }
 
+spc5_status spc5_convert_hybrid(int64_t nrows, int64_t ncols, int64_t nnz, const int32_t *rowptr,
+                                const int32_t *colidx, const void *vals, spc5_dtype vals_dtype,
+                                spc5_dtype store_dtype, int r, int c, void *stream,
+                                spc5_matrix **out) {
+  spc5_matrix *A = nullptr;
+  spc5_status st = spc5_convert_csr(nrows, ncols, nnz, rowptr, colidx, vals, vals_dtype,
+                                    store_dtype, r, c, stream, &A);
+  if (st != SPC5_OK) return st;
+  {
+    DeviceGuard g(A->device);
+    st = hybrid_split(A, (cudaStream_t)stream);
+  }
+  if (st != SPC5_OK) {
+    free_matrix(A);
+    return st;
+  }
+  *out = A;
+  return SPC5_OK;
+}
+
+spc5_status spc5_export_hybrid(const spc5_matrix *A, const int32_t **s_rowptr,
+                               const int32_t **s_colidx, const void **s_vals) {
+  RETURN_IF(!A, SPC5_EINVAL, "NULL handle");
+  RETURN_IF(!A->hybrid, SPC5_EINVAL, "not a hybrid matrix");
+  if (s_rowptr) *s_rowptr = A->s_rowptr;
+  if (s_colidx) *s_colidx = A->s_colidx;
+  if (s_vals) *s_vals = A->s_vals;
+  return SPC5_OK;
+}
+
 spc5_status spc5_matrix_info(const spc5_matrix *A, spc5_info *info) {
   RETURN_IF(!A || !info, SPC5_EINVAL, "NULL argument");
   std::memset(info, 0, sizeof(*info));
@@ -207,6 +244,10 @@ spc5_status spc5_matrix_info(const spc5_matrix *A, spc5_info *info) {
   info->tuned_us = A->tuned_us;
   info->flat = A->flat;
   info->group_efficiency = A->group_efficiency;
+  info->hybrid = A->hybrid;
+  info->nscalars = A->nscalars;
+  info->nnz = A->nnz + A->nscalars;
+  info->filling = A->nblocks ? (double)A->nnz / ((double)A->nblocks * A->r * A->c) : 0.0;
   return SPC5_OK;
 }
 

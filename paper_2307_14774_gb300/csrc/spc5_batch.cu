@@ -285,6 +285,10 @@ extern "C" spc5_status spc5_batch_create(int nmat, const spc5_matrix *const *A,
       set_error("NULL matrix or vector in the batch");
       return SPC5_EINVAL;
     }
+    if (A[m]->hybrid) {
+      set_error("the batched product does not take hybrid matrices");
+      return SPC5_EUNSUPPORTED;
+    }
     if (A[m]->value_dtype != A[0]->value_dtype || A[m]->device != A[0]->device) {
       set_error("all matrices of a batch share one value dtype and one device");
       return SPC5_EINVAL;

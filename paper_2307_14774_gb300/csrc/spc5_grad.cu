@@ -253,6 +253,10 @@ extern "C" spc5_status spc5_spmv_t(const spc5_matrix *A, const void *g, void *dx
     set_error("NULL argument");
     return SPC5_EINVAL;
   }
+  if (A->hybrid) {
+    set_error("spc5_spmv_t does not take hybrid matrices");
+    return SPC5_EUNSUPPORTED;
+  }
   if (A->ncols == 0) return SPC5_OK;
   if ((A->nrows > 0 && !device_readable(g)) || !device_readable(dx)) {
     set_error("spc5_spmv_t takes device vectors");
@@ -278,6 +282,10 @@ extern "C" spc5_status spc5_values_grad(const spc5_matrix *A, const void *g, con
     set_error("NULL argument");
     return SPC5_EINVAL;
   }
+  if (A->hybrid) {
+    set_error("spc5_values_grad does not take hybrid matrices");
+    return SPC5_EUNSUPPORTED;
+  }
   if (A->nnz == 0) return SPC5_OK;
   if (!device_readable(g) || !device_readable(x) || !device_readable(dvals)) {
     set_error("spc5_values_grad takes device arrays");
@@ -301,6 +309,10 @@ extern "C" spc5_status spc5_set_values(spc5_matrix *A, const double *vals, void 
   if (!A || (A->nnz > 0 && !vals)) {
     set_error("NULL argument");
     return SPC5_EINVAL;
+  }
+  if (A->hybrid) {
+    set_error("spc5_set_values does not take hybrid matrices");
+    return SPC5_EUNSUPPORTED;
   }
   if (A->nnz == 0) return SPC5_OK;
   if (!device_readable(vals)) {

@@ -88,6 +88,20 @@ struct spc5_matrix {
   int64_t fnlong = 0, fnpieces = 0;
   double *fpartial = nullptr;       // fnpieces * r partial row sums
   uint16_t *frowoff = nullptr;      // expanded plan: (npanels + fnpieces) * r row starts
+
+  // Hybrid form (hybrid != 0): the single-value blocks were moved to a CSR of
+  // scalars; the arrays above then hold the blocks of two or more values
+  // (nblocks of them, nnz values) and the scalars come on top.
+  int hybrid = 0;
+  int64_t nscalars = 0;
+  int32_t *s_rowptr = nullptr;      // nrows + 1
+  int32_t *s_colidx = nullptr;      // nscalars (+16 bytes of padding)
+  void *s_vals = nullptr;           // nscalars values in the storage type (+16 bytes)
+  spc5::Tile *stiles = nullptr;     // expanded tiles over the scalars' rows
+  int64_t sntiles = 0;
+  int32_t *slong_rows = nullptr, *slong_slots = nullptr;
+  int64_t snlong = 0, snpieces = 0;
+  double *spartial = nullptr;       // snpieces partial sums
   uint32_t *fsched = nullptr;       // [2]: next tile, finished warps (reset by the kernel)
 
   // staging for host vectors in spc5_spmv
@@ -145,11 +159,34 @@ spc5_status spmv_device_scratch(const spc5_matrix *A, const void *x, void *y, do
 // Pieces of split panels in the plan the SpMV uses.
 int64_t spmv_pieces(const spc5_matrix *A);
 
+// Expanded tiles over panels of `r` rows whose blocks hold the values
+// [vptr[p], vptr[p+1]) (boff[b] = value offset of block b): tiles of whole
+// panels (at most kExpandCap values and kExpandRows rows) and pieces of
+// longer panels.  Allocates tiles, long_panels and long_slots.
+struct ExpandedPlan {
+  Tile *tiles = nullptr;
+  int32_t *long_panels = nullptr, *long_slots = nullptr;
+  int64_t ntiles = 0, nlong = 0, npieces = 0;
+};
+spc5_status build_expanded(int64_t npanels, int64_t nblocks, int64_t nvalues, int r,
+                           const int32_t *brp, const int32_t *vptr, const int32_t *boff,
+                           cudaStream_t stream, ExpandedPlan *out);
+
 // Row starts of the expanded plan's tiles (A->frowoff, allocated), computed
 // on the GPU once the tiles are written.
 spc5_status expand_row_starts(spc5_matrix *A, cudaStream_t stream);
 
 // Number of kernel launches one spmv_device call makes.
 int spmv_launches(const spc5_matrix *A);
+
+// Hybrid form: move the single-value blocks of a converted matrix to a CSR
+// of scalars, rebuild the block part's plan and build the scalars' plan.
+spc5_status hybrid_split(spc5_matrix *A, cudaStream_t stream);
+
+// y += alpha * S x for the scalars of a hybrid matrix (after the block part
+// wrote y), partial sums of split rows at `partial` (snpieces values), tile
+// counters at `sched`.
+spc5_status spmv_scalars(const spc5_matrix *A, const void *x, void *y, double alpha,
+                         cudaStream_t stream, void *partial, uint32_t *sched);
 
 }  // namespace spc5

@@ -97,7 +97,7 @@ extern "C" spc5_status spc5_spmv_noalloc(const spc5_matrix *A, const void *x, vo
     set_error("spc5_spmv_noalloc takes device vectors only (host vectors need staging buffers)");
     return SPC5_EINVAL;
   }
-  const int64_t need = spmv_pieces(A) * A->r;
+  const int64_t need = spmv_pieces(A) * A->r + (A->hybrid ? A->snpieces : 0);
   if (need > kNoallocScratchDoubles) {
     set_error("the matrix's split panels need " + std::to_string(need) +
               " partial sums; spc5_spmv_noalloc holds at most " +
@@ -116,6 +116,9 @@ extern "C" spc5_status spc5_spmv_noalloc(const spc5_matrix *A, const void *x, vo
     if (st != SPC5_OK) return st;
   }
   st = spmv_device_scratch(A, x, y, alpha, beta, (cudaStream_t)stream, scratch, sched);
+  if (st == SPC5_OK && A->hybrid)  // the scalars' partial sums follow the blocks'
+    st = spmv_scalars(A, x, y, alpha, (cudaStream_t)stream,
+                      (char *)scratch + spmv_pieces(A) * A->r * sizeof(double), sched);
   if (cur != A->device) cudaSetDevice(cur);
   return st;
 }

@@ -414,6 +414,69 @@ int round_up(int v, int m) { return (v + m - 1) / m * m; }
     if (_st != SPC5_OK) return _st;               \
   } while (0)
 
+spc5_status build_expanded(int64_t np, int64_t nb, int64_t nvalues, int r, const int32_t *brp,
+                           const int32_t *vptr, const int32_t *boff, cudaStream_t s,
+                           ExpandedPlan *out) {
+  *out = ExpandedPlan{};
+  int32_t counts[3] = {0, 0, 0};
+  Tmp<int32_t> bpanel(s), pf(s), pscan(s), tc(s), lf(s), tbase(s), lbase(s), tmp(s);
+  ExpandParams E{np, nb, nvalues, kExpandRows / r, brp, vptr};
+  PlanParams P{};
+  P.npanels = np;
+  P.nblocks = nb;
+  P.brp = brp;
+  if (np > 0) {
+    CK(bpanel.alloc(nb), "alloc");
+    CK(pf.alloc(nb), "alloc");
+    CK(pscan.alloc(nb + 1), "alloc");
+    CK(tc.alloc(np), "alloc");
+    CK(lf.alloc(np), "alloc");
+    CK(tbase.alloc(np + 1), "alloc");
+    CK(lbase.alloc(np + 1), "alloc");
+    CK(tmp.alloc(scan_tmp_elems(std::max<int64_t>(nb, np) + 1)), "alloc");
+    if (nb > 0) {
+      CK(cudaMemsetAsync(bpanel.p, 0, (size_t)nb * sizeof(int32_t), s), "memset");
+      if (np > 1) k_mark_panels<<<grid_for(np), kThreads, 0, s>>>(P, bpanel.p);
+      CK(device_scan<int32_t>(nb, ReadI32{bpanel.p}, WriteI32{bpanel.p}, AddI32{}, 0, true,
+                              tmp.p, s),
+         "scan panels");
+      k_ex_piece_flags<<<grid_for(nb), kThreads, 0, s>>>(E, bpanel.p, boff, pf.p);
+    }
+    CK(device_scan<int32_t>(nb + 1, ReadI32Pad{pf.p, nb}, WriteI32{pscan.p}, AddI32{}, 0, false,
+                            tmp.p, s),
+       "scan pieces");
+    k_ex_counts<<<grid_for(np), kThreads, 0, s>>>(E, pscan.p, tc.p, lf.p);
+    CK(device_scan<int32_t>(np + 1, ReadI32Pad{tc.p, np}, WriteI32{tbase.p}, AddI32{}, 0, false,
+                            tmp.p, s),
+       "scan expanded tiles");
+    CK(device_scan<int32_t>(np + 1, ReadI32Pad{lf.p, np}, WriteI32{lbase.p}, AddI32{}, 0, false,
+                            tmp.p, s),
+       "scan expanded long panels");
+    CK(cudaMemcpyAsync(&counts[0], tbase.p + np, 4, cudaMemcpyDeviceToHost, s), "rd");
+    CK(cudaMemcpyAsync(&counts[1], lbase.p + np, 4, cudaMemcpyDeviceToHost, s), "rd");
+    CK(cudaMemcpyAsync(&counts[2], pscan.p + nb, 4, cudaMemcpyDeviceToHost, s), "rd");
+  }
+  CK(cudaStreamSynchronize(s), "sync expanded plan counts");
+  out->ntiles = counts[0];
+  out->nlong = counts[1];
+  out->npieces = counts[2];
+  CK(cudaMalloc((void **)&out->tiles, (size_t)std::max<int64_t>(out->ntiles, 1) * sizeof(Tile)),
+     "alloc expanded tiles");
+  CK(cudaMalloc((void **)&out->long_panels, (size_t)std::max<int64_t>(out->nlong, 1) * 4),
+     "alloc");
+  CK(cudaMalloc((void **)&out->long_slots, (size_t)std::max<int64_t>(out->nlong, 1) * 8),
+     "alloc");
+  if (np > 0) {
+    k_ex_write_panels<<<grid_for(np), kThreads, 0, s>>>(E, tbase.p, lbase.p, pscan.p, out->tiles,
+                                                        out->long_panels, out->long_slots);
+    if (nb > 0 && out->nlong > 0)
+      k_ex_write_pieces<<<grid_for(nb), kThreads, 0, s>>>(E, bpanel.p, pf.p, pscan.p, tbase.p,
+                                                          boff, out->tiles);
+  }
+  CK(cudaGetLastError(), "expanded plan kernels");
+  return SPC5_OK;
+}
+
 namespace {
 
 // Device arrays of the block-balanced or expanded plan (fntiles, fnlong and
@@ -514,55 +577,23 @@ spc5_status plan_flat(spc5_matrix *A, const int32_t *boff, cudaStream_t s,
     return SPC5_OK;
   }
 
-  ExpandParams E{np, nb, A->nnz, kExpandRows / A->r, A->block_rowptr, A->panel_vptr};
-  PlanParams P{};
-  P.npanels = np;
-  P.nblocks = nb;
-  P.brp = A->block_rowptr;
-  if (np > 0) {
-    CK(bpanel.alloc(nb), "alloc");
-    CK(pf.alloc(nb), "alloc");
-    CK(pscan.alloc(nb + 1), "alloc");
-    CK(tc.alloc(np), "alloc");
-    CK(lf.alloc(np), "alloc");
-    CK(tbase.alloc(np + 1), "alloc");
-    CK(lbase.alloc(np + 1), "alloc");
-    CK(tmp.alloc(scan_tmp_elems(std::max<int64_t>(nb, np) + 1)), "alloc");
-    if (nb > 0) {
-      CK(cudaMemsetAsync(bpanel.p, 0, (size_t)nb * sizeof(int32_t), s), "memset");
-      if (np > 1) k_mark_panels<<<grid_for(np), kThreads, 0, s>>>(P, bpanel.p);
-      CK(device_scan<int32_t>(nb, ReadI32{bpanel.p}, WriteI32{bpanel.p}, AddI32{}, 0, true,
-                              tmp.p, s),
-         "scan panels");
-      k_ex_piece_flags<<<grid_for(nb), kThreads, 0, s>>>(E, bpanel.p, boff, pf.p);
-    }
-    CK(device_scan<int32_t>(nb + 1, ReadI32Pad{pf.p, nb}, WriteI32{pscan.p}, AddI32{}, 0, false,
-                            tmp.p, s),
-       "scan pieces");
-    k_ex_counts<<<grid_for(np), kThreads, 0, s>>>(E, pscan.p, tc.p, lf.p);
-    CK(device_scan<int32_t>(np + 1, ReadI32Pad{tc.p, np}, WriteI32{tbase.p}, AddI32{}, 0, false,
-                            tmp.p, s),
-       "scan expanded tiles");
-    CK(device_scan<int32_t>(np + 1, ReadI32Pad{lf.p, np}, WriteI32{lbase.p}, AddI32{}, 0, false,
-                            tmp.p, s),
-       "scan expanded long panels");
-    CK(cudaMemcpyAsync(&counts[0], tbase.p + np, 4, cudaMemcpyDeviceToHost, s), "rd");
-    CK(cudaMemcpyAsync(&counts[1], lbase.p + np, 4, cudaMemcpyDeviceToHost, s), "rd");
-    CK(cudaMemcpyAsync(&counts[2], pscan.p + nb, 4, cudaMemcpyDeviceToHost, s), "rd");
+  ExpandedPlan ep;
+  {
+    spc5_status st = build_expanded(np, nb, A->nnz, A->r, A->block_rowptr, A->panel_vptr, boff, s,
+                                    &ep);
+    if (st != SPC5_OK) return st;
   }
-  CK(cudaStreamSynchronize(s), "sync expanded plan counts");
-  A->fntiles = counts[0];
-  A->fnlong = counts[1];
-  A->fnpieces = counts[2];
-  CK(alloc_flat_arrays(A), "alloc expanded plan");
-  if (np > 0) {
-    k_ex_write_panels<<<grid_for(np), kThreads, 0, s>>>(E, tbase.p, lbase.p, pscan.p, A->ftiles,
-                                                        A->flong_panels, A->flong_slots);
-    if (nb > 0 && A->fnlong > 0)
-      k_ex_write_pieces<<<grid_for(nb), kThreads, 0, s>>>(E, bpanel.p, pf.p, pscan.p, tbase.p,
-                                                          boff, A->ftiles);
-  }
-  CK(cudaGetLastError(), "expanded plan kernels");
+  A->ftiles = ep.tiles;
+  A->flong_panels = ep.long_panels;
+  A->flong_slots = ep.long_slots;
+  A->fntiles = ep.ntiles;
+  A->fnlong = ep.nlong;
+  A->fnpieces = ep.npieces;
+  CK(cudaMalloc((void **)&A->fpartial,
+                (size_t)std::max<int64_t>(A->fnpieces, 1) * A->r * sizeof(double)),
+     "alloc expanded partial");
+  A->device_bytes += A->fntiles * (int64_t)sizeof(Tile) + A->fnlong * 12 +
+                     A->fnpieces * A->r * (int64_t)sizeof(double);
   const int64_t nro = (np + A->fnpieces) * A->r;
   CK(cudaMalloc((void **)&A->frowoff, (size_t)std::max<int64_t>(nro, 1) * sizeof(uint16_t)),
      "alloc expanded row starts");

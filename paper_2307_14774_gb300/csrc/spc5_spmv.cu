@@ -1075,6 +1075,131 @@ __global__ void __launch_bounds__(32 * kExpandWarps, kExpandBlocksPerSM)
   }
 }
 
+// ----------------------------------------------------------- scalar kernel --
+
+// Scalars of a hybrid matrix: y += alpha * S x for the CSR of single-value
+// blocks, after the block part wrote y.  The scalars are already row by row,
+// so this is the FP64 step of the expanded kernel reading global memory:
+// tiles of whole rows (at most kExpandCap values and kExpandRows rows) split
+// into 32 equal runs of values, one per lane, one FMA per value; a lane adds
+// the rows that start and end in its run to y, and a segmented warp scan of
+// the lanes' last partial sums completes the rows cut between lanes.  A piece
+// of a long row writes its sum to the partial buffer.
+template <typename VT, typename AT>
+__global__ void __launch_bounds__(32 * kExpandWarps)
+    k_spmv_scalars(const Tile *__restrict__ tiles, int32_t ntiles, uint32_t *sched,
+                   const int32_t *__restrict__ s_rowptr, const int32_t *__restrict__ s_colidx,
+                   const VT *__restrict__ s_vals, const AT *__restrict__ x, AT *__restrict__ y,
+                   AT *__restrict__ partial, AT alpha) {
+  __shared__ int32_t s_row_all[kExpandWarps][kExpandRows];
+  const int wid = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  int32_t *s_row = s_row_all[wid];
+  uint32_t grab = 0;
+  if (lane == 0) grab = atomicAdd(&sched[0], 1u);
+  int32_t t = (int32_t)__shfl_sync(kFull, grab, 0);
+  while (t < ntiles) {
+    if (lane == 0) grab = atomicAdd(&sched[0], 1u);  // next tile, used after this one
+    const Tile cur = tiles[t];
+    const bool piece = (cur.mode & kPartial) != 0;
+    const int rows_t = piece ? 1 : cur.p1 - cur.p0;
+    const int32_t nv = cur.v1 - cur.v0;
+    // end of each tile row's values, relative to the tile's first value
+    for (int r = lane; r < rows_t; r += 32)
+      s_row[r] = (piece ? cur.v1 : s_rowptr[cur.p0 + r + 1]) - cur.v0;
+    __syncwarp();
+    auto emit = [&](int r, AT v) {
+      if (piece) partial[cur.slot] = v;
+      else {
+        const int64_t row = (int64_t)cur.p0 + r;
+        y[row] = fma(alpha, v, y[row]);
+      }
+    };
+    const int32_t K = ((nv + 31) >> 5) | 1;
+    const int32_t lo = min(lane * K, nv), hi = min(lo + K, nv);
+    const VT *__restrict__ tv = s_vals + cur.v0;
+    const int32_t *__restrict__ tc = s_colidx + cur.v0;
+    AT acc = 0, head_val = 0;
+    int head_row = -1, tail_row = -1;
+    if (lo < hi) {
+      int a = 0, bnd = rows_t - 1;  // first row ending after lo
+      while (a < bnd) {
+        const int mid = (a + bnd) >> 1;
+        if (s_row[mid] > lo) bnd = mid; else a = mid + 1;
+      }
+      int r = a;
+      int32_t rend = s_row[r];
+      bool started_here = (r == 0 ? 0 : s_row[r - 1]) >= lo;
+      for (int32_t i0 = lo; i0 < hi; i0 += 4) {
+        AT av[4], xv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if (i0 + u < hi) {
+            av[u] = (AT)widen(tv[i0 + u]);
+            xv[u] = __ldg(x + tc[i0 + u]);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int32_t i = i0 + u;
+          if (i < hi) {
+            acc = fma(av[u], xv[u], acc);
+            if (i + 1 == rend) {
+              if (started_here) {
+                emit(r, acc);
+              } else {
+                head_row = r;
+                head_val = acc;
+              }
+              acc = 0;
+              if (i + 1 < nv) {
+                do {
+                  ++r;
+                } while (s_row[r] <= i + 1);
+                rend = s_row[r];
+                started_here = true;
+              }
+            }
+          }
+        }
+      }
+      if (hi < nv) tail_row = r;
+    }
+    AT sv = (tail_row >= 0) ? acc : (AT)0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const AT tsv = __shfl_up_sync(kFull, sv, o);
+      const int kr = __shfl_up_sync(kFull, tail_row, o);
+      if (lane >= o && kr == tail_row && tail_row >= 0) sv += tsv;
+    }
+    const AT cin = __shfl_up_sync(kFull, sv, 1);
+    if (head_row >= 0) emit(head_row, head_val + cin);
+    __syncwarp();
+    t = (int32_t)__shfl_sync(kFull, grab, 0);
+  }
+  if (lane == 0) {
+    const uint32_t nwarps = gridDim.x * (blockDim.x >> 5);
+    if (atomicAdd(&sched[1], 1u) == nwarps - 1) {
+      atomicExch(&sched[0], 0u);
+      atomicExch(&sched[1], 0u);
+    }
+  }
+}
+
+// y[row] += alpha * (sum of the row's pieces, in order) for rows of scalars
+// cut into pieces.
+template <typename AT>
+__global__ void k_fixup_add(int64_t nlong, const int32_t *long_rows, const int32_t *long_slots,
+                            const AT *partial, AT *y, AT alpha) {
+  for (int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; l < nlong;
+       l += (int64_t)gridDim.x * blockDim.x) {
+    AT acc = 0;
+    for (int32_t s = long_slots[2 * l]; s < long_slots[2 * l + 1]; ++s) acc += partial[s];
+    const int64_t row = long_rows[l];
+    y[row] = fma(alpha, acc, y[row]);
+  }
+}
+
 // ------------------------------------------------------------ staged kernel --
 
 // Written by the producer before it arms the stage's barrier.  `seq` is the
@@ -1634,8 +1759,9 @@ cudaError_t launch(const spc5_matrix *A, const void *x, void *y, double alpha, d
 
 int spmv_launches(const spc5_matrix *A) {
   if (A->nrows == 0) return 0;
-  if (A->flat) return (A->fntiles > 0 ? 1 : 0) + (A->fnlong > 0 ? 1 : 0);
-  return (A->ntiles > 0 ? 1 : 0) + (A->nlong > 0 ? 1 : 0);
+  const int sc = A->hybrid ? (A->sntiles > 0 ? 1 : 0) + (A->snlong > 0 ? 1 : 0) : 0;
+  if (A->flat) return (A->fntiles > 0 ? 1 : 0) + (A->fnlong > 0 ? 1 : 0) + sc;
+  return (A->ntiles > 0 ? 1 : 0) + (A->nlong > 0 ? 1 : 0) + sc;
 }
 
 int64_t spmv_pieces(const spc5_matrix *A) { return A->flat ? A->fnpieces : A->npieces; }
@@ -1674,10 +1800,53 @@ spc5_status spmv_device_scratch(const spc5_matrix *A, const void *x, void *y, do
   return cuda_check(e, "spmv launch");
 }
 
+namespace {
+template <typename VT, typename AT>
+cudaError_t launch_scalars(const spc5_matrix *A, const AT *x, AT *y, double alpha,
+                           cudaStream_t s, AT *partial, uint32_t *sched) {
+  cudaError_t e = cudaSuccess;
+  if (A->sntiles > 0) {
+    int64_t blocks = (A->sntiles + kExpandWarps - 1) / kExpandWarps;
+    const int64_t resident = (int64_t)num_sms() * 16;
+    if (blocks > resident) blocks = resident;
+    k_spmv_scalars<VT, AT><<<(unsigned)blocks, 32 * kExpandWarps, 0, s>>>(
+        A->stiles, (int32_t)A->sntiles, sched, A->s_rowptr, A->s_colidx, (const VT *)A->s_vals,
+        x, y, partial, (AT)alpha);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  if (A->snlong > 0) {
+    int blocks = (int)std::min<int64_t>((A->snlong + 255) / 256, 4096);
+    k_fixup_add<AT><<<blocks, 256, 0, s>>>(A->snlong, A->slong_rows, A->slong_slots, partial, y,
+                                           (AT)alpha);
+    e = cudaGetLastError();
+  }
+  return e;
+}
+}  // namespace
+
+spc5_status spmv_scalars(const spc5_matrix *A, const void *x, void *y, double alpha,
+                         cudaStream_t s, void *partial, uint32_t *sched) {
+  if (!A->hybrid || A->nrows == 0 || alpha == 0.0) return SPC5_OK;
+  cudaError_t e;
+  if (A->value_dtype == SPC5_F64)
+    e = launch_scalars<double, double>(A, (const double *)x, (double *)y, alpha, s,
+                                       (double *)partial, sched);
+  else if (A->value_dtype == SPC5_F32)
+    e = launch_scalars<float, float>(A, (const float *)x, (float *)y, alpha, s,
+                                     (float *)partial, sched);
+  else
+    e = launch_scalars<uint16_t, float>(A, (const float *)x, (float *)y, alpha, s,
+                                        (float *)partial, sched);
+  return cuda_check(e, "scalar spmv launch");
+}
+
 spc5_status spmv_device(const spc5_matrix *A, const void *x, void *y, double alpha, double beta,
                         cudaStream_t s) {
-  return spmv_device_scratch(A, x, y, alpha, beta, s, A->flat ? A->fpartial : A->partial,
-                             A->fsched);
+  spc5_status st = spmv_device_scratch(A, x, y, alpha, beta, s,
+                                       A->flat ? A->fpartial : A->partial, A->fsched);
+  if (st != SPC5_OK || !A->hybrid) return st;
+  return spmv_scalars(A, x, y, alpha, s, A->spartial, A->fsched);
 }
 
 }  // namespace spc5

@@ -27,7 +27,7 @@ EXPORTS = ("spc5_convert_csr", "spc5_matrix_info", "spc5_export", "spc5_spmv", "
            "spc5_status_str", "spc5_last_error", "spc5_spmv_t", "spc5_values_grad",
            "spc5_set_values", "spc5_tune", "spc5_convert_tuned", "spc5_spmv_batched",
            "spc5_batch_create", "spc5_batch_run", "spc5_batch_destroy", "spc5_ircg",
-           "spc5_spmv_noalloc")
+           "spc5_spmv_noalloc", "spc5_convert_hybrid", "spc5_export_hybrid")
 
 
 class SPC5Error(RuntimeError):
@@ -47,7 +47,8 @@ class Info(ctypes.Structure):
                 ("ntiles", ctypes.c_int64), ("long_panels", ctypes.c_int64),
                 ("stages", ctypes.c_int32), ("consumers", ctypes.c_int32),
                 ("device_error", ctypes.c_uint32), ("tuned_us", ctypes.c_double),
-                ("flat", ctypes.c_int32), ("group_efficiency", ctypes.c_double)]
+                ("flat", ctypes.c_int32), ("group_efficiency", ctypes.c_double),
+                ("hybrid", ctypes.c_int32), ("nscalars", ctypes.c_int64)]
 
 
 class CGReport(ctypes.Structure):
@@ -103,6 +104,10 @@ def load(path: str | None = None):
         lib.spc5_ircg.restype = ci
         lib.spc5_spmv_noalloc.argtypes = [vp, vp, vp, dbl, dbl, vp]
         lib.spc5_spmv_noalloc.restype = ci
+        lib.spc5_convert_hybrid.argtypes = lib.spc5_convert_csr.argtypes
+        lib.spc5_convert_hybrid.restype = ci
+        lib.spc5_export_hybrid.argtypes = [vp] + [ctypes.POINTER(vp)] * 3
+        lib.spc5_export_hybrid.restype = ci
         lib.spc5_destroy.argtypes = [vp]
         for f in (lib.spc5_convert_csr, lib.spc5_matrix_info, lib.spc5_export, lib.spc5_spmv,
                   lib.spc5_destroy):
@@ -184,6 +189,25 @@ def spc5_convert_csr(nrows, ncols, nnz, rowptr, colidx, vals, vals_dtype=SPC5_F6
                                 vals_dtype, store_dtype, r, c, _stream_ptr(stream),
                                 ctypes.byref(out)))
     return Matrix(out.value)
+
+
+def spc5_convert_hybrid(nrows, ncols, nnz, rowptr, colidx, vals, vals_dtype=SPC5_F64,
+                        store_dtype=SPC5_F64, r=4, c=8, stream=None) -> Matrix:
+    """CSR -> hybrid beta(r,c): blocks of two or more values plus scalars."""
+    lib = load()
+    out = ctypes.c_void_p()
+    _check(lib.spc5_convert_hybrid(nrows, ncols, nnz, _ptr(rowptr), _ptr(colidx), _ptr(vals),
+                                   vals_dtype, store_dtype, r, c, _stream_ptr(stream),
+                                   ctypes.byref(out)))
+    return Matrix(out.value)
+
+
+def spc5_export_hybrid(A: Matrix) -> dict:
+    """Device pointers of a hybrid matrix's scalars (owned by A)."""
+    lib = load()
+    outs = [ctypes.c_void_p() for _ in range(3)]
+    _check(lib.spc5_export_hybrid(A.handle, *[ctypes.byref(o) for o in outs]))
+    return dict(zip(("s_rowptr", "s_colidx", "s_vals"), (o.value for o in outs)))
 
 
 def spc5_matrix_info(A: Matrix) -> dict:
@@ -332,7 +356,8 @@ def export_tensors(A: Matrix) -> dict:
     import torch
     info = spc5_matrix_info(A)
     p = spc5_export(A)
-    npan, nb, nnz = info["npanels"], info["nblocks"], info["nnz"]
+    npan, nb = info["npanels"], info["nblocks"]
+    nnz = info["nnz"] - info["nscalars"]  # values stored in blocks
     dev = torch.device("cuda", info["device"])
 
     def view(ptr, n, typestr):
@@ -341,7 +366,7 @@ def export_tensors(A: Matrix) -> dict:
                                                      "<f8": torch.float64}[typestr])
         return torch.as_tensor(_DeviceArray(ptr, (n,), typestr, A), device=dev)
 
-    return {"block_rowptr": view(p["block_rowptr"], npan + 1, "<i4"),
+    out = {"block_rowptr": view(p["block_rowptr"], npan + 1, "<i4"),
             "panel_vptr": view(p["panel_vptr"], npan + 1, "<i4"),
             "block_colidx": view(p["block_colidx"], nb, "<i4"),
             # packed mask words as raw little-endian bytes, mask_bytes per block
@@ -350,3 +375,12 @@ def export_tensors(A: Matrix) -> dict:
             "values": (view(p["values"], nnz, "<f8") if info["value_dtype"] == SPC5_F64 else
                        view(p["values"], nnz * (4 if info["value_dtype"] == SPC5_F32 else 2),
                             "|u1"))}
+    if info["hybrid"]:
+        h = spc5_export_hybrid(A)
+        ns = info["nscalars"]
+        out["s_rowptr"] = view(h["s_rowptr"], info["nrows"] + 1, "<i4")
+        out["s_colidx"] = view(h["s_colidx"], ns, "<i4")
+        out["s_vals"] = (view(h["s_vals"], ns, "<f8") if info["value_dtype"] == SPC5_F64 else
+                         view(h["s_vals"], ns * (4 if info["value_dtype"] == SPC5_F32 else 2),
+                              "|u1"))
+    return out
