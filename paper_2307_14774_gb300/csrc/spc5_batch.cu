@@ -21,6 +21,7 @@
 #include <vector>
 
 #include "spc5_internal.h"
+#include "spc5_reduce.cuh"
 
 namespace spc5 {
 namespace {
@@ -160,30 +161,42 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
-// Split panels: add each panel's pieces in order, for every row and RHS.
+// Split panels, one warp per panel: the panel's partials are W = r * k
+// values per slot (slot-major, row q and RHS j at q * k + j).  For W <= 32
+// lane t adds elements t, t + 32, ... (all of element t % W) and the lanes of
+// each element are then added; for W > 32 each lane adds its elements' slots.
 // lp_mat / lp_idx: matrix and local long-panel index of every global entry.
 template <int K, typename AT>
 __global__ void k_batch_fixup(const MatDesc *__restrict__ table,
                               const int32_t *__restrict__ lp_mat,
                               const int32_t *__restrict__ lp_idx, int64_t nlong_total, AT alpha,
                               AT beta) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nlong_total * 8 * K;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t e = i / (8 * K);
-    const int q = (int)((i / K) % 8);
-    const int rhs = (int)(i % K);
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; e < nlong_total;
+       e += nw) {
     const MatDesc d = table[lp_mat[e]];
-    if (q >= d.r) continue;
     const int l = lp_idx[e];
-    const int64_t row = (int64_t)d.long_panels[l] * d.r + q;
-    AT acc = 0;
-    for (int32_t s = d.long_slots[2 * l]; s < d.long_slots[2 * l + 1]; ++s)
-      acc += ((const AT *)d.partial)[((int64_t)s * d.r + q) * K + rhs];
-    if (row < d.nrows) {
-      AT *yr = (AT *)d.y + row * K + rhs;
-      AT out = alpha * acc;
-      if (beta != (AT)0) out = fma(beta, *yr, out);
-      *yr = out;
+    const int W = d.r * K;
+    const AT *p = (const AT *)d.partial;
+    const int64_t s0 = d.long_slots[2 * l];
+    const int64_t n = d.long_slots[2 * l + 1] - s0;
+    auto put = [&](int t, AT acc) {
+      const int64_t row = (int64_t)d.long_panels[l] * d.r + t / K;
+      if (row < d.nrows) {
+        AT *yr = (AT *)d.y + row * K + t % K;
+        AT out = alpha * acc;
+        if (beta != (AT)0) out = fma(beta, *yr, out);
+        *yr = out;
+      }
+    };
+    if (W <= 32) {
+      const int64_t first = s0 * W + lane, end = (s0 + n) * W;
+      AT acc = first < end ? strided_sum(p + first, (end - first + 31) / 32, 32) : (AT)0;
+      for (int o = 16; o >= W; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
+      if (lane < W) put(lane, acc);
+    } else {
+      for (int t = lane; t < W; t += 32) put(t, strided_sum(p + s0 * W + t, n, W));
     }
   }
 }
@@ -248,8 +261,7 @@ cudaError_t run_batch(const spc5_batch *B, double alpha, double beta, cudaStream
     if (e != cudaSuccess) return e;
   }
   if (B->nlong > 0) {
-    int64_t threads = B->nlong * 8 * K;
-    int blocks = (int)std::min<int64_t>((threads + 255) / 256, 8192);
+    const int blocks = (int)std::min<int64_t>((B->nlong + 7) / 8, (int64_t)sm_count() * 8);
     k_batch_fixup<K, AT><<<blocks, 256, 0, s>>>(B->table, B->lp_mat, B->lp_idx, B->nlong,
                                                 (AT)alpha, (AT)beta);
   }

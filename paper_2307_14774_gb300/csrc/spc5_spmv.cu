@@ -42,6 +42,7 @@
 
 #include "spc5_internal.h"
 #include "spc5_ptx.cuh"
+#include "spc5_reduce.cuh"
 
 namespace spc5 {
 namespace {
@@ -1186,17 +1187,22 @@ __global__ void __launch_bounds__(32 * kExpandWarps)
   }
 }
 
-// y[row] += alpha * (sum of the row's pieces, in order) for rows of scalars
-// cut into pieces.
+// y[row] += alpha * (sum of the row's pieces) for rows of scalars cut into
+// pieces, one warp per row as in k_fixup.
 template <typename AT>
 __global__ void k_fixup_add(int64_t nlong, const int32_t *long_rows, const int32_t *long_slots,
                             const AT *partial, AT *y, AT alpha) {
-  for (int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; l < nlong;
-       l += (int64_t)gridDim.x * blockDim.x) {
-    AT acc = 0;
-    for (int32_t s = long_slots[2 * l]; s < long_slots[2 * l + 1]; ++s) acc += partial[s];
-    const int64_t row = long_rows[l];
-    y[row] = fma(alpha, acc, y[row]);
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t l = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; l < nlong; l += nw) {
+    const int64_t first = (int64_t)long_slots[2 * l] + lane;
+    const int64_t end = long_slots[2 * l + 1];
+    AT acc = first < end ? strided_sum(partial + first, (end - first + 31) / 32, 32) : (AT)0;
+    acc = warp_sum(acc);
+    if (lane == 0) {
+      const int64_t row = long_rows[l];
+      y[row] = fma(alpha, acc, y[row]);
+    }
   }
 }
 
@@ -1516,19 +1522,24 @@ __global__ void __launch_bounds__(32 * 17, 1) k_spmv_staged(const StagedParams P
                              (size_t)(warp - 1) * kXsPerConsumer);
 }
 
-// y rows of panels that were cut into pieces: add the pieces in order.
+// y rows of panels that were cut into pieces.  One warp per split panel:
+// the panel's partials are R values per slot, slot-major, so lane j adds
+// elements j, j + 32, ... (all of row j % R) and the lanes of each row are
+// then added, a fixed order for every launch.
 template <int R, typename AT>
 __global__ void k_fixup(int64_t nlong, const int32_t *long_panels, const int32_t *long_slots,
                         const AT *partial, AT *y, Scale<AT> sc, int64_t nrows) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nlong * R;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t l = i / R;
-    const int q = (int)(i % R);
-    const int64_t row = (int64_t)long_panels[l] * R + q;
-    AT acc = 0;
-    for (int32_t s = long_slots[2 * l]; s < long_slots[2 * l + 1]; ++s)
-      acc += partial[(int64_t)s * R + q];
-    if (row < nrows) put_row(sc, y, row, acc);
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t l = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; l < nlong; l += nw) {
+    const int64_t first = (int64_t)long_slots[2 * l] * R + lane;
+    const int64_t end = (int64_t)long_slots[2 * l + 1] * R;
+    AT acc = first < end ? strided_sum(partial + first, (end - first + 31) / 32, 32) : (AT)0;
+    for (int o = 16; o >= R; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
+    if (lane < R) {
+      const int64_t row = (int64_t)long_panels[l] * R + lane;
+      if (row < nrows) put_row(sc, y, row, acc);
+    }
   }
 }
 
@@ -1541,6 +1552,11 @@ int num_sms() {
     if (n <= 0) n = 1;
   }
   return n;
+}
+
+// Blocks of 256 threads for a fixup over n split panels (one warp each).
+int fixup_blocks(int64_t n) {
+  return (int)std::min<int64_t>((n + 7) / 8, (int64_t)num_sms() * 8);
 }
 
 template <int R, int C, int BODY>
@@ -1593,8 +1609,7 @@ cudaError_t launch_staged(const spc5_matrix *A, const double *x, double *y, doub
     if (e != cudaSuccess) return e;
   }
   if (A->nlong > 0) {
-    int64_t threads = A->nlong * R;
-    int blocks = (int)std::min<int64_t>((threads + 255) / 256, 4096);
+    const int blocks = fixup_blocks(A->nlong);
     k_fixup<R, double><<<blocks, 256, 0, s>>>(A->nlong, A->long_panels, A->long_slots, partial,
                                               y, make_scale<double>(alpha, beta), A->nrows);
     e = cudaGetLastError();
@@ -1620,8 +1635,7 @@ cudaError_t launch_direct(const spc5_matrix *A, const AT *x, AT *y, double alpha
     if (e != cudaSuccess) return e;
   }
   if (A->nlong > 0) {
-    int64_t threads = A->nlong * R;
-    int fblocks = (int)std::min<int64_t>((threads + 255) / 256, 4096);
+    const int fblocks = fixup_blocks(A->nlong);
     k_fixup<R, AT><<<fblocks, 256, 0, s>>>(A->nlong, A->long_panels, A->long_slots, partial, y,
                                            make_scale<AT>(alpha, beta), A->nrows);
     e = cudaGetLastError();
@@ -1647,8 +1661,7 @@ cudaError_t launch_flat(const spc5_matrix *A, const AT *x, AT *y, double alpha, 
     if (e != cudaSuccess) return e;
   }
   if (A->fnlong > 0) {
-    int64_t threads = A->fnlong * R;
-    int fblocks = (int)std::min<int64_t>((threads + 255) / 256, 4096);
+    const int fblocks = fixup_blocks(A->fnlong);
     k_fixup<R, AT><<<fblocks, 256, 0, s>>>(A->fnlong, A->flong_panels, A->flong_slots, partial,
                                            y, make_scale<AT>(alpha, beta), A->nrows);
     e = cudaGetLastError();
@@ -1673,8 +1686,7 @@ cudaError_t launch_expand(const spc5_matrix *A, const AT *x, AT *y, double alpha
     if (e != cudaSuccess) return e;
   }
   if (A->fnlong > 0) {
-    int64_t threads = A->fnlong * R;
-    int fblocks = (int)std::min<int64_t>((threads + 255) / 256, 4096);
+    const int fblocks = fixup_blocks(A->fnlong);
     k_fixup<R, AT><<<fblocks, 256, 0, s>>>(A->fnlong, A->flong_panels, A->flong_slots, partial,
                                            y, make_scale<AT>(alpha, beta), A->nrows);
     e = cudaGetLastError();
@@ -1816,7 +1828,7 @@ cudaError_t launch_scalars(const spc5_matrix *A, const AT *x, AT *y, double alph
     if (e != cudaSuccess) return e;
   }
   if (A->snlong > 0) {
-    int blocks = (int)std::min<int64_t>((A->snlong + 255) / 256, 4096);
+    const int blocks = fixup_blocks(A->snlong);
     k_fixup_add<AT><<<blocks, 256, 0, s>>>(A->snlong, A->slong_rows, A->slong_slots, partial, y,
                                            (AT)alpha);
     e = cudaGetLastError();
