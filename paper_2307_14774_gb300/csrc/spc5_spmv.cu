@@ -907,6 +907,7 @@ __global__ void __launch_bounds__(32 * kExpandWarps, kExpandBlocksPerSM)
   int32_t *s_row = s_row_all[wid];
   int32_t *s_brp = s_brp_all[wid];
   constexpr int32_t kNoPanel = 0x7fffffff;
+  using MaskT = typename MaskType<R, C>::T;
 
   uint32_t grab = 0;
   if (lane == 0) grab = atomicAdd(&sched[0], 1u);
@@ -918,9 +919,14 @@ __global__ void __launch_bounds__(32 * kExpandWarps, kExpandBlocksPerSM)
     const int32_t np_t = piece ? 1 : cur.p1 - cur.p0;
     const int rows_t = np_t * R;
     const int32_t nv = cur.v1 - cur.v0;
-    {  // the tile's values are read in step 3: start bringing them to L1
+    {  // start bringing the tile's masks and block columns (step 2) and its
+       // values (step 3) to L2; shared memory leaves little room in L1
       constexpr int kLine = 128 / (int)sizeof(VT);
-      for (int32_t o = lane * kLine; o < nv; o += 32 * kLine) prefetch_l1(vals + cur.v0 + o);
+      constexpr int kLineM = 128 / (int)sizeof(MaskT);
+      const int32_t nbt = cur.b1 - cur.b0;
+      for (int32_t o = lane * kLine; o < nv; o += 32 * kLine) prefetch_l2(vals + cur.v0 + o);
+      for (int32_t o = lane * kLineM; o < nbt; o += 32 * kLineM) prefetch_l2(masks + cur.b0 + o);
+      for (int32_t o = lane * 32; o < nbt; o += 32 * 32) prefetch_l2(block_colidx + cur.b0 + o);
     }
     // tile rows' starts (computed when the plan was built)
     const int64_t rbase = piece ? (npanels + cur.slot) * R : (int64_t)cur.p0 * R;
