@@ -226,27 +226,29 @@ __device__ __forceinline__ AT row_stream(const MaskT *__restrict__ masks,
   uint32_t mq = 0u;
   int32_t off = 0, col = 0;
   AT acc = 0;
-  for (;;) {
-    const bool enter = (mq == 0u) && (b < nbp);
-    if (!__any_sync(kFull, enter || mq != 0u)) break;
-    if (enter) {
-      mq = (m1 >> qc) & cmask;
-      off = v + __popc(m1 & row_low);
-      v += __popc(m1);
-      col = c1;
-      ++b;
-      m1 = 0u;
-      if (b < nbp) {
-        m1 = (uint32_t)masks[bl + b];
-        c1 = block_colidx[bl + b];
-        prefetch_l1(vals + v);  // the next block's values, needed a few trips later
+  // two trips per vote: a trip of a lane whose row is done does nothing
+  while (__any_sync(kFull, mq != 0u || b < nbp)) {
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      if (mq == 0u && b < nbp) {
+        mq = (m1 >> qc) & cmask;
+        off = v + __popc(m1 & row_low);
+        v += __popc(m1);
+        col = c1;
+        ++b;
+        m1 = 0u;
+        if (b < nbp) {
+          m1 = (uint32_t)masks[bl + b];
+          c1 = block_colidx[bl + b];
+          prefetch_l1(vals + v);  // the next block's values, needed a few trips later
+        }
       }
-    }
-    if (mq) {
-      const int k = __ffs(mq) - 1;
-      acc = fma((AT)widen(vals[off]), __ldg(x + col + k), acc);
-      mq &= mq - 1u;
-      ++off;
+      if (mq) {
+        const int k = __ffs(mq) - 1;
+        acc = fma((AT)widen(vals[off]), __ldg(x + col + k), acc);
+        mq &= mq - 1u;
+        ++off;
+      }
     }
   }
   return acc;
@@ -530,23 +532,37 @@ __device__ __forceinline__ AT warp_sum(AT v) {
 
 
 // Adds the block's products to s[q] (q < R): values packed row by row,
-// ascending bit within a row (Algorithm 1's order).
+// ascending bit within a row (Algorithm 1's order).  One loop over all the
+// block's set bits, the row's sum chosen by selects, so a warp issues as
+// many FMA instructions as its fullest block has values (a loop per row
+// would issue, for every row, as many as the block fullest in that row).
 template <int R, int C, typename VT, typename AT>
 __device__ __forceinline__ void block_rows(AT (&s)[R], uint32_t m, const VT *__restrict__ vals,
                                            const AT *__restrict__ xp) {
-  const uint32_t cmask = (1u << C) - 1u;
+  constexpr int LOG2C = C == 8 ? 3 : 2;
   int o = 0;
-#pragma unroll
-  for (int q = 0; q < R; ++q) {
-    uint32_t mq = (m >> (q * C)) & cmask;
-    AT acc = s[q];
-    while (mq) {
-      const int k = __ffs(mq) - 1;
-      mq &= mq - 1u;
+  if (R == 1) {
+    AT acc = s[0];
+    while (m) {
+      const int k = __ffs(m) - 1;
+      m &= m - 1u;
       acc = fma((AT)widen(vals[o]), __ldg(xp + k), acc);
       ++o;
     }
-    s[q] = acc;
+    s[0] = acc;
+    return;
+  }
+  while (m) {
+    const int kf = __ffs(m) - 1;
+    m &= m - 1u;
+    const int q = kf >> LOG2C;
+    AT t = s[0];
+#pragma unroll
+    for (int qq = 1; qq < R; ++qq) t = (q == qq) ? s[qq] : t;
+    t = fma((AT)widen(vals[o]), __ldg(xp + (kf & (C - 1))), t);
+#pragma unroll
+    for (int qq = 0; qq < R; ++qq) s[qq] = (q == qq) ? t : s[qq];
+    ++o;
   }
 }
 
