@@ -681,9 +681,15 @@ __global__ void __launch_bounds__(kDirectThreads, FlatBlocksPerSM<R>::v)
         for (int i = 0; i < kFlatKB; ++i) ef |= (endbit(kFlatKB * lane + i) ? 1u : 0u) << i;
         // does the lane's first block start a panel?
         bool fresh = (lane == 0) ? !open : endbit(kFlatKB * lane - 1);
+        // lane 0 starts from the sums of the panel still open (0 if none),
+        // so carrying them costs no adds
         AT acc[R], head[R];
 #pragma unroll
-        for (int q = 0; q < R; ++q) acc[q] = head[q] = 0;
+        for (int q = 0; q < R; ++q) {
+          const AT cq = __shfl_sync(kFull, carry, q);
+          acc[q] = lane == 0 ? cq : (AT)0;
+          head[q] = 0;
+        }
         bool has_head = false;
         int32_t head_pid = 0;
 #pragma unroll
@@ -709,33 +715,29 @@ __global__ void __launch_bounds__(kDirectThreads, FlatBlocksPerSM<R>::v)
             fresh = true;
           }
         }
-        // lane 0's partial continues the open panel when it ends no panel
-#pragma unroll
-        for (int q = 0; q < R; ++q) {
-          const AT cq = __shfl_sync(kFull, carry, q);
-          if (lane == 0 && ef == 0u) acc[q] += cq;
-        }
         // segmented scan of the lanes' last partial sums: lane adds lane - o
-        // when no lane in (lane - o, lane] ends a panel
+        // when no lane in (lane - o, lane] ends a panel; once no lane can,
+        // no longer step can either
         const uint32_t endl = __ballot_sync(kFull, ef != 0u);
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
           const bool same =
               lane >= o && ((endl >> (lane - o + 1)) & ((1u << o) - 1u)) == 0u;
+          if (!__any_sync(kFull, same)) break;
 #pragma unroll
           for (int q = 0; q < R; ++q) {
             const AT tq = __shfl_up_sync(kFull, acc[q], o);
             if (same) acc[q] += tq;
           }
         }
-        // panels cut between lanes: the head plus the scanned partial before it
+        // panels cut between lanes: the head plus the scanned partial before
+        // it (lane 0's head already holds the open panel's sums)
 #pragma unroll
         for (int q = 0; q < R; ++q) {
           const AT cin = __shfl_up_sync(kFull, acc[q], 1);
-          const AT cq = __shfl_sync(kFull, carry, q);
           if (has_head) {
             const int64_t row = (int64_t)head_pid * R + q;
-            if (row < nrows) put_row(sc, y, row, head[q] + (lane == 0 ? cq : cin));
+            if (row < nrows) put_row(sc, y, row, lane == 0 ? head[q] : head[q] + cin);
           }
         }
         // the panel open at the end of the round
@@ -1077,10 +1079,12 @@ __global__ void __launch_bounds__(32 * kExpandWarps, kExpandBlocksPerSM)
       // rows cut between lanes: segmented scan of the lanes' last partial sums
       AT sv = (tail_row >= 0) ? acc : (AT)0;
 #pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
+      for (int o = 1; o < 32; o <<= 1) {  // tail rows ascend with the lane
         const AT tsv = __shfl_up_sync(kFull, sv, o);
         const int kr = __shfl_up_sync(kFull, tail_row, o);
-        if (lane >= o && kr == tail_row && tail_row >= 0) sv += tsv;
+        const bool add = lane >= o && kr == tail_row && tail_row >= 0;
+        if (!__any_sync(kFull, add)) break;
+        if (add) sv += tsv;
       }
       const AT cin = __shfl_up_sync(kFull, sv, 1);
       if (head_row >= 0) emit(head_row, head_val + cin);
@@ -1190,10 +1194,12 @@ __global__ void __launch_bounds__(32 * kExpandWarps)
     }
     AT sv = (tail_row >= 0) ? acc : (AT)0;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
+    for (int o = 1; o < 32; o <<= 1) {  // tail rows ascend with the lane
       const AT tsv = __shfl_up_sync(kFull, sv, o);
       const int kr = __shfl_up_sync(kFull, tail_row, o);
-      if (lane >= o && kr == tail_row && tail_row >= 0) sv += tsv;
+      const bool add = lane >= o && kr == tail_row && tail_row >= 0;
+      if (!__any_sync(kFull, add)) break;
+      if (add) sv += tsv;
     }
     const AT cin = __shfl_up_sync(kFull, sv, 1);
     if (head_row >= 0) emit(head_row, head_val + cin);
