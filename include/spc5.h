@@ -84,7 +84,7 @@ typedef struct {
                               1 blocks dealt to lanes evenly (block-balanced plan);
                               2 each tile's values split evenly over the lanes (expanded) */
   double group_efficiency; /* busy share of the row-group plan's block slots; below 0.7 the
-                              converter picks plan 1 for r <= 4 and plan 2 for r = 8 */
+                              converter picks plan 1 */
   int32_t hybrid;          /* 1 for a matrix from spc5_convert_hybrid */
   int64_t nscalars;        /* hybrid: single-value blocks stored as scalars (nnz counts them;
                               nblocks and filling describe the remaining blocks) */

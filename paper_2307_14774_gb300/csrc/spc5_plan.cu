@@ -522,11 +522,9 @@ spc5_status plan_flat(spc5_matrix *A, const int32_t *boff, cudaStream_t s,
   // Which plan the SpMV uses.  The staged kernel reads its tiles as
   // contiguous panel ranges, so the other plans are for the direct kernels.
   // Default: row groups unless they would keep less than 70% of their block
-  // slots busy; then the block-balanced plan for blocks of up to 4 rows and
-  // the expanded plan for blocks of 8 rows (a lane of the block-balanced
-  // kernel keeps r row sums and picks one by selects for every value, which
-  // costs registers and issue slots at r = 8).
-  const int dflt = A->group_efficiency < 0.7 ? (A->r <= 4 ? 1 : 2) : 0;
+  // slots busy; then the block-balanced plan (the expanded plan measured
+  // slower on every block shape; spc5_tune still tries it).
+  const int dflt = A->group_efficiency < 0.7 ? 1 : 0;
   int flat = opt.flat >= 0 ? opt.flat : env_int("SPC5_FLAT", dflt);
   if (flat < 0 || flat > 2) flat = dflt;
   A->flat = A->kernel == 0 ? flat : 0;

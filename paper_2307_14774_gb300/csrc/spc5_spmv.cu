@@ -692,10 +692,9 @@ __global__ void __launch_bounds__(kDirectThreads, FlatBlocksPerSM<R>::v)
         }
         bool has_head = false;
         int32_t head_pid = 0;
-#pragma unroll
-        for (int i = 0; i < kFlatKB; ++i) {
-          block_rows<R, C>(acc, m[i], vals + off, x + cb[i]);
-          off += __popc(m[i]);
+        // block i was the lane's last block of a panel: write the panel's rows
+        // if it started here, else keep them as the head for the scan
+        auto end_block = [&](int i) {
           if ((ef >> i) & 1u) {
             const int64_t p = pid[kFlatKB * lane + i];
             if (fresh) {
@@ -714,6 +713,49 @@ __global__ void __launch_bounds__(kDirectThreads, FlatBlocksPerSM<R>::v)
             for (int q = 0; q < R; ++q) acc[q] = 0;
             fresh = true;
           }
+        };
+        if (R <= 2) {
+#pragma unroll
+          for (int i = 0; i < kFlatKB; ++i) {
+            block_rows<R, C>(acc, m[i], vals + off, x + cb[i]);
+            off += __popc(m[i]);
+            end_block(i);
+          }
+        } else {
+          // one FMA per trip over all the set bits of the lane's blocks, so
+          // a warp issues as many FMA instructions as its fullest lane has
+          // values (blocks hold at least one value; the round's padding
+          // blocks hold none and end no panel); for r <= 2 the loop per
+          // block measured faster
+          const int trips = __reduce_max_sync(kFull, cnt);
+          int i = 0;
+          uint32_t mc = m[0];
+          int32_t cc = cb[0];
+          for (int t = 0; t < trips; ++t) {
+            while (mc == 0u && i < kFlatKB - 1) {
+              end_block(i);
+              ++i;
+#pragma unroll
+              for (int j = 1; j < kFlatKB; ++j) {
+                mc = (i == j) ? m[j] : mc;
+                cc = (i == j) ? cb[j] : cc;
+              }
+            }
+            if (mc) {
+              constexpr int LOG2C = C == 8 ? 3 : 2;
+              const int kf = __ffs(mc) - 1;
+              mc &= mc - 1u;
+              const int q = kf >> LOG2C;
+              AT tq = acc[0];
+#pragma unroll
+              for (int qq = 1; qq < R; ++qq) tq = (q == qq) ? acc[qq] : tq;
+              tq = fma((AT)widen(vals[off]), __ldg(x + cc + (kf & (C - 1))), tq);
+#pragma unroll
+              for (int qq = 0; qq < R; ++qq) acc[qq] = (q == qq) ? tq : acc[qq];
+              ++off;
+            }
+          }
+          end_block(i);
         }
         // segmented scan of the lanes' last partial sums: lane adds lane - o
         // when no lane in (lane - o, lane] ends a panel; once no lane can,

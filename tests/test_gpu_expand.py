@@ -96,16 +96,13 @@ def test_skewed_plans_integer_exact(monkeypatch, r, c, plan):
 
 
 def test_skewed_plans_default_choice():
-    """The converter picks the block-balanced plan for skewed rows in blocks of
-    up to 4 rows, the expanded plan for skewed rows in blocks of 8 rows, and
-    keeps row groups for a stencil."""
+    """The converter picks the block-balanced plan for skewed rows and keeps
+    row groups for a stencil."""
     torch_cuda()
-    skewed = convert(synth.powerlaw(60_000, seed=3), 1, 8).info()
-    assert skewed["group_efficiency"] < 0.7 and skewed["flat"] == 1
-    wide = convert(synth.powerlaw(60_000, seed=3), 4, 8).info()
-    assert wide["group_efficiency"] >= 0.7 or wide["flat"] == 1
-    tall = convert(synth.powerlaw(60_000, seed=3), 8, 4).info()
-    assert tall["group_efficiency"] >= 0.7 or tall["flat"] == 2
+    for r, c in BETAS:
+        skewed = convert(synth.powerlaw(60_000, seed=3), r, c).info()
+        assert skewed["group_efficiency"] >= 0.7 or skewed["flat"] == 1
+    assert convert(synth.powerlaw(60_000, seed=3), 1, 8).info()["group_efficiency"] < 0.7
     regular = convert(synth.stencil27(20, 20, 20, values="normal"), 4, 8).info()
     assert regular["group_efficiency"] >= 0.7 and regular["flat"] == 0
 
