@@ -447,7 +447,8 @@ def grad_section(torch, spc5, synth, log, reps=10):
 def batched_section(torch, spc5, synth, stream, log, nmat=256, reps=10):
     """256 matrices of uneven size (n log-uniform in [1e3, 2e5]; 5-point,
     27-point and power-law generators in turn), FP32 values, each converted
-    into the block shape and mapping the autotuner picks; for every k in
+    into the block shape and mapping whose row-group plan (the plan the
+    batched kernel runs) the autotuner finds fastest; for every k in
     {1, 4, 8, 16}: one persistent batched launch captured in a CUDA graph,
     timed by replaying the graph."""
     import math
@@ -468,8 +469,8 @@ def batched_section(torch, spc5, synth, stream, log, nmat=256, reps=10):
         else:
             A = synth.powerlaw(int(n), seed=100 + i)
         dev = [torch.from_numpy(a).cuda() for a in (A.rowptr, A.colidx, A.vals)]
-        M = spc5.spc5_convert_tuned(A.nrows, A.ncols, A.nnz, *dev, store_dtype=spc5.SPC5_F32,
-                                    iters=3, stream=stream)
+        M = spc5.spc5_convert_tuned_ex(A.nrows, A.ncols, A.nnz, *dev, store_dtype=spc5.SPC5_F32,
+                                       iters=3, rows_plan=True, stream=stream)
         info = M.info()
         key = f"{info['r']}x{info['c']}/G{info['lanes_per_row']}"
         shapes[key] = shapes.get(key, 0) + 1

@@ -88,6 +88,9 @@ typedef struct {
   int32_t hybrid;          /* 1 for a matrix from spc5_convert_hybrid */
   int64_t nscalars;        /* hybrid: single-value blocks stored as scalars (nnz counts them;
                               nblocks and filling describe the remaining blocks) */
+  double tuned_rows_us;    /* SpMV time of the fastest row-group plan spc5_tune tried (the
+                              plan of the batched, transposed and gradient kernels), 0 if
+                              untuned */
 } spc5_info;
 
 /*
@@ -252,6 +255,19 @@ spc5_status spc5_convert_tuned(int64_t nrows, int64_t ncols, int64_t nnz, const 
                                const int32_t *colidx, const void *vals, spc5_dtype vals_dtype,
                                spc5_dtype store_dtype, const int *shapes, int nshapes, int iters,
                                void *stream, spc5_matrix **out);
+
+/*
+ * spc5_convert_tuned_ex -- spc5_convert_tuned with the ranking chosen by
+ * `rows_plan`: 0 ranks the shapes by their fastest SpMV plan (as
+ * spc5_convert_tuned); nonzero ranks them by their fastest row-group plan,
+ * the plan that spc5_spmv_batched, spc5_spmv_t and spc5_values_grad run
+ * (spc5_info.tuned_rows_us).  The matrix returned is tuned as by spc5_tune.
+ */
+spc5_status spc5_convert_tuned_ex(int64_t nrows, int64_t ncols, int64_t nnz,
+                                  const int32_t *rowptr, const int32_t *colidx, const void *vals,
+                                  spc5_dtype vals_dtype, spc5_dtype store_dtype, const int *shapes,
+                                  int nshapes, int iters, int rows_plan, void *stream,
+                                  spc5_matrix **out);
 
 /*
  * spc5_spmv_batched -- Y[m] = A[m] X[m] for m < nmat in one launch, with k

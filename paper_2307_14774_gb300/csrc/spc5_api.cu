@@ -242,6 +242,7 @@ spc5_status spc5_matrix_info(const spc5_matrix *A, spc5_info *info) {
   }
   info->device_error = derr;
   info->tuned_us = A->tuned_us;
+  info->tuned_rows_us = A->tuned_rows_us;
   info->flat = A->flat;
   info->group_efficiency = A->group_efficiency;
   info->hybrid = A->hybrid;

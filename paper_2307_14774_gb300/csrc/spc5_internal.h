@@ -73,6 +73,7 @@ struct spc5_matrix {
                                     // bits (else set-bit loop), bit 1 = x staged in smem
   int kernel = 0;                   // 0: direct tile kernel, 1: staged tile kernel
   double tuned_us = 0.0;            // SpMV time of the plan chosen by spc5_tune (0 = untuned)
+  double tuned_rows_us = 0.0;       // SpMV time of the best row-group plan it found
   uint32_t *dev_error = nullptr;    // set by kernels on a timed-out wait
 
   // Block-balanced (flat = 1) or expanded (flat = 2) plan, used by the SpMV

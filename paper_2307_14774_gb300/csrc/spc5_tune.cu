@@ -10,7 +10,8 @@
 //                       expanded plan for one
 //                       converted matrix, keeping the fastest plan;
 //   spc5_convert_tuned  every requested beta(r,c), each tuned, keeping the
-//                       fastest matrix.
+//                       fastest matrix (spc5_convert_tuned_ex: optionally
+//                       ranked by the row-group plan the batched kernel runs).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -105,6 +106,7 @@ spc5_status tune(spc5_matrix *A, const void *x, void *y, int iters, cudaStream_t
     if (st != SPC5_OK) return st;
   }
   A->tuned_us = best;
+  A->tuned_rows_us = best_rows;
   return SPC5_OK;
 }
 
@@ -128,6 +130,16 @@ extern "C" spc5_status spc5_convert_tuned(int64_t nrows, int64_t ncols, int64_t 
                                           const void *vals, spc5_dtype vals_dtype,
                                           spc5_dtype store_dtype, const int *shapes, int nshapes,
                                           int iters, void *stream, spc5_matrix **out) {
+  return spc5_convert_tuned_ex(nrows, ncols, nnz, rowptr, colidx, vals, vals_dtype, store_dtype,
+                               shapes, nshapes, iters, 0, stream, out);
+}
+
+extern "C" spc5_status spc5_convert_tuned_ex(int64_t nrows, int64_t ncols, int64_t nnz,
+                                             const int32_t *rowptr, const int32_t *colidx,
+                                             const void *vals, spc5_dtype vals_dtype,
+                                             spc5_dtype store_dtype, const int *shapes,
+                                             int nshapes, int iters, int rows_plan, void *stream,
+                                             spc5_matrix **out) {
   static const int kAll[12] = {1, 8, 2, 4, 2, 8, 4, 4, 4, 8, 8, 4};
   if (!out || iters < 1 || (shapes && nshapes < 1)) {
     set_error("invalid argument");
@@ -159,7 +171,8 @@ extern "C" spc5_status spc5_convert_tuned(int64_t nrows, int64_t ncols, int64_t 
       spc5_destroy(A);
       break;
     }
-    if (!best || A->tuned_us < best->tuned_us) {
+    const double t = rows_plan ? A->tuned_rows_us : A->tuned_us;
+    if (!best || t < (rows_plan ? best->tuned_rows_us : best->tuned_us)) {
       if (best) spc5_destroy(best);
       best = A;
     } else {

@@ -25,7 +25,8 @@ SUPPORTED_RC = ((1, 8), (2, 4), (2, 8), (4, 4), (4, 8), (8, 4))
 # Exported symbols declared in include/spc5.h.
 EXPORTS = ("spc5_convert_csr", "spc5_matrix_info", "spc5_export", "spc5_spmv", "spc5_destroy",
            "spc5_status_str", "spc5_last_error", "spc5_spmv_t", "spc5_values_grad",
-           "spc5_set_values", "spc5_tune", "spc5_convert_tuned", "spc5_spmv_batched",
+           "spc5_set_values", "spc5_tune", "spc5_convert_tuned", "spc5_convert_tuned_ex",
+           "spc5_spmv_batched",
            "spc5_batch_create", "spc5_batch_run", "spc5_batch_destroy", "spc5_ircg",
            "spc5_spmv_noalloc", "spc5_convert_hybrid", "spc5_export_hybrid")
 
@@ -48,7 +49,8 @@ class Info(ctypes.Structure):
                 ("stages", ctypes.c_int32), ("consumers", ctypes.c_int32),
                 ("device_error", ctypes.c_uint32), ("tuned_us", ctypes.c_double),
                 ("flat", ctypes.c_int32), ("group_efficiency", ctypes.c_double),
-                ("hybrid", ctypes.c_int32), ("nscalars", ctypes.c_int64)]
+                ("hybrid", ctypes.c_int32), ("nscalars", ctypes.c_int64),
+                ("tuned_rows_us", ctypes.c_double)]
 
 
 class CGReport(ctypes.Structure):
@@ -92,6 +94,10 @@ def load(path: str | None = None):
                                            ctypes.POINTER(ctypes.c_int), ci, ci, vp,
                                            ctypes.POINTER(vp)]
         lib.spc5_convert_tuned.restype = ci
+        lib.spc5_convert_tuned_ex.argtypes = [i64, i64, i64, vp, vp, vp, ci, ci,
+                                              ctypes.POINTER(ctypes.c_int), ci, ci, ci, vp,
+                                              ctypes.POINTER(vp)]
+        lib.spc5_convert_tuned_ex.restype = ci
         pvp = ctypes.POINTER(vp)
         lib.spc5_spmv_batched.argtypes = [ci, pvp, pvp, pvp, ci, vp]
         lib.spc5_batch_create.argtypes = [ci, pvp, pvp, pvp, ci, vp, pvp]
@@ -259,15 +265,33 @@ def spc5_convert_tuned(nrows, ncols, nnz, rowptr, colidx, vals, vals_dtype=SPC5_
     """Convert into each block shape (default: all six), tune each, keep the fastest."""
     lib = load()
     out = ctypes.c_void_p()
-    if shapes is None:
-        arr, n = None, 0
-    else:
-        flat = [v for rc in shapes for v in rc]
-        arr, n = (ctypes.c_int * len(flat))(*flat), len(shapes)
+    arr, n = _shape_array(shapes)
     _check(lib.spc5_convert_tuned(nrows, ncols, nnz, _ptr(rowptr), _ptr(colidx), _ptr(vals),
                                   vals_dtype, store_dtype, arr, n, int(iters),
                                   _stream_ptr(stream), ctypes.byref(out)))
     return Matrix(out.value)
+
+
+def spc5_convert_tuned_ex(nrows, ncols, nnz, rowptr, colidx, vals, vals_dtype=SPC5_F64,
+                          store_dtype=SPC5_F64, shapes=None, iters: int = 5,
+                          rows_plan: bool = False, stream=None) -> Matrix:
+    """spc5_convert_tuned; rows_plan ranks the shapes by their fastest
+    row-group plan (the batched, transposed and gradient kernels' plan)."""
+    lib = load()
+    out = ctypes.c_void_p()
+    arr, n = _shape_array(shapes)
+    _check(lib.spc5_convert_tuned_ex(nrows, ncols, nnz, _ptr(rowptr), _ptr(colidx), _ptr(vals),
+                                     vals_dtype, store_dtype, arr, n, int(iters),
+                                     1 if rows_plan else 0, _stream_ptr(stream),
+                                     ctypes.byref(out)))
+    return Matrix(out.value)
+
+
+def _shape_array(shapes):
+    if shapes is None:
+        return None, 0
+    flat = [v for rc in shapes for v in rc]
+    return (ctypes.c_int * len(flat))(*flat), len(shapes)
 
 
 def _ptr_array(items):

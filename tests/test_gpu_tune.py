@@ -51,3 +51,32 @@ def test_convert_tuned_picks_a_valid_shape(dtype):
         spc5.spc5_spmv(M, dxx, dyy)
         torch.cuda.synchronize()
         assert_within_tol(dyy.cpu().numpy().astype(np.float64), y_ref, scale, tol=2e-6)
+
+
+def test_convert_tuned_ex_ranks_by_the_row_group_plan():
+    """rows_plan ranks the shapes by their fastest row-group plan: the shape
+    kept has the smallest tuned_rows_us among the shapes, each tuned alone
+    (timings repeat within 25 %), and it serves the batched kernel."""
+    torch = torch_cuda()
+    A = synth.powerlaw(80_000, seed=21)
+    rp, ci, vv = to_device(A)
+    shapes = [(1, 8), (4, 4), (8, 4)]
+    M = spc5.spc5_convert_tuned_ex(A.nrows, A.ncols, A.nnz, rp, ci, vv, shapes=shapes, iters=5,
+                                   rows_plan=True)
+    info = M.info()
+    assert (info["r"], info["c"]) in shapes
+    assert 0 < info["tuned_rows_us"] and 0 < info["tuned_us"] <= info["tuned_rows_us"]
+    x = synth.vector_uniform(A.ncols, seed=5)
+    dx = torch.from_numpy(x).cuda()
+    dy = torch.empty(A.nrows, dtype=torch.float64, device="cuda")
+    alone = {}
+    for r, c in shapes:
+        Ms = convert(A, r, c)
+        alone[(r, c)] = spc5.spc5_tune(Ms, dx, dy, iters=5)["tuned_rows_us"]
+    assert info["tuned_rows_us"] <= 1.25 * min(alone.values())
+    y_ref, scale = oracle.csr_spmv(A, x)
+    assert_within_tol(spmv(M, x), y_ref, scale)
+    Y = torch.full((A.nrows, 1), float("nan"), dtype=torch.float64, device="cuda")
+    spc5.spc5_spmv_batched([M], [dx.reshape(-1, 1)], [Y], 1)
+    torch.cuda.synchronize()
+    assert_within_tol(Y.cpu().numpy()[:, 0], y_ref, scale)
