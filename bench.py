@@ -94,6 +94,13 @@ VALUE_BYTES = {0: 8, 1: 4, 2: 2}  # FP64, FP32, BF16 storage
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 
 
+def plan_label(info):
+    """The SpMV's work mapping: blocks (block-balanced), values (value-balanced
+    block rounds), expanded, or rows/G<lanes per row> (row groups)."""
+    return ({1: "blocks", 2: "expanded", 3: "values"}.get(info["flat"])
+            or f"rows/G{info['lanes_per_row']}")
+
+
 def algorithmic_bytes(info: dict) -> int:
     """Bytes an SpMV must move: values + block column indices + masks + panel
     pointers (block_rowptr and panel value offsets) + x + y.  FP64 matrices
@@ -306,8 +313,7 @@ def precision_section(hosts, torch, spc5, stream, hbm, case_rows, log, reps=10, 
                              "frac": round(b / (us * 1e-6) / 1e9 / hbm, 3),
                              "speedup_vs_fp64": round(ref / us, 2) if ref else None,
                              "tol": PRECISION_TOL[dt], "max_err_over_tol": round(ratio, 4),
-                             "plan": ({1: "blocks", 2: "expanded"}.get(info["flat"])
-                                      or f"rows/G{info['lanes_per_row']}")})
+                             "plan": plan_label(info)})
                 del M
         del dev, dabs, flush
         torch.cuda.synchronize()
@@ -355,8 +361,7 @@ def hybrid_section(hosts, torch, spc5, stream, hbm, case_rows, log, reps=10, tun
                          "frac": round(b / (us * 1e-6) / 1e9 / hbm, 3),
                          "scalar_share": round(ns / A.nnz, 3),
                          "speedup_vs_blocks": round(ref / us, 2) if ref else None,
-                         "plan": ({1: "blocks", 2: "expanded"}.get(info["flat"])
-                                  or f"rows/G{info['lanes_per_row']}")})
+                         "plan": plan_label(info)})
             del M
         del dev
         torch.cuda.synchronize()
@@ -626,8 +631,7 @@ def run_native(args):
                           "fp64_frac": round(gf / (FP64_PEAK_TFLOPS * 1e3), 3),
                           "bound": "alu" if t_fp64 > t_hbm else "hbm",
                           "floor_us": round(max(t_hbm, t_fp64), 2),
-                          "plan": ({1: "blocks", 2: "expanded"}.get(cs["info"]["flat"])
-                                   or f"rows/G{cs['info']['lanes_per_row']}"),
+                          "plan": plan_label(cs["info"]),
                           "convert_ms": round(cs["convert_s"] * 1e3, 2)})
 
     result = {

@@ -82,9 +82,11 @@ typedef struct {
   double tuned_us;         /* SpMV time of the plan chosen by spc5_tune, 0 if untuned */
   int32_t flat;            /* work mapping of the SpMV: 0 lanes own rows (row-group plan);
                               1 blocks dealt to lanes evenly (block-balanced plan);
-                              2 each tile's values split evenly over the lanes (expanded) */
+                              2 each tile's values split evenly over the lanes (expanded);
+                              3 block-balanced tiles, each round's values split evenly over
+                              the lanes (value-balanced) */
   double group_efficiency; /* busy share of the row-group plan's block slots; below 0.7 the
-                              converter picks plan 1 */
+                              converter picks plan 3 for r >= 4 and plan 1 for r <= 2 */
   int32_t hybrid;          /* 1 for a matrix from spc5_convert_hybrid */
   int64_t nscalars;        /* hybrid: single-value blocks stored as scalars (nnz counts them;
                               nblocks and filling describe the remaining blocks) */

@@ -522,11 +522,14 @@ spc5_status plan_flat(spc5_matrix *A, const int32_t *boff, cudaStream_t s,
   // Which plan the SpMV uses.  The staged kernel reads its tiles as
   // contiguous panel ranges, so the other plans are for the direct kernels.
   // Default: row groups unless they would keep less than 70% of their block
-  // slots busy; then the block-balanced plan (the expanded plan measured
-  // slower on every block shape; spc5_tune still tries it).
-  const int dflt = A->group_efficiency < 0.7 ? 1 : 0;
+  // slots busy; then the block-balanced plan, with values split evenly over
+  // the lanes for r >= 4 (plan 3: the cross-lane scan of r sums is paid per
+  // 256 blocks) and four blocks per lane for r <= 2 (plan 1, cheaper per
+  // value there).  The expanded plan measured slower on every block shape;
+  // spc5_tune still tries it.
+  const int dflt = A->group_efficiency < 0.7 ? (A->r >= 4 ? 3 : 1) : 0;
   int flat = opt.flat >= 0 ? opt.flat : env_int("SPC5_FLAT", dflt);
-  if (flat < 0 || flat > 2) flat = dflt;
+  if (flat < 0 || flat > 3) flat = dflt;
   A->flat = A->kernel == 0 ? flat : 0;
   const bool expanded = A->flat == 2;
 

@@ -566,6 +566,63 @@ __device__ __forceinline__ void block_rows(AT (&s)[R], uint32_t m, const VT *__r
   }
 }
 
+// A piece of a long panel (block-balanced plans): the lanes keep private row
+// sums over all rounds of four blocks per lane, reduce them with shuffles
+// and write them to the partial buffer for the fixup kernel.
+template <int R, int C, typename VT, typename AT>
+__device__ __forceinline__ void flat_piece(const Tile &cur, int lane,
+                                           const int32_t *__restrict__ block_colidx,
+                                           const typename MaskType<R, C>::T *__restrict__ masks,
+                                           const VT *__restrict__ vals,
+                                           const AT *__restrict__ x, AT *__restrict__ partial) {
+  int32_t v = cur.v0;
+  AT s[R];
+#pragma unroll
+  for (int q = 0; q < R; ++q) s[q] = 0;
+  for (int32_t base = cur.b0; base < cur.b1; base += kFlatRound) {
+    uint32_t m[kFlatKB];
+    int32_t cb[kFlatKB];
+    int cnt = 0;
+#pragma unroll
+    for (int i = 0; i < kFlatKB; ++i) {
+      const int32_t b = base + kFlatKB * lane + i;
+      const bool ok = b < cur.b1;
+      m[i] = ok ? (uint32_t)masks[b] : 0u;
+      cb[i] = ok ? block_colidx[b] : 0;
+      cnt += __popc(m[i]);
+    }
+    int total;
+    int32_t off = v + warp_excl_scan(cnt, lane, &total);
+    v += total;
+#pragma unroll
+    for (int i = 0; i < kFlatKB; ++i) {
+      block_rows<R, C>(s, m[i], vals + off, x + cb[i]);
+      off += __popc(m[i]);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < R; ++q) {
+    const AT tot = warp_sum(s[q]);
+    if (lane == q) partial[(int64_t)cur.slot * R + q] = tot;
+  }
+}
+
+// Rows of a tile's empty panels (block-balanced plans).
+template <int R, typename AT>
+__device__ __forceinline__ void flat_empty_rows(const Tile &cur, int lane,
+                                                const int32_t *__restrict__ brp, AT *y,
+                                                const Scale<AT> &sc, int64_t nrows) {
+  for (int32_t p = cur.p0 + lane; p < cur.p1; p += 32) {
+    if (brp[p] == brp[p + 1]) {
+#pragma unroll
+      for (int q = 0; q < R; ++q) {
+        const int64_t row = (int64_t)p * R + q;
+        if (row < nrows) put_empty_row(sc, y, row);
+      }
+    }
+  }
+}
+
 template <int R>
 struct FlatBlocksPerSM {  // registers grow with the r row sums a lane keeps
   static constexpr int v = R == 1 ? 6 : (R == 2 ? 5 : (R == 4 ? 4 : 3));
@@ -589,46 +646,9 @@ __global__ void __launch_bounds__(kDirectThreads, FlatBlocksPerSM<R>::v)
     const Tile cur = tiles[t];
     int32_t v = cur.v0;
     if (cur.mode & kPartial) {
-      AT s[R];
-#pragma unroll
-      for (int q = 0; q < R; ++q) s[q] = 0;
-      for (int32_t base = cur.b0; base < cur.b1; base += kFlatRound) {
-        uint32_t m[kFlatKB];
-        int32_t cb[kFlatKB];
-        int cnt = 0;
-#pragma unroll
-        for (int i = 0; i < kFlatKB; ++i) {
-          const int32_t b = base + kFlatKB * lane + i;
-          const bool ok = b < cur.b1;
-          m[i] = ok ? (uint32_t)masks[b] : 0u;
-          cb[i] = ok ? block_colidx[b] : 0;
-          cnt += __popc(m[i]);
-        }
-        int total;
-        int32_t off = v + warp_excl_scan(cnt, lane, &total);
-        v += total;
-#pragma unroll
-        for (int i = 0; i < kFlatKB; ++i) {
-          block_rows<R, C>(s, m[i], vals + off, x + cb[i]);
-          off += __popc(m[i]);
-        }
-      }
-#pragma unroll
-      for (int q = 0; q < R; ++q) {
-        const AT tot = warp_sum(s[q]);
-        if (lane == q) partial[(int64_t)cur.slot * R + q] = tot;
-      }
+      flat_piece<R, C>(cur, lane, block_colidx, masks, vals, x, partial);
     } else {
-      // rows of the tile's empty panels
-      for (int32_t p = cur.p0 + lane; p < cur.p1; p += 32) {
-        if (brp[p] == brp[p + 1]) {
-#pragma unroll
-          for (int q = 0; q < R; ++q) {
-            const int64_t row = (int64_t)p * R + q;
-            if (row < nrows) put_empty_row(sc, y, row);
-          }
-        }
-      }
+      flat_empty_rows<R>(cur, lane, brp, y, sc, nrows);
       AT carry = 0;       // lane q < R: row q's sum of the panel still open
       bool open = false;  // a panel continues from the previous round
       int32_t pcur = cur.p0;
@@ -791,6 +811,220 @@ __global__ void __launch_bounds__(kDirectThreads, FlatBlocksPerSM<R>::v)
           const AT sl = __shfl_sync(kFull, acc[q], ll);
           if (lane == q) carry = open ? sl : (AT)0;
         }
+        __syncwarp();
+      }
+    }
+    t = (int32_t)__shfl_sync(kFull, grab, 0);
+  }
+  // every warp has made its last grab: the last one to finish resets the counters
+  if (lane == 0) {
+    const uint32_t nwarps = gridDim.x * (blockDim.x >> 5);
+    if (atomicAdd(&sched[1], 1u) == nwarps - 1) {
+      atomicExch(&sched[0], 0u);
+      atomicExch(&sched[1], 0u);
+    }
+  }
+}
+
+// ------------------------------------------- value-balanced flat kernel --
+
+// Value-balanced variant of the block-balanced kernel (plan 3), same tiles.
+// A round stages up to kVRound consecutive blocks in shared memory (masks,
+// block columns, each block's value offset in the round, and the id of the
+// panel a block ends); the round's values are then split into 32 equal
+// runs, one per lane, so a warp issues about values / 32 FMA instructions
+// per round whatever the blocks' fill.  A lane finds its run's first block
+// by a binary search of the offsets, walks the blocks one set bit per trip
+// (a block holds at least one value), picks the row's sum by selects, and
+// at the end of a block that ends a panel writes the panel's rows if the
+// panel started in its run, else keeps them as the head.  The lanes' last
+// partial sums are completed by the segmented warp scan of the
+// block-balanced kernel; the open panel carries into the next round.
+// Rounds of 256 blocks pay the scan's adds half as often as rounds of 128.
+constexpr int kVRound = 256;
+constexpr int kVPerLane = kVRound / 32;
+
+template <int R>
+struct VFlatBlocksPerSM {
+  static constexpr int v = R <= 2 ? 5 : (R == 4 ? 4 : 3);
+};
+
+struct VFlatWarpSmem {
+  uint32_t m[kVRound];
+  int32_t c[kVRound];
+  int32_t o[kVRound];    // value offset of the block in the round
+  int32_t pid[kVRound];  // panel the block ends, -1 if none
+};
+
+template <int R, int C, typename VT, typename AT>
+__global__ void __launch_bounds__(kDirectThreads, VFlatBlocksPerSM<R>::v)
+    k_spmv_vflat(const Tile *__restrict__ tiles, int32_t ntiles, uint32_t *sched,
+                 const int32_t *__restrict__ brp, const int32_t *__restrict__ block_colidx,
+                 const typename MaskType<R, C>::T *__restrict__ masks,
+                 const VT *__restrict__ vals, const AT *__restrict__ x, AT *__restrict__ y,
+                 AT *__restrict__ partial, Scale<AT> sc, int64_t nrows) {
+  __shared__ VFlatWarpSmem s_all[kDirectThreads / 32];
+  VFlatWarpSmem &S = s_all[threadIdx.x >> 5];
+  const int lane = threadIdx.x & 31;
+  constexpr int LOG2C = C == 8 ? 3 : 2;
+  uint32_t grab = 0;
+  if (lane == 0) grab = atomicAdd(&sched[0], 1u);
+  int32_t t = (int32_t)__shfl_sync(kFull, grab, 0);
+  while (t < ntiles) {
+    if (lane == 0) grab = atomicAdd(&sched[0], 1u);  // next tile, used after this one
+    const Tile cur = tiles[t];
+    if (cur.mode & kPartial) {
+      flat_piece<R, C>(cur, lane, block_colidx, masks, vals, x, partial);
+    } else {
+      flat_empty_rows<R>(cur, lane, brp, y, sc, nrows);
+      int32_t v = cur.v0;  // value index of the round's first value
+      AT carry = 0;        // lane q < R: row q's sum of the panel still open
+      bool open = false;   // a panel continues from the previous round
+      int32_t pcur = cur.p0;
+      for (int32_t base = cur.b0; base < cur.b1; base += kVRound) {
+        const int32_t lim = (base + kVRound < cur.b1) ? base + kVRound : cur.b1;
+        const int nbr = lim - base;
+        // 1. stage the round's blocks, kVPerLane consecutive blocks per lane
+        int cnt = 0;
+        uint32_t mm[kVPerLane];
+#pragma unroll
+        for (int i = 0; i < kVPerLane; ++i) {
+          const int32_t b = base + kVPerLane * lane + i;
+          const bool ok = b < lim;
+          mm[i] = ok ? (uint32_t)masks[b] : 0u;
+          S.m[kVPerLane * lane + i] = mm[i];
+          S.c[kVPerLane * lane + i] = ok ? block_colidx[b] : 0;
+          S.pid[kVPerLane * lane + i] = -1;
+          cnt += __popc(mm[i]);
+        }
+        int V;
+        int o = warp_excl_scan(cnt, lane, &V);
+#pragma unroll
+        for (int i = 0; i < kVPerLane; ++i) {
+          S.o[kVPerLane * lane + i] = o;
+          o += __popc(mm[i]);
+        }
+        __syncwarp();
+        // 2. the panels whose last block lies in the round
+        for (int32_t w = pcur;; w += 32) {
+          const int32_t p = w + lane;
+          const bool in = p < cur.p1;
+          const int32_t st = in ? brp[p] : 0;
+          const int32_t en = in ? brp[p + 1] : 0;
+          if (in && en > st && en > base && en <= lim) S.pid[en - 1 - base] = p;
+          const unsigned beyond = __ballot_sync(kFull, !in || en > lim);
+          if (beyond) {
+            pcur = w + __ffs(beyond) - 1;
+            break;
+          }
+        }
+        __syncwarp();
+        // 3. the lane's run of values [lo, hi) of the round
+        const int K = (V + 31) >> 5;
+        const int lo = min(lane * K, V);
+        const int n = min(lo + K, V) - lo;
+        int b = 0;
+        uint32_t mr = 0u;
+        int32_t col = 0;
+        bool fresh = true;  // the lane's current panel started in its run
+        if (n > 0) {
+          int a = 0, z = nbr - 1;  // the last block whose offset is <= lo
+          while (a < z) {
+            const int mid = (a + z + 1) >> 1;
+            if (S.o[mid] <= lo) a = mid; else z = mid - 1;
+          }
+          b = a;
+          const int rank = lo - S.o[b];
+          const uint32_t mb = S.m[b];
+          mr = rank ? mb & ~((1u << __fns(mb, 0, rank + 1)) - 1u) : mb;
+          col = S.c[b];
+          fresh = rank == 0 && (b == 0 ? !open : S.pid[b - 1] >= 0);
+        }
+        // lane 0 starts from the sums of the panel still open (0 if none)
+        AT acc[R], head[R];
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+          const AT cq = __shfl_sync(kFull, carry, q);
+          acc[q] = lane == 0 ? cq : (AT)0;
+          head[q] = 0;
+        }
+        bool has_head = false, ended = false;
+        int32_t head_pid = 0;
+        auto end_panel = [&](int bb) {  // block bb ends panel S.pid[bb]
+          const int64_t p = S.pid[bb];
+          if (fresh) {
+#pragma unroll
+            for (int q = 0; q < R; ++q) {
+              const int64_t row = p * R + q;
+              if (row < nrows) put_row(sc, y, row, acc[q]);
+            }
+          } else {
+#pragma unroll
+            for (int q = 0; q < R; ++q) head[q] = acc[q];
+            has_head = true;
+            head_pid = (int32_t)p;
+          }
+#pragma unroll
+          for (int q = 0; q < R; ++q) acc[q] = 0;
+          fresh = true;
+          ended = true;
+        };
+        int32_t off = v + lo;
+        for (int tt = 0; tt < K; ++tt) {
+          if (tt < n) {
+            if (mr == 0u) {  // the run goes on in the next block
+              if (S.pid[b] >= 0) end_panel(b);
+              ++b;
+              mr = S.m[b];
+              col = S.c[b];
+            }
+            const int kf = __ffs(mr) - 1;
+            mr &= mr - 1u;
+            const int q = kf >> LOG2C;
+            AT tq = acc[0];
+#pragma unroll
+            for (int qq = 1; qq < R; ++qq) tq = (q == qq) ? acc[qq] : tq;
+            tq = fma((AT)widen(vals[off]), __ldg(x + col + (kf & (C - 1))), tq);
+#pragma unroll
+            for (int qq = 0; qq < R; ++qq) acc[qq] = (q == qq) ? tq : acc[qq];
+            ++off;
+          }
+        }
+        if (n > 0 && mr == 0u && S.pid[b] >= 0) end_panel(b);  // run ends with a panel
+        // segmented scan of the lanes' last partial sums (stops at the first
+        // step where no lane can add)
+        const uint32_t endl = __ballot_sync(kFull, ended);
+#pragma unroll
+        for (int o2 = 1; o2 < 32; o2 <<= 1) {
+          const bool same =
+              lane >= o2 && ((endl >> (lane - o2 + 1)) & ((1u << o2) - 1u)) == 0u;
+          if (!__any_sync(kFull, same)) break;
+#pragma unroll
+          for (int q = 0; q < R; ++q) {
+            const AT tq = __shfl_up_sync(kFull, acc[q], o2);
+            if (same) acc[q] += tq;
+          }
+        }
+        // panels cut between lanes: the head plus the scanned partial before
+        // it (lane 0's head already holds the open panel's sums)
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+          const AT cin = __shfl_up_sync(kFull, acc[q], 1);
+          if (has_head) {
+            const int64_t row = (int64_t)head_pid * R + q;
+            if (row < nrows) put_row(sc, y, row, lane == 0 ? head[q] : head[q] + cin);
+          }
+        }
+        // the panel open at the end of the round: its sums are those of the
+        // lane holding the round's last value
+        open = S.pid[nbr - 1] < 0;
+        const int ll = (V - 1) / K;
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+          const AT sl = __shfl_sync(kFull, acc[q], ll);
+          if (lane == q) carry = open ? sl : (AT)0;
+        }
+        v += V;
         __syncwarp();
       }
     }
@@ -1740,6 +1974,32 @@ cudaError_t launch_flat(const spc5_matrix *A, const AT *x, AT *y, double alpha, 
 }
 
 template <int R, int C, typename VT, typename AT>
+cudaError_t launch_vflat(const spc5_matrix *A, const AT *x, AT *y, double alpha, double beta,
+                         cudaStream_t s, AT *partial, uint32_t *sched) {
+  using MaskT = typename MaskType<R, C>::T;
+  cudaError_t e = cudaSuccess;
+  if (A->fntiles > 0) {
+    const int warps_per_block = kDirectThreads / 32;
+    int64_t blocks = (A->fntiles + warps_per_block - 1) / warps_per_block;
+    const int64_t resident = (int64_t)num_sms() * VFlatBlocksPerSM<R>::v;
+    if (blocks > resident) blocks = resident;
+    k_spmv_vflat<R, C, VT, AT><<<(unsigned)blocks, kDirectThreads, 0, s>>>(
+        A->ftiles, (int32_t)A->fntiles, sched, A->block_rowptr, A->block_colidx,
+        (const MaskT *)A->masks, (const VT *)A->values, x, y, partial,
+        make_scale<AT>(alpha, beta), A->nrows);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  if (A->fnlong > 0) {
+    const int fblocks = fixup_blocks(A->fnlong);
+    k_fixup<R, AT><<<fblocks, 256, 0, s>>>(A->fnlong, A->flong_panels, A->flong_slots, partial,
+                                           y, make_scale<AT>(alpha, beta), A->nrows);
+    e = cudaGetLastError();
+  }
+  return e;
+}
+
+template <int R, int C, typename VT, typename AT>
 cudaError_t launch_expand(const spc5_matrix *A, const AT *x, AT *y, double alpha, double beta,
                           cudaStream_t s, AT *partial, uint32_t *sched) {
   using MaskT = typename MaskType<R, C>::T;
@@ -1810,6 +2070,16 @@ cudaError_t launch(const spc5_matrix *A, const void *x, void *y, double alpha, d
                                                 (float *)partial, sched);
     return launch_flat<R, C, double, double>(A, (const double *)x, (double *)y, alpha, beta, s,
                                              (double *)partial, sched);
+  }
+  if (A->flat == 3) {
+    if (A->value_dtype == SPC5_F32)
+      return launch_vflat<R, C, float, float>(A, (const float *)x, (float *)y, alpha, beta, s,
+                                              (float *)partial, sched);
+    if (A->value_dtype == SPC5_BF16)
+      return launch_vflat<R, C, uint16_t, float>(A, (const float *)x, (float *)y, alpha, beta,
+                                                 s, (float *)partial, sched);
+    return launch_vflat<R, C, double, double>(A, (const double *)x, (double *)y, alpha, beta,
+                                              s, (double *)partial, sched);
   }
   if (A->flat == 2) {
     if (A->value_dtype == SPC5_F32)

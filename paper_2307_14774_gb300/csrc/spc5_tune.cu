@@ -61,11 +61,12 @@ spc5_status tune(spc5_matrix *A, const void *x, void *y, int iters, cudaStream_t
   struct Cand {
     int log2g, body, flat;
   };
-  // the block-balanced and expanded plans, and row-group plans (lanes per
+  // the block-balanced (two kernels) and expanded plans, and row-group plans (lanes per
   // row; bodies 2 to 4 need one lane per row)
   std::vector<Cand> cands;
   cands.push_back({0, 0, 1});
   cands.push_back({0, 0, 2});
+  cands.push_back({0, 0, 3});
   cands.push_back({0, 2, 0});
   cands.push_back({0, 3, 0});
   cands.push_back({0, 4, 0});

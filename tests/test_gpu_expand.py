@@ -1,10 +1,12 @@
-"""The two plans for skewed rows.  Block-balanced (SPC5_FLAT=1): the blocks
-of runs of whole panels dealt to the lanes one block per lane, row sums by
-a segmented warp scan, long panels cut into pieces of a fixed block count.
-Expanded (SPC5_FLAT=2): runs of whole panels (at most 1024 values and 128
-rows) whose values a warp lays out row by row in shared memory and splits
-evenly over its lanes; panels of more than 1024 values cut into pieces.
-Pieces' row sums are added by a fixup kernel.
+"""The three plans for skewed rows.  Block-balanced (SPC5_FLAT=1): the
+blocks of runs of whole panels dealt to the lanes four blocks per lane per
+round, row sums by a segmented warp scan, long panels cut into pieces of a
+fixed block count.  Value-balanced (SPC5_FLAT=3): the same tiles, each
+round of 256 blocks staged in shared memory and its values split into 32
+equal runs.  Expanded (SPC5_FLAT=2): runs of whole panels (at most 1024
+values and 128 rows) whose values a warp lays out row by row in shared
+memory and splits evenly over its lanes; panels of more than 1024 values
+cut into pieces.  Pieces' row sums are added by a fixup kernel.
 
 Checked through the C ABI against the CPU oracle at the FP64 tolerance
 |y - y_ref| <= 1e-13 * sum_j |a_ij x_j| (and the FP32/BF16 bounds of the
@@ -24,7 +26,7 @@ from gpuhelpers import assert_within_tol, convert, spmv, to_device, torch_cuda
 pytestmark = pytest.mark.gpu
 
 BETAS = [(1, 8), (2, 4), (2, 8), (4, 4), (4, 8), (8, 4)]
-PLANS = ["1", "2"]
+PLANS = ["1", "2", "3"]
 
 
 def _sparse_rows(n=6000, ncols=700, seed=9):
@@ -96,12 +98,12 @@ def test_skewed_plans_integer_exact(monkeypatch, r, c, plan):
 
 
 def test_skewed_plans_default_choice():
-    """The converter picks the block-balanced plan for skewed rows and keeps
-    row groups for a stencil."""
+    """The converter picks a block-balanced plan for skewed rows (values split
+    over the lanes for r >= 4) and keeps row groups for a stencil."""
     torch_cuda()
     for r, c in BETAS:
         skewed = convert(synth.powerlaw(60_000, seed=3), r, c).info()
-        assert skewed["group_efficiency"] >= 0.7 or skewed["flat"] == 1
+        assert skewed["group_efficiency"] >= 0.7 or skewed["flat"] == (3 if r >= 4 else 1)
     assert convert(synth.powerlaw(60_000, seed=3), 1, 8).info()["group_efficiency"] < 0.7
     regular = convert(synth.stencil27(20, 20, 20, values="normal"), 4, 8).info()
     assert regular["group_efficiency"] >= 0.7 and regular["flat"] == 0

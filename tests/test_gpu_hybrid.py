@@ -77,7 +77,7 @@ def test_hybrid_split_bit_exact(mats, r, c):
         assert np.array_equal(g["s_vals"].view(np.uint64), Sc.vals.view(np.uint64))
 
 
-@pytest.mark.parametrize("plan", ["0", "1", "2"])
+@pytest.mark.parametrize("plan", ["0", "1", "2", "3"])
 @pytest.mark.parametrize("r,c", BETAS)
 def test_hybrid_spmv_fp64(monkeypatch, mats, r, c, plan):
     monkeypatch.setenv("SPC5_KERNEL", "0")

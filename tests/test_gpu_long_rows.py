@@ -43,7 +43,7 @@ def long_rows():
     return _long_rows()
 
 
-@pytest.mark.parametrize("plan", ["0", "1", "2"])
+@pytest.mark.parametrize("plan", ["0", "1", "2", "3"])
 @pytest.mark.parametrize("r,c", BETAS)
 def test_long_rows_every_plan(monkeypatch, long_rows, r, c, plan):
     monkeypatch.setenv("SPC5_FLAT", plan)

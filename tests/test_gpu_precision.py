@@ -103,7 +103,7 @@ def test_reduced_precision_integer_exact(monkeypatch, dtype, body):
             assert np.array_equal(y, A.todense() @ x.astype(np.float64))
 
 
-@pytest.mark.parametrize("flat", ["0", "1", "2"])
+@pytest.mark.parametrize("flat", ["0", "1", "2", "3"])
 @pytest.mark.parametrize("dtype", list(DTYPES))
 def test_reduced_precision_pieces_alpha_beta_host(monkeypatch, dtype, flat):
     monkeypatch.setenv("SPC5_FLAT", flat)

@@ -25,10 +25,11 @@ def _run(fn, M, x, nrows, alpha=1.0, beta=0.0, y0=None):
     return dy.cpu().numpy()
 
 
-@pytest.mark.parametrize("plan", ["rows", "staged", "flat", "expanded", "hybrid"])
+@pytest.mark.parametrize("plan", ["rows", "staged", "flat", "expanded", "vflat", "hybrid"])
 def test_noalloc_matches_spmv_twice(monkeypatch, plan):
     monkeypatch.setenv("SPC5_KERNEL", "1" if plan == "staged" else "0")
-    monkeypatch.setenv("SPC5_FLAT", {"flat": "1", "expanded": "2", "hybrid": "1"}.get(plan, "0"))
+    monkeypatch.setenv("SPC5_FLAT", {"flat": "1", "expanded": "2", "vflat": "3",
+                                          "hybrid": "1"}.get(plan, "0"))
     A = synth.powerlaw(200_000, seed=17)          # long rows: split into pieces
     if plan == "hybrid":                          # scalar rows cut into pieces too
         from gpuhelpers import to_device
@@ -37,7 +38,7 @@ def test_noalloc_matches_spmv_twice(monkeypatch, plan):
         M = convert(A, 4, 8)
     info = M.info()
     assert info["long_panels"] > 0               # the scratch array is used
-    assert info["flat"] == {"flat": 1, "expanded": 2, "hybrid": 1}.get(plan, 0)
+    assert info["flat"] == {"flat": 1, "expanded": 2, "vflat": 3, "hybrid": 1}.get(plan, 0)
     for call, seed in enumerate((1, 2)):         # two calls in a row, different x
         x = synth.vector_uniform(A.ncols, seed=seed)
         y_ref, scale = oracle.csr_spmv(A, x)
