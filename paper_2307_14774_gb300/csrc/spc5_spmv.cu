@@ -34,6 +34,15 @@
 // FP64 path is bound by the FP64 pipe (2 FMA per cycle per SM), which needs
 // many warps in flight more than it needs shared-memory staging; the staged
 // kernel (SPC5_KERNEL=1) stays available for comparison.
+//
+// For rows of very different lengths (spc5_info.flat) the lanes own work
+// instead of rows: blocks dealt four per lane per round (k_spmv_flat, plan
+// 1), each round's values split evenly over the lanes (k_spmv_vflat, plan
+// 3), or each tile's values laid out row by row in shared memory and split
+// evenly (k_spmv_expand, plan 2); row sums cut between lanes are completed
+// by segmented warp scans.  Hybrid matrices add their scalar entries with
+// k_spmv_scalars.  No kernel waits on another warp or CTA except the staged
+// kernel, whose waits are bounded.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stdlib.h>
