@@ -79,6 +79,23 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(x: float, world: int, device="cuda") -> float:
+    """The largest x over all ranks (timings are the slowest rank's)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(world: int, flops_per_step: float, seconds_per_step: float) -> float:
+    """GFlop/s of the whole job: every rank runs the full workload (replicas,
+    weak scaling), so N ranks do N times the work in the slowest rank's time."""
+    return world * flops_per_step / seconds_per_step / 1e9
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -597,14 +614,10 @@ def run_native(args):
         time.sleep(0.3)
     if world > 1:
         torch.distributed.barrier()
-    total_ms = t_start.elapsed_time(t_end)
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(t_start.elapsed_time(t_end), world)
     ms_per_step = total_ms / args.steps
     flops_per_step = sum(2.0 * cs["nnz"] for cs in cases)
-    value = world * flops_per_step / (ms_per_step * 1e-3) / 1e9
+    value = whole_job_value(world, flops_per_step, ms_per_step * 1e-3)
 
     # per-launch durations (CUDA events on the launching stream)
     per_case_ms = [statistics.median(ev[k][i][0].elapsed_time(ev[k][i][1])
@@ -715,12 +728,9 @@ def run_native(args):
         for _ in range(args.steps):
             e2e_step()
         torch.cuda.synchronize()
-        dt = (time.perf_counter() - t0) / args.steps
-        if world > 1:
-            t = torch.tensor([dt], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            dt = float(t.item())
-        result["e2e"] = {"value": round(world * flops_per_step / dt / 1e9, 2), "unit": UNIT,
+        dt = max_over_ranks((time.perf_counter() - t0) / args.steps, world)
+        result["e2e"] = {"value": round(whole_job_value(world, flops_per_step, dt), 2),
+                         "unit": UNIT,
                          "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                          "ms_per_step": round(dt * 1e3, 3),
                          "api": "spc5_spmv with pinned host x and y"}
