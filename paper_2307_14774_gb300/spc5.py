@@ -177,6 +177,79 @@ class Matrix:
     def info(self) -> dict:
         return spc5_matrix_info(self)
 
+    @classmethod
+    def from_csr(cls, A, r: int = 4, c: int = 8, store_dtype=SPC5_F64, stream=None) -> "Matrix":
+        """beta(r,c) from a torch sparse CSR tensor (indices narrowed to int32,
+        values widened to FP64 for the conversion; the call synchronises)."""
+        import torch
+        if getattr(A, "layout", None) != torch.sparse_csr:
+            raise TypeError("expected a torch.sparse_csr tensor")
+        nrows, ncols = A.shape
+        rowptr = A.crow_indices().to(torch.int32).contiguous()
+        colidx = A.col_indices().to(torch.int32).contiguous()
+        vals = A.values().to(torch.float64).contiguous()
+        return spc5_convert_csr(nrows, ncols, vals.numel(), rowptr, colidx, vals,
+                                store_dtype=store_dtype, r=r, c=c, stream=stream)
+
+    @property
+    def shape(self) -> tuple:
+        info = self.info()
+        return (info["nrows"], info["ncols"])
+
+    def _vector_dtype(self):
+        import torch
+        return torch.float64 if self.info()["value_dtype"] == SPC5_F64 else torch.float32
+
+    def __matmul__(self, x):
+        """y = A x for x [ncols] or X [ncols][k] (torch tensors; k columns go
+        through the batched kernel when k is 1, 2, 4, 8 or 16)."""
+        import torch
+        info = self.info()
+        dt = self._vector_dtype()
+        xc = x.to(dt).contiguous()
+        if xc.dim() == 1:
+            y = torch.empty(info["nrows"], dtype=dt, device=x.device)
+            spc5_spmv(self, xc, y)
+            return y
+        if xc.dim() != 2:
+            raise ValueError("x must be a vector or a matrix of right-hand sides")
+        k = xc.shape[1]
+        y = torch.empty((info["nrows"], k), dtype=dt, device=x.device)
+        if k in (1, 2, 4, 8, 16) and not info["hybrid"] and x.is_cuda:
+            spc5_spmv_batched([self], [xc], [y], k)
+        else:
+            for j in range(k):
+                col = torch.empty(info["nrows"], dtype=dt, device=x.device)
+                spc5_spmv(self, xc[:, j].contiguous(), col)
+                y[:, j] = col
+        return y
+
+    def t(self) -> "_Transposed":
+        """A^T, for products A^T g (spc5_spmv_t)."""
+        return _Transposed(self)
+
+
+class _Transposed:
+    """A^T of a converted matrix: A.t() @ g = spc5_spmv_t(A, g)."""
+
+    def __init__(self, A: "Matrix"):
+        self.A = A
+
+    @property
+    def shape(self) -> tuple:
+        return tuple(reversed(self.A.shape))
+
+    def __matmul__(self, g):
+        import torch
+        info = self.A.info()
+        dt = self.A._vector_dtype()
+        gc = g.to(dt).contiguous()
+        if gc.dim() != 1:
+            raise ValueError("g must be a vector")
+        dx = torch.empty(info["ncols"], dtype=dt, device=g.device)
+        spc5_spmv_t(self.A, gc, dx)
+        return dx
+
     def __del__(self):
         try:
             if self._h:
