@@ -389,13 +389,20 @@ __device__ __forceinline__ AT row_rounds4(const MaskT *__restrict__ masks,
   return acc;
 }
 
+// Launch shape of the row-group kernel: two CTAs of 24 warps per SM, so
+// that 24 consecutive tiles (neighbouring rows, which share x) run on one
+// SM's L1 at a time (the four-block body holds more registers: 5 x 8 warps).
 template <int BODY>
-struct TileBlocksPerSM {  // the four-block body holds more registers
-  static constexpr int v = BODY == 4 ? 5 : kDirectBlocksPerSM;
+struct TileThreads {
+  static constexpr int v = BODY == 4 ? 256 : 768;
+};
+template <int BODY>
+struct TileBlocksPerSM {
+  static constexpr int v = BODY == 4 ? 5 : 2;
 };
 
 template <int R, int C, int BODY, typename VT, typename AT>
-__global__ void __launch_bounds__(kDirectThreads, TileBlocksPerSM<BODY>::v)
+__global__ void __launch_bounds__(TileThreads<BODY>::v, TileBlocksPerSM<BODY>::v)
     k_spmv_tiles(const Tile *__restrict__ tiles, int64_t ntiles,
                  const int32_t *__restrict__ block_rowptr, const int32_t *__restrict__ panel_vptr,
                  const int32_t *__restrict__ block_colidx,
@@ -1936,11 +1943,11 @@ cudaError_t launch_direct(const spc5_matrix *A, const AT *x, AT *y, double alpha
   using MaskT = typename MaskType<R, C>::T;
   cudaError_t e = cudaSuccess;
   if (A->ntiles > 0) {
-    const int warps_per_block = kDirectThreads / 32;
+    const int warps_per_block = TileThreads<BODY>::v / 32;
     int64_t blocks = (A->ntiles + warps_per_block - 1) / warps_per_block;
     const int64_t resident = (int64_t)num_sms() * TileBlocksPerSM<BODY>::v;
     if (blocks > resident) blocks = resident;
-    k_spmv_tiles<R, C, BODY, VT, AT><<<(unsigned)blocks, kDirectThreads, 0, s>>>(
+    k_spmv_tiles<R, C, BODY, VT, AT><<<(unsigned)blocks, TileThreads<BODY>::v, 0, s>>>(
         A->tiles, A->ntiles, A->block_rowptr, A->panel_vptr, A->block_colidx,
         (const MaskT *)A->masks, (const VT *)A->values, x, y, partial,
           make_scale<AT>(alpha, beta), A->nrows);
