@@ -71,6 +71,10 @@ spc5_status tune(spc5_matrix *A, const void *x, void *y, int iters, cudaStream_t
   cands.push_back({0, 3, 0});
   cands.push_back({0, 4, 0});
   for (int lg = 0; lg <= max_log2g; ++lg) cands.push_back({lg, 0, 0});
+  // the predicated loop over the c bits spends an FMA on every bit: cheap
+  // with FP32 arithmetic (64 FMAs per cycle per SM), not with FP64 (2)
+  if (A->value_dtype != SPC5_F64)
+    for (int lg = 0; lg <= max_log2g; ++lg) cands.push_back({lg, 1, 0});
   double best = -1.0, best_rows = -1.0;
   size_t best_i = 0, best_rows_i = 1;
   for (size_t i = 0; i < cands.size(); ++i) {
