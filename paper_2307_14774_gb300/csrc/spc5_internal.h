@@ -17,7 +17,8 @@ namespace spc5 {
 //                 32/r lanes per row; with mode & kPartial the r row sums go
 //                 to partial[slot * r + q] and a fixup adds the pieces.
 //   flat tile:    (mode & kFlat) whole panels [p0, p1) whose blocks
-//                 [b0, b1) are dealt to the lanes one block per lane; with
+//                 [b0, b1) are dealt to the lanes in rounds (four blocks
+//                 per lane, or each round's values split evenly); with
 //                 mode & kPartial the blocks [b0, b1) of the single long
 //                 panel p0, whose r row sums go to partial[slot * r + q].
 //   expanded tile: (mode & kExpand) whole panels [p0, p1) whose values are

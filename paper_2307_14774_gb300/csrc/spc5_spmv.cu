@@ -58,7 +58,6 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kDirectThreads = 256;
-constexpr int kDirectBlocksPerSM = 6;  // 48 warps per SM at <= 40 registers
 constexpr long long kWaitBudget = 4000000000LL;  // SM cycles (about 2 s) before a wait gives up
 
 enum : uint32_t { kErrProducerWait = 1u, kErrConsumerWait = 2u, kErrTileTooLarge = 4u };
@@ -207,8 +206,9 @@ __device__ __forceinline__ void put_empty_row(const Scale<AT> &sc, AT *y, int64_
 // planner's tiles (warp w takes tiles w, w + nwarps, ...), prefetching the
 // next tile's descriptor, and pipelines each round's block metadata one
 // round ahead so that a round waits for one memory round trip (its values)
-// instead of two (metadata, then values).  Many resident warps (up to 64
-// per SM) keep the FP64 pipe and the memory system busy.
+// instead of two (metadata, then values).  Many resident warps (48 per SM)
+// keep the FP64 pipe and the memory system busy.
+//
 // Row-stream body for row-group tiles with one lane per row: the lane walks
 // its row's values across the panel's blocks, one FMA per loop trip, so a
 // warp issues as many FP64 FMAs as its longest row has values (plus one trip
