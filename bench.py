@@ -628,7 +628,6 @@ def run_native(args):
     hbm, peak_kind = measured_peaks()
     achieved = bytes_per_step * args.steps / (sum_launch_ms * 1e-3) / 1e9
     achieved_tflops = flops_per_step * args.steps / (sum_launch_ms * 1e-3) / 1e12
-    launches_per_spmv = max(cs["info"].get("launches_per_spmv", 1) for cs in cases)
     traffic_tab = ncu_traffic()
     traffic = None
     if traffic_tab:
@@ -669,7 +668,7 @@ def run_native(args):
                               if not args.no_tune else "planner default"},
         "roofline": roofline_object(achieved, achieved_tflops, hbm, peak_kind, traffic,
                                     bytes_per_step, flops_per_step),
-        "gpu_launches": nlaunch * launches_per_spmv * args.steps,
+        "gpu_launches": sum(cs["info"].get("launches_per_spmv", 1) for cs in cases) * args.steps,
         "cases": case_rows,
         "convert": {"ms_total": round(sum(cs["convert_s"] for cs in cases) * 1e3, 1),
                     "note": "CSR (device) -> beta(r,c), all 24 conversions, wall clock"},
