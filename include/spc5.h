@@ -238,11 +238,14 @@ spc5_status spc5_set_values(spc5_matrix *A, const double *vals, void *stream);
 
 /*
  * spc5_tune -- autotune the SpMV mapping of a converted matrix: time the
- * candidate numbers of lanes sharing one row (1, 2, 4, 8, those that fit
- * 32 / r) over `iters` products with the caller's vectors x and y (device
- * memory, typed as for spc5_spmv; y is overwritten) and keep the fastest
- * plan.  The paper observes that the best blocking depends on the machine
- * and the matrix (Section 4.3); the tuner measures instead of modelling.
+ * candidate plans (lanes sharing one row: 1, 2, 4, 8, those that fit 32 / r,
+ * with the one-lane-per-row bodies; the two block-balanced plans; the
+ * expanded plan) over `iters` products with the caller's vectors x and y
+ * (device memory, typed as for spc5_spmv; y is overwritten) and keep the
+ * fastest, with the fastest row-group plan kept for the transposed,
+ * gradient and batched kernels (spc5_info.tuned_us, tuned_rows_us).  The
+ * paper observes that the best blocking depends on the machine and the
+ * matrix (Section 4.3); the tuner measures instead of modelling.
  * Synchronises `stream`; rebuilds the plan (reallocates its buffers).
  */
 spc5_status spc5_tune(spc5_matrix *A, const void *x, void *y, int iters, void *stream);

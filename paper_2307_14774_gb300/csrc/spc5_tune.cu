@@ -6,9 +6,9 @@
 // x accesses of neighbouring rows together.  Rather than a model, the tuner
 // times the candidates on the caller's vectors:
 //   spc5_tune           G in {1, 2, 4, 8} (those that fit 32 / r), the
-//                       one-lane-per-row bodies, the block-balanced and the
-//                       expanded plan for one
-//                       converted matrix, keeping the fastest plan;
+//                       one-lane-per-row bodies, the two block-balanced
+//                       plans and the expanded plan for one converted
+//                       matrix, keeping the fastest plan;
 //   spc5_convert_tuned  every requested beta(r,c), each tuned, keeping the
 //                       fastest matrix (spc5_convert_tuned_ex: optionally
 //                       ranked by the row-group plan the batched kernel runs).
