@@ -115,8 +115,10 @@ def test_host_csr_input_matches_device_csr_input():
         assert np.array_equal(gh[k], gd[k])
 
 
+@pytest.mark.parametrize("plan", ["0", "1", "2", "3"])
 @pytest.mark.parametrize("r,c", BETAS)
-def test_degenerate_shapes(r, c):
+def test_degenerate_shapes(monkeypatch, r, c, plan):
+    monkeypatch.setenv("SPC5_FLAT", plan)
     cases = [
         synth.CSR(1, 1, np.array([0, 1], np.int32), np.array([0], np.int32), np.array([3.0])),
         synth.CSR(5, 9, np.zeros(6, np.int32), np.zeros(0, np.int32), np.zeros(0)),  # no entries
@@ -129,10 +131,14 @@ def test_degenerate_shapes(r, c):
     ]
     for A in cases:
         M = convert(A, r, c)
+        assert M.info()["flat"] == int(plan)
         assert_conversion_equal(M, oracle.convert(A, r, c), A)
         x = synth.vector_uniform(A.ncols, seed=2)
         y_ref, scale = oracle.csr_spmv(A, x)
         assert_within_tol(spmv(M, x), y_ref, scale)
+        y0 = synth.vector_normal(A.nrows, seed=4)
+        assert_within_tol(spmv(M, x, y0.copy(), 2.0, -1.0), 2.0 * y_ref - y0, 2.0 * scale,
+                          extra=np.abs(y0))
 
 
 def test_explicit_zeros_are_kept():
