@@ -186,8 +186,11 @@ spc5_status spc5_export(const spc5_matrix *A, const int32_t **block_rowptr,
  * FP64 matrix, FP32 for FP32 and BF16 matrices (accumulation in the vector
  * type).  With beta == 0, y is not read (no NaN or Inf from a previous y
  * propagates).
- * Device vectors: asynchronous on `stream`.  Host vectors: copied through
- * device buffers owned by A; the call returns when y is on the host.  x and y
+ * Device vectors: asynchronous on `stream`.  Host vectors: x (and a pageable
+ * y) are copied through device buffers owned by A; a pinned (page-locked)
+ * host y is written in place by the kernels through its device mapping, so
+ * the result crosses to the host while the product runs; the call returns
+ * when y is on the host.  x and y
  * must not overlap.  Products on the same handle whose kernels could overlap
  * on the GPU (different streams) must be serialised by the caller: they
  * share the handle's buffer of partial sums and its tile counter.

@@ -32,14 +32,18 @@ bool supported_rc(int r, int c) {
 namespace {
 
 // True when `p` is host memory (pageable or pinned), false when the device
-// can read it directly (device or managed memory).
-bool is_host_pointer(const void *p) {
+// can read it directly (device or managed memory).  *mapped (if given)
+// receives the device address of pinned (page-locked, mapped) host memory,
+// nullptr otherwise.
+bool is_host_pointer(const void *p, void **mapped = nullptr) {
+  if (mapped) *mapped = nullptr;
   cudaPointerAttributes attr;
   cudaError_t e = cudaPointerGetAttributes(&attr, p);
   if (e != cudaSuccess) {
     cudaGetLastError();  // clear the sticky-free error of an unknown pointer
     return true;
   }
+  if (mapped && attr.type == cudaMemoryTypeHost) *mapped = attr.devicePointer;
   return attr.type == cudaMemoryTypeUnregistered || attr.type == cudaMemoryTypeHost;
 }
 
@@ -270,16 +274,21 @@ spc5_status spc5_spmv(const spc5_matrix *A, const void *x, void *y, double alpha
   RETURN_IF((A->ncols > 0 && !x) || (A->nrows > 0 && !y), SPC5_EINVAL, "NULL vector");
   cudaStream_t s = (cudaStream_t)stream;
   DeviceGuard guard(A->device);
+  void *y_mapped = nullptr;
   const bool host_x = A->ncols > 0 && is_host_pointer(x);
-  const bool host_y = A->nrows > 0 && is_host_pointer(y);
+  const bool host_y = A->nrows > 0 && is_host_pointer(y, &y_mapped);
   if (!host_x && !host_y) return spmv_device(A, x, y, alpha, beta, s);
+  // pinned y is written in place by the kernels (through its mapping), so
+  // the result reaches the host while the product runs; pageable y goes
+  // through a device buffer and a copy back
+  const bool stage_y = host_y && !y_mapped;
 
   const size_t es = A->value_dtype == SPC5_F64 ? sizeof(double) : sizeof(float);
   spc5_matrix *M = const_cast<spc5_matrix *>(A);
   spc5_status st = SPC5_OK;
   if (host_x && !M->x_stage)
     st = cuda_check(cudaMalloc(&M->x_stage, (size_t)A->ncols * es + 16), "alloc x staging");
-  if (st == SPC5_OK && host_y && !M->y_stage)
+  if (st == SPC5_OK && stage_y && !M->y_stage)
     st = cuda_check(cudaMalloc(&M->y_stage, (size_t)A->nrows * es + 16), "alloc y staging");
   if (st != SPC5_OK) return st;
   const void *dx = x;
@@ -291,7 +300,8 @@ spc5_status spc5_spmv(const spc5_matrix *A, const void *x, void *y, double alpha
     if (st != SPC5_OK) return st;
     dx = M->x_stage;
   }
-  if (host_y) {
+  if (y_mapped) dy = y_mapped;
+  if (stage_y) {
     if (beta != 0.0) {
       st = cuda_check(cudaMemcpyAsync(M->y_stage, y, (size_t)A->nrows * es,
                                       cudaMemcpyHostToDevice, s),
@@ -302,7 +312,7 @@ spc5_status spc5_spmv(const spc5_matrix *A, const void *x, void *y, double alpha
   }
   st = spmv_device(A, dx, dy, alpha, beta, s);
   if (st != SPC5_OK) return st;
-  if (host_y) {
+  if (stage_y) {
     st = cuda_check(cudaMemcpyAsync(y, dy, (size_t)A->nrows * es, cudaMemcpyDeviceToHost, s),
                     "copy y back");
     if (st != SPC5_OK) return st;
