@@ -69,6 +69,8 @@ def parse_args():
     ap.add_argument("--no-tune", action="store_true",
                     help="keep the planner's default mapping instead of autotuning it")
     ap.add_argument("--cases-out", default=None, help="write the per-case table here")
+    ap.add_argument("--clocks-out", default=None,
+                    help="directory for the raw nvidia-smi clock samples (default: a temp dir)")
     return ap.parse_args()
 
 
@@ -172,10 +174,12 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: int, out_dir=None):
+        import tempfile
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        self.path = os.path.join(out_dir or tempfile.gettempdir(),
+                                 f"spc5_clocks_rank{gpu_index}.csv")
 
     def __enter__(self):
         try:
@@ -604,7 +608,7 @@ def run_native(args):
     torch.cuda.synchronize()
     t_start = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local) as clk:
+    with ClockSampler(local, args.clocks_out) as clk:
         time.sleep(0.3)
         t_start.record(stream)
         for k in range(args.steps):
