@@ -18,7 +18,8 @@
  *     stream).  Work is enqueued on it.
  *   - Array arguments may live in device memory or in host memory; the
  *     library asks the CUDA runtime which one (cudaPointerGetAttributes).
- *     Host arguments are copied through device buffers and make the call
+ *     Host arguments are copied through device buffers (spc5_spmv writes a
+ *     pinned host y in place through its device mapping) and make the call
  *     blocking.
  *   - No call throws, aborts or uses a device fault to report an error: every
  *     failure is a returned spc5_status, and spc5_last_error() gives a
