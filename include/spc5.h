@@ -94,6 +94,9 @@ typedef struct {
   double tuned_rows_us;    /* SpMV time of the fastest row-group plan spc5_tune tried (the
                               plan of the batched, transposed and gradient kernels), 0 if
                               untuned */
+  int64_t pieces;          /* pieces the SpMV's plan cuts long panels into (r partial sums
+                              each) */
+  int64_t scalar_pieces;   /* hybrid: pieces of long scalar rows (one partial sum each) */
 } spc5_info;
 
 /*
@@ -192,7 +195,8 @@ spc5_status spc5_export(const spc5_matrix *A, const int32_t **block_rowptr,
  * host y is written in place by the kernels through its device mapping, so
  * the result crosses to the host while the product runs; the call returns
  * when y is on the host.  x and y
- * must not overlap.  Products on the same handle whose kernels could overlap
+ * must not overlap; device memory of another GPU than the matrix's gives
+ * SPC5_EINVAL.  Products on the same handle whose kernels could overlap
  * on the GPU (different streams) must be serialised by the caller: they
  * share the handle's buffer of partial sums and its tile counter.
  *
@@ -345,10 +349,12 @@ spc5_status spc5_ircg(const spc5_matrix *A64, const spc5_matrix *Alo, const doub
 
 /*
  * spc5_spmv_noalloc -- the same product as spc5_spmv for callers that must
- * not allocate device memory during the call (for example while a CUDA
- * graph is being captured on `stream`, or in a loop that must never reach
- * the allocator).  The paper has no counterpart: this is a deployment
- * variant of Algorithm 1's product, not part of the method.
+ * not allocate device memory during the call: a real-time loop that must
+ * never reach the allocator (or the device-wide synchronisation a cudaFree
+ * implies), a library that may use only the memory its host application
+ * hands it, or code under a device-memory budget fixed at start-up.  The
+ * paper has no counterpart: this is a deployment variant of Algorithm 1's
+ * product, not part of the method.
  *
  * x[ncols], y[nrows] must be in device (or managed) memory, typed as for
  * spc5_spmv (FP64 for an FP64 matrix, FP32 otherwise);
@@ -357,7 +363,9 @@ spc5_status spc5_ircg(const spc5_matrix *A64, const spc5_matrix *Alo, const doub
  * fixed array inside the library (1 MiB = 131072 doubles, kept on every
  * GPU that loads the library until the process exits) instead of the
  * handle's own buffer; a matrix needing more than 131072 partial sums
- * (pieces * r) is rejected with SPC5_EOVERFLOW before any work is queued.
+ * (spc5_info.pieces * r + spc5_info.scalar_pieces) is rejected with
+ * SPC5_EOVERFLOW before any work is queued.  x and y must be memory of the
+ * matrix's device (or managed memory), else SPC5_EINVAL.
  * The call makes no cudaMalloc, cudaFree or other allocating call.
  *
  * The tile counter of the block-balanced and expanded plans is likewise a
@@ -375,6 +383,19 @@ spc5_status spc5_ircg(const spc5_matrix *A64, const spc5_matrix *Alo, const doub
  */
 spc5_status spc5_spmv_noalloc(const spc5_matrix *A, const void *x, void *y, double alpha,
                               double beta, void *stream);
+
+/*
+ * spc5_measure_fma_peak -- measured FMA throughput of the current device in
+ * TFLOP/s (2 flop per FMA), for dtype SPC5_F64 or SPC5_F32: a kernel of
+ * eight independent FMA chains per thread on every SM, the best of five
+ * timed launches (CUDA events on `stream`).  Not part of the paper: the
+ * arithmetic ceiling that SpMV throughput is reported against (GB300 runs
+ * FP64 FMAs at 1/64 of the FP32 rate, so FP64 SpMV can be bound by it
+ * rather than by memory).  Synchronises `stream`; allocates and frees a
+ * small result buffer.  SPC5_EUNSUPPORTED for other dtypes, SPC5_EINVAL if
+ * tflops is NULL.
+ */
+spc5_status spc5_measure_fma_peak(spc5_dtype dtype, void *stream, double *tflops);
 
 /* Release the handle and every device array it owns (synchronising). */
 spc5_status spc5_destroy(spc5_matrix *A);

@@ -31,6 +31,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "spc5_oracle.c")
 _OUT_DIR = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_OUT_DIR, "libspc5oracle.so")
+_OMP_LIB_PATH = os.path.join(_OUT_DIR, "libspc5oracle_omp.so")
 _lock = threading.Lock()
 
 ERRORS = {1: "EINVAL", 2: "EUNSORTED", 3: "ERANGE", 4: "EROWPTR"}
@@ -44,15 +45,29 @@ class OracleError(ValueError):
 
 def build(force: bool = False) -> str:
     """Compile the oracle (plain C, -O2, no OpenMP, no target-specific flags)."""
+    return _compile(_LIB_PATH, [], force)
+
+
+def build_omp(force: bool = False) -> str | None:
+    """Compile the same source with OpenMP (-fopenmp): the two CSR products
+    then run their rows on several host threads.  Used only to time the CPU
+    baseline; None if the compiler has no OpenMP."""
+    try:
+        return _compile(_OMP_LIB_PATH, ["-fopenmp"], force)
+    except subprocess.CalledProcessError:
+        return None
+
+
+def _compile(out: str, extra, force: bool) -> str:
     os.makedirs(_OUT_DIR, exist_ok=True)
-    if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
-        return _LIB_PATH
-    tmp = _LIB_PATH + f".tmp{os.getpid()}"
-    subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", _SRC, "-o", tmp, "-lm"],
+    if (not force and os.path.exists(out)
+            and os.path.getmtime(out) >= os.path.getmtime(_SRC)):
+        return out
+    tmp = out + f".tmp{os.getpid()}"
+    subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", *extra, _SRC, "-o", tmp, "-lm"],
                    check=True, capture_output=True)
-    os.replace(tmp, _LIB_PATH)
-    return _LIB_PATH
+    os.replace(tmp, out)
+    return out
 
 
 def _p(dtype):
@@ -65,6 +80,8 @@ def _bind(lib):
                                   _p(np.uint64), _p(np.uint8))
     opt = ctypes.c_void_p
     lib.oracle_check_csr.argtypes = [i64, i64, i32p, i32p]
+    lib.oracle_set_threads.argtypes = [ci]
+    lib.oracle_set_threads.restype = ci
     lib.oracle_csr_spmv.argtypes = [i64, i32p, i32p, f64p, f64p, f64p, opt]
     lib.oracle_csr_spmv_plain.argtypes = [i64, i32p, i32p, f64p, f64p, f64p]
     lib.oracle_spc5_convert.argtypes = [i64, i64, i32p, i32p, opt, ci, ci, i64p,
@@ -148,6 +165,10 @@ class Oracle:
 
     def __init__(self, path: str | None = None):
         self.lib = _bind(ctypes.CDLL(path or build()))
+
+    def set_threads(self, n: int) -> int:
+        """Host threads of the CSR products (1 unless this copy has OpenMP)."""
+        return self.lib.oracle_set_threads(int(n))
 
     def check_csr(self, nrows, ncols, rowptr, colidx) -> int:
         """0 if the CSR pattern is valid, else the oracle's error code."""
@@ -286,6 +307,13 @@ def _default() -> Oracle:
         if _default_oracle is None:
             _default_oracle = Oracle()
     return _default_oracle
+
+
+def timing_oracle() -> Oracle | None:
+    """The OpenMP build of the oracle (for timing the CPU baseline on all host
+    cores), or None when the compiler cannot build it."""
+    path = build_omp()
+    return Oracle(path) if path else None
 
 
 def check_csr(nrows, ncols, rowptr, colidx) -> int:

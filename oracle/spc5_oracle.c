@@ -43,6 +43,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 enum {
   ORACLE_OK = 0,
@@ -79,6 +82,7 @@ int oracle_check_csr(int64_t nrows, int64_t ncols, const int32_t *rowptr, const 
  */
 int oracle_csr_spmv(int64_t nrows, const int32_t *rowptr, const int32_t *colidx,
                     const double *vals, const double *x, double *y, double *scale) {
+#pragma omp parallel for schedule(static, 1024)
   for (int64_t i = 0; i < nrows; ++i) {
     double s = 0.0, comp = 0.0, mag = 0.0;
     for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
@@ -101,12 +105,30 @@ int oracle_csr_spmv(int64_t nrows, const int32_t *rowptr, const int32_t *colidx,
  * time the CPU baseline and as an extra consistency check. */
 int oracle_csr_spmv_plain(int64_t nrows, const int32_t *rowptr, const int32_t *colidx,
                           const double *vals, const double *x, double *y) {
+#pragma omp parallel for schedule(static, 1024)
   for (int64_t i = 0; i < nrows; ++i) {
     double s = 0.0;
     for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) s += vals[e] * x[colidx[e]];
     y[i] = s;
   }
   return ORACLE_OK;
+}
+
+/*
+ * Host threads of the two CSR products above.  Rows are independent and each
+ * row is summed by one thread in the order stated above, so the results do
+ * not depend on the thread count.  The library built without OpenMP (the
+ * one the tests use) ignores the request and returns 1; the build with
+ * OpenMP (used only to time the CPU baseline) returns the count set.
+ */
+int oracle_set_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+  return omp_get_max_threads();
+#else
+  (void)n;
+  return 1;
+#endif
 }
 
 /*

@@ -5,11 +5,13 @@
 #include <stdint.h>
 #include <stdlib.h>
 
+#include <atomic>
 #include <cstring>
 #include <new>
 #include <string>
 
 #include "spc5_internal.h"
+#include "spc5_pointer.h"
 
 namespace spc5 {
 
@@ -24,6 +26,23 @@ spc5_status cuda_check(cudaError_t e, const char *what) {
   return SPC5_ECUDA;
 }
 
+int device_sm_count() {
+  static std::atomic<int> cache[kMaxDevices];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  if (dev < 0 || dev >= kMaxDevices) dev = 0;
+  int n = cache[dev].load(std::memory_order_relaxed);
+  if (n <= 0) {
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
+      n = 1;
+    cache[dev].store(n, std::memory_order_relaxed);
+  }
+  return n;
+}
+
 bool supported_rc(int r, int c) {
   return (r == 1 && c == 8) || (r == 2 && c == 4) || (r == 2 && c == 8) || (r == 4 && c == 4) ||
          (r == 4 && c == 8) || (r == 8 && c == 4);
@@ -31,21 +50,23 @@ bool supported_rc(int r, int c) {
 
 namespace {
 
-// True when `p` is host memory (pageable or pinned), false when the device
-// can read it directly (device or managed memory).  *mapped (if given)
+// Where `p` lives relative to device `dev`: host memory (pageable or
+// pinned), memory the device reads directly (its own device memory, or
+// managed memory), or device memory of another GPU.  *mapped (if given)
 // receives the device address of pinned (page-locked, mapped) host memory,
 // nullptr otherwise.
-bool is_host_pointer(const void *p, void **mapped = nullptr) {
+Placement locate(const void *p, int dev, void **mapped = nullptr) {
   if (mapped) *mapped = nullptr;
   cudaPointerAttributes attr;
   cudaError_t e = cudaPointerGetAttributes(&attr, p);
   if (e != cudaSuccess) {
     cudaGetLastError();  // clear the sticky-free error of an unknown pointer
-    return true;
+    return placement_of(-1, -1, dev);
   }
   if (mapped && attr.type == cudaMemoryTypeHost) *mapped = attr.devicePointer;
-  return attr.type == cudaMemoryTypeUnregistered || attr.type == cudaMemoryTypeHost;
+  return placement_of((int)attr.type, attr.device, dev);
 }
+
 
 struct DeviceGuard {
   int prev = -1;
@@ -162,7 +183,13 @@ spc5_status spc5_convert_csr(int64_t nrows, int64_t ncols, int64_t nnz, const in
   const double *d_vals = (const double *)vals;
   void *tmp[3] = {nullptr, nullptr, nullptr};
   auto stage = [&](const void *src, size_t bytes, int slot, const void **dst) -> spc5_status {
-    if (!src || !is_host_pointer(src)) return SPC5_OK;
+    if (!src) return SPC5_OK;
+    const Placement pl = locate(src, A->device);
+    if (pl == Placement::kOtherDevice) {
+      set_error("a CSR array is device memory of another GPU than the current one");
+      return SPC5_EINVAL;
+    }
+    if (pl == Placement::kDevice) return SPC5_OK;
     spc5_status e = cuda_check(cudaMallocAsync(&tmp[slot], bytes > 0 ? bytes : 4, s), "alloc staging");
     if (e != SPC5_OK) return e;
     e = cuda_check(cudaMemcpyAsync(tmp[slot], src, bytes, cudaMemcpyHostToDevice, s), "copy CSR");
@@ -251,6 +278,8 @@ spc5_status spc5_matrix_info(const spc5_matrix *A, spc5_info *info) {
   info->group_efficiency = A->group_efficiency;
   info->hybrid = A->hybrid;
   info->nscalars = A->nscalars;
+  info->pieces = spmv_pieces(A);
+  info->scalar_pieces = A->hybrid ? A->snpieces : 0;
   info->nnz = A->nnz + A->nscalars;
   info->filling = A->nblocks ? (double)A->nnz / ((double)A->nblocks * A->r * A->c) : 0.0;
   return SPC5_OK;
@@ -275,8 +304,12 @@ spc5_status spc5_spmv(const spc5_matrix *A, const void *x, void *y, double alpha
   cudaStream_t s = (cudaStream_t)stream;
   DeviceGuard guard(A->device);
   void *y_mapped = nullptr;
-  const bool host_x = A->ncols > 0 && is_host_pointer(x);
-  const bool host_y = A->nrows > 0 && is_host_pointer(y, &y_mapped);
+  const Placement px = A->ncols > 0 ? locate(x, A->device) : Placement::kDevice;
+  const Placement py = A->nrows > 0 ? locate(y, A->device, &y_mapped) : Placement::kDevice;
+  RETURN_IF(px == Placement::kOtherDevice || py == Placement::kOtherDevice, SPC5_EINVAL,
+            "x or y is device memory of another GPU than the matrix's");
+  const bool host_x = px == Placement::kHost;
+  const bool host_y = py == Placement::kHost;
   if (!host_x && !host_y) return spmv_device(A, x, y, alpha, beta, s);
   // pinned y is written in place by the kernels (through its mapping), so
   // the result reaches the host while the product runs; pageable y goes

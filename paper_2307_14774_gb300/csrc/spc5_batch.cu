@@ -42,26 +42,12 @@ struct MatDesc {
   int32_t r, c, ntiles, nlong;
 };
 
-__device__ __forceinline__ double widen(double v) { return v; }
-__device__ __forceinline__ float widen(float v) { return v; }
-__device__ __forceinline__ float widen(uint16_t v) { return __uint_as_float((uint32_t)v << 16); }
-
-template <int R, int C>
-struct Mask {
-  using T = typename std::conditional<(R * C == 8), uint8_t,
-                                      typename std::conditional<(R * C == 16), uint16_t,
-                                                                uint32_t>::type>::type;
-};
-template <int R>
-struct L2 {
-  static constexpr int v = R == 1 ? 0 : R == 2 ? 1 : R == 4 ? 2 : 3;
-};
 
 // One tile of one matrix with K right-hand sides.
 template <int R, int C, int K, typename VT, typename AT>
 __device__ __forceinline__ void batch_tile(const MatDesc &d, const Tile &cur, int lane, AT alpha,
                                            AT beta) {
-  using MT = typename Mask<R, C>::T;
+  using MT = typename MaskType<R, C>::T;
   const MT *__restrict__ masks = (const MT *)d.masks;
   const VT *__restrict__ vals = (const VT *)d.values;
   const AT *__restrict__ x = (const AT *)d.x;
@@ -69,7 +55,7 @@ __device__ __forceinline__ void batch_tile(const MatDesc &d, const Tile &cur, in
   const bool segment = (cur.mode & kSegment) != 0;
   const int log2G = cur.mode & 15;
   const int G = 1 << log2G;
-  const int shift_j = L2<R>::v + log2G;
+  const int shift_j = Log2<R>::v + log2G;
   const int g = lane & (G - 1);
   const int q = (lane >> log2G) & (R - 1);
   const int j = lane >> shift_j;
@@ -212,16 +198,7 @@ __global__ void k_iota(int32_t *dst, int64_t n) {
     dst[i] = (int32_t)i;
 }
 
-int sm_count() {
-  static int n = 0;
-  if (n == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    if (n <= 0) n = 1;
-  }
-  return n;
-}
+int sm_count() { return device_sm_count(); }
 
 }  // namespace
 }  // namespace spc5

@@ -25,20 +25,6 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kThreads = 256;
 
-template <int R, int C>
-struct Mask {
-  using T = typename std::conditional<(R * C == 8), uint8_t,
-                                      typename std::conditional<(R * C == 16), uint16_t,
-                                                                uint32_t>::type>::type;
-};
-template <int R>
-struct L2 {
-  static constexpr int v = R == 1 ? 0 : R == 2 ? 1 : R == 4 ? 2 : 3;
-};
-
-__device__ __forceinline__ double widen(double v) { return v; }
-__device__ __forceinline__ float widen(float v) { return v; }
-__device__ __forceinline__ float widen(uint16_t v) { return __uint_as_float((uint32_t)v << 16); }
 
 // Calls f(row, col, mq, off, valid) for every block of the lane's row in the
 // tile: row = global row, col = block start column, mq = the row's c-bit
@@ -48,12 +34,12 @@ __device__ __forceinline__ void walk_tile(const Tile &cur, int lane,
                                           const int32_t *__restrict__ brp,
                                           const int32_t *__restrict__ vptr,
                                           const int32_t *__restrict__ bcol,
-                                          const typename Mask<R, C>::T *__restrict__ masks,
+                                          const typename MaskType<R, C>::T *__restrict__ masks,
                                           int64_t nrows, F &&f) {
   const bool segment = (cur.mode & kSegment) != 0;
   const int log2G = cur.mode & 15;
   const int G = 1 << log2G;
-  const int shift_j = L2<R>::v + log2G;
+  const int shift_j = Log2<R>::v + log2G;
   const int g = lane & (G - 1);
   const int q = (lane >> log2G) & (R - 1);
   const int j = lane >> shift_j;
@@ -100,7 +86,7 @@ template <int R, int C, typename VT, typename AT>
 __global__ void __launch_bounds__(kThreads)
     k_spmv_t(const Tile *__restrict__ tiles, int64_t ntiles, const int32_t *__restrict__ brp,
              const int32_t *__restrict__ vptr, const int32_t *__restrict__ bcol,
-             const typename Mask<R, C>::T *__restrict__ masks, const VT *__restrict__ vals,
+             const typename MaskType<R, C>::T *__restrict__ masks, const VT *__restrict__ vals,
              const AT *__restrict__ g, AT *__restrict__ dx, AT alpha, int64_t nrows) {
   const int lane = threadIdx.x & 31;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -124,7 +110,7 @@ __global__ void __launch_bounds__(kThreads)
     k_values_grad(const Tile *__restrict__ tiles, int64_t ntiles,
                   const int32_t *__restrict__ brp, const int32_t *__restrict__ vptr,
                   const int32_t *__restrict__ bcol,
-                  const typename Mask<R, C>::T *__restrict__ masks,
+                  const typename MaskType<R, C>::T *__restrict__ masks,
                   const int32_t *__restrict__ value_src, const AT *__restrict__ g,
                   const AT *__restrict__ x, AT *__restrict__ dvals, AT alpha, int64_t nrows) {
   const int lane = threadIdx.x & 31;
@@ -170,16 +156,7 @@ __global__ void k_set_values(int64_t nnz, const int32_t *__restrict__ value_src,
     store(values + i, vals_csr[value_src[i]]);
 }
 
-int sms() {
-  static int n = 0;
-  if (n == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    if (n <= 0) n = 1;
-  }
-  return n;
-}
+int sms() { return device_sm_count(); }
 
 unsigned tile_grid(int64_t ntiles) {
   int64_t blocks = (ntiles + (kThreads / 32) - 1) / (kThreads / 32);
@@ -196,7 +173,7 @@ unsigned flat_grid(int64_t n) {
 template <int R, int C, typename VT, typename AT>
 cudaError_t run_t(const spc5_matrix *A, const void *g, void *dx, double alpha, double beta,
                   cudaStream_t s) {
-  using MT = typename Mask<R, C>::T;
+  using MT = typename MaskType<R, C>::T;
   k_scale<AT><<<flat_grid(A->ncols), kThreads, 0, s>>>(A->ncols, (AT *)dx, (AT)beta);
   if (A->ntiles > 0)
     k_spmv_t<R, C, VT, AT><<<tile_grid(A->ntiles), kThreads, 0, s>>>(
@@ -209,7 +186,7 @@ cudaError_t run_t(const spc5_matrix *A, const void *g, void *dx, double alpha, d
 template <int R, int C, typename AT>
 cudaError_t run_grad(const spc5_matrix *A, const void *g, const void *x, void *dvals,
                      double alpha, cudaStream_t s) {
-  using MT = typename Mask<R, C>::T;
+  using MT = typename MaskType<R, C>::T;
   if (A->ntiles > 0)
     k_values_grad<R, C, AT><<<tile_grid(A->ntiles), kThreads, 0, s>>>(
         A->tiles, A->ntiles, A->block_rowptr, A->panel_vptr, A->block_colidx,

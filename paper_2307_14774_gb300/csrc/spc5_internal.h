@@ -42,6 +42,43 @@ constexpr int32_t kExpandCap = 1024;
 constexpr int32_t kExpandWindow = 512;
 constexpr int32_t kExpandRows = 128;
 
+// Packed mask word of one block: r * c bits, row q at bits [q * c, (q + 1) * c)
+// (uint8 for r * c = 8, uint16 for 16, uint32 for 32).
+template <int R, int C>
+struct MaskType {
+  using T = uint32_t;
+};
+template <>
+struct MaskType<1, 8> {
+  using T = uint8_t;
+};
+template <>
+struct MaskType<2, 4> {
+  using T = uint8_t;
+};
+template <>
+struct MaskType<2, 8> {
+  using T = uint16_t;
+};
+template <>
+struct MaskType<4, 4> {
+  using T = uint16_t;
+};
+
+// log2 of a block height r in {1, 2, 4, 8}.
+template <int R>
+struct Log2 {
+  static constexpr int v = R == 1 ? 0 : R == 2 ? 1 : R == 4 ? 2 : 3;
+};
+
+#ifdef __CUDACC__
+// Stored value -> accumulation type.  FP64 and FP32 are used as they are;
+// a BF16 bit pattern is the upper half of an FP32, so widening is exact.
+__device__ __forceinline__ double widen(double v) { return v; }
+__device__ __forceinline__ float widen(float v) { return v; }
+__device__ __forceinline__ float widen(uint16_t v) { return __uint_as_float((uint32_t)v << 16); }
+#endif
+
 }  // namespace spc5
 
 // A converted matrix.  Every array is device memory owned by the handle.
@@ -121,6 +158,12 @@ spc5_status cuda_check(cudaError_t e, const char *what);
 
 // Supported block shapes.
 bool supported_rc(int r, int c);
+
+// Multiprocessor count of the current device (looked up once per device).
+int device_sm_count();
+
+// Largest device ordinal the library's per-device tables hold, plus one.
+constexpr int kMaxDevices = 64;
 
 // Conversion: fills A (sizes set by the caller) from a device CSR.
 spc5_status convert_device(spc5_matrix *A, const int32_t *d_rowptr, const int32_t *d_colidx,

@@ -1,16 +1,18 @@
 // spc5_spmv_noalloc: the SpMV for callers that must not allocate.
 //
 // Some callers cannot call cudaMalloc at the moment they need a product: a
-// solver step running while a CUDA graph is being captured on its stream, a
-// real-time loop that must not hit the allocator (or its implicit device
-// synchronisation), or code running under a memory budget that was fixed at
-// start-up.  spc5_spmv itself allocates nothing for device vectors either,
-// but it writes the partial sums of panels split into pieces to a buffer
-// owned by the matrix handle, and the expanded plan schedules its
-// tiles through a counter owned by the handle.  This entry point uses
+// real-time loop that must not hit the allocator (or the device-wide
+// synchronisation a cudaFree implies), a library that may only use memory
+// its host application hands it, or code running under a device-memory
+// budget fixed at start-up.  spc5_spmv itself allocates nothing for device
+// vectors either, but it writes the partial sums of panels split into pieces
+// to a buffer owned by the matrix handle, and the expanded plan schedules
+// its tiles through a counter owned by the handle.  This entry point uses
 // instead a fixed array and a fixed counter pair compiled into the library
 // (file-scope __device__ storage), so the whole call allocates nothing and
-// touches no per-matrix scratch.
+// touches neither of those per-matrix buffers.  (The staged kernel, when a
+// plan selects it, still reports a timed-out wait through the handle's
+// error word.)
 //
 // The array holds kNoallocScratchDoubles doubles (1 MiB); every GPU that
 // loads the library keeps it until the process exits.  A matrix whose split
@@ -23,12 +25,12 @@
 #include <string>
 
 #include "spc5_internal.h"
+#include "spc5_pointer.h"
 
 namespace spc5 {
 namespace {
 
 constexpr int64_t kNoallocScratchDoubles = 131072;  // 1 MiB
-constexpr int kMaxDevices = 64;
 
 // Shared by every call on a device.  Every slot a call reads is written
 // earlier in the same call (each piece writes its own r sums before the
@@ -72,13 +74,15 @@ spc5_status scratch_address(int dev, double **out, uint32_t **sched) {
   return SPC5_OK;
 }
 
-bool device_readable(const void *p) {
+// True when device `dev` can read `p` directly: its own device memory or
+// managed memory (not host memory, not another GPU's memory).
+bool device_readable(const void *p, int dev) {
   cudaPointerAttributes attr;
   if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+  return placement_of((int)attr.type, attr.device, dev) == Placement::kDevice;
 }
 
 }  // namespace
@@ -93,8 +97,10 @@ extern "C" spc5_status spc5_spmv_noalloc(const spc5_matrix *A, const void *x, vo
     return SPC5_EINVAL;
   }
   if (A->nrows == 0) return SPC5_OK;
-  if ((A->ncols > 0 && (!x || !device_readable(x))) || !y || !device_readable(y)) {
-    set_error("spc5_spmv_noalloc takes device vectors only (host vectors need staging buffers)");
+  if ((A->ncols > 0 && (!x || !device_readable(x, A->device))) || !y ||
+      !device_readable(y, A->device)) {
+    set_error("spc5_spmv_noalloc takes vectors in the matrix's device memory (or managed "
+              "memory) only: host vectors need staging buffers");
     return SPC5_EINVAL;
   }
   const int64_t need = spmv_pieces(A) * A->r + (A->hybrid ? A->snpieces : 0);

@@ -62,38 +62,6 @@ constexpr long long kWaitBudget = 4000000000LL;  // SM cycles (about 2 s) before
 
 enum : uint32_t { kErrProducerWait = 1u, kErrConsumerWait = 2u, kErrTileTooLarge = 4u };
 
-template <int R, int C>
-struct MaskType {
-  using T = uint32_t;
-};
-template <>
-struct MaskType<1, 8> {
-  using T = uint8_t;
-};
-template <>
-struct MaskType<2, 4> {
-  using T = uint8_t;
-};
-template <>
-struct MaskType<2, 8> {
-  using T = uint16_t;
-};
-template <>
-struct MaskType<4, 4> {
-  using T = uint16_t;
-};
-
-template <int R>
-struct Log2 {
-  static constexpr int v = R == 1 ? 0 : R == 2 ? 1 : R == 4 ? 2 : 3;
-};
-
-// Stored value -> accumulation type.  FP64 and FP32 are used as they are;
-// a BF16 bit pattern is the upper half of an FP32, so widening is exact.
-__device__ __forceinline__ double widen(double v) { return v; }
-__device__ __forceinline__ float widen(float v) { return v; }
-__device__ __forceinline__ float widen(uint16_t v) { return __uint_as_float((uint32_t)v << 16); }
-
 // One row's contribution of one block: sum over set bits k of mq of
 // vals[running index] * x[col + k], accumulated in AT (FP64 for FP64
 // values; FP32 for FP32 and BF16 values).
@@ -1863,16 +1831,7 @@ __global__ void k_fixup(int64_t nlong, const int32_t *long_panels, const int32_t
   }
 }
 
-int num_sms() {
-  static int n = 0;
-  if (n == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    if (n <= 0) n = 1;
-  }
-  return n;
-}
+int num_sms() { return device_sm_count(); }
 
 // Blocks of 256 threads for a fixup over n split panels (one warp each).
 int fixup_blocks(int64_t n) {
@@ -1914,13 +1873,16 @@ cudaError_t launch_staged(const spc5_matrix *A, const double *x, double *y, doub
   P.xs_base = P.stage_base + A->stages * P.stage_bytes;
   const size_t smem = (size_t)P.xs_base +
                       (BODY >= 2 ? (size_t)A->consumers * kXsPerConsumer * sizeof(double) : 0);
-  static size_t configured = 0;  // per instantiation
-  cudaError_t e = cudaSuccess;
-  if (smem > configured) {
+  // the attribute belongs to the device's context: remember it per device
+  static size_t configured[kMaxDevices] = {};  // per instantiation
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices || smem > configured[dev]) {
     e = cudaFuncSetAttribute(k_spmv_staged<R, C, BODY>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    configured = smem;
+    if (dev >= 0 && dev < kMaxDevices) configured[dev] = smem;
   }
   if (A->ntiles > 0) {
     int grid = (int)std::min<int64_t>(num_sms(), A->ntiles);

@@ -28,7 +28,8 @@ EXPORTS = ("spc5_convert_csr", "spc5_matrix_info", "spc5_export", "spc5_spmv", "
            "spc5_set_values", "spc5_tune", "spc5_convert_tuned", "spc5_convert_tuned_ex",
            "spc5_spmv_batched",
            "spc5_batch_create", "spc5_batch_run", "spc5_batch_destroy", "spc5_ircg",
-           "spc5_spmv_noalloc", "spc5_convert_hybrid", "spc5_export_hybrid")
+           "spc5_spmv_noalloc", "spc5_convert_hybrid", "spc5_export_hybrid",
+           "spc5_measure_fma_peak")
 
 
 class SPC5Error(RuntimeError):
@@ -50,7 +51,8 @@ class Info(ctypes.Structure):
                 ("device_error", ctypes.c_uint32), ("tuned_us", ctypes.c_double),
                 ("flat", ctypes.c_int32), ("group_efficiency", ctypes.c_double),
                 ("hybrid", ctypes.c_int32), ("nscalars", ctypes.c_int64),
-                ("tuned_rows_us", ctypes.c_double)]
+                ("tuned_rows_us", ctypes.c_double), ("pieces", ctypes.c_int64),
+                ("scalar_pieces", ctypes.c_int64)]
 
 
 class CGReport(ctypes.Structure):
@@ -114,6 +116,8 @@ def load(path: str | None = None):
         lib.spc5_convert_hybrid.restype = ci
         lib.spc5_export_hybrid.argtypes = [vp] + [ctypes.POINTER(vp)] * 3
         lib.spc5_export_hybrid.restype = ci
+        lib.spc5_measure_fma_peak.argtypes = [ci, vp, ctypes.POINTER(dbl)]
+        lib.spc5_measure_fma_peak.restype = ci
         lib.spc5_destroy.argtypes = [vp]
         for f in (lib.spc5_convert_csr, lib.spc5_matrix_info, lib.spc5_export, lib.spc5_spmv,
                   lib.spc5_destroy):
@@ -324,6 +328,13 @@ def spc5_values_grad(A: Matrix, g, x, dvals, alpha: float = 1.0, stream=None) ->
 def spc5_set_values(A: Matrix, vals, stream=None) -> None:
     """Replace the stored values with CSR-ordered FP64 device values."""
     _check(load().spc5_set_values(A.handle, _ptr(vals), _stream_ptr(stream)))
+
+
+def spc5_measure_fma_peak(dtype: int = SPC5_F64, stream=None) -> float:
+    """Measured FMA throughput of the current device in TFLOP/s (FP64 or FP32)."""
+    out = ctypes.c_double(0.0)
+    _check(load().spc5_measure_fma_peak(int(dtype), _stream_ptr(stream), ctypes.byref(out)))
+    return out.value
 
 
 def spc5_tune(A: Matrix, x, y, iters: int = 5, stream=None) -> dict:

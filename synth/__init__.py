@@ -215,19 +215,23 @@ def vector_int(n: int, lo: int = -3, hi: int = 3, seed: int = 0,
 # Named workloads with the sizes of the benchmark configurations.
 def workload(name: str, scale: str = "full") -> CSR:
     """Named workloads.  scale="full": the benchmark sizes; "small": reduced
-    instances of the same generators for quick parity runs."""
-    full = scale == "full"
+    instances of the same generators for quick parity runs; "profile":
+    instances still larger than the GPU's L2 cache (129 MB) but a quarter or
+    less of the full size, for hardware-counter captures."""
+    if scale not in ("full", "small", "profile"):
+        raise ValueError(scale)
+    pick = {"full": 0, "profile": 1, "small": 2}[scale]
     if name == "laplace2d_128":
         return laplace2d(128, 128)
     if name == "stencil27":
-        k = 100 if full else 24
+        k = (100, 90, 24)[pick]
         return stencil27(k, k, k, values="normal", seed=1)
     if name == "fem3d":
-        return fem3d(1_000_000 if full else 20_000, seed=2)
+        return fem3d((1_000_000, 250_000, 20_000)[pick], seed=2)
     if name == "powerlaw":
-        return powerlaw(2_000_000 if full else 40_000, seed=3)
+        return powerlaw((2_000_000, 1_000_000, 40_000)[pick], seed=3)
     if name == "uniform":
-        return uniform(1_000_000 if full else 30_000, 16, seed=4)
+        return uniform((1_000_000, 1_000_000, 30_000)[pick], 16, seed=4)
     if name == "poisson27_128":
         return stencil27(128, 128, 128, values="poisson")
     if name == "dense2048":

@@ -84,3 +84,32 @@ def test_struct_layout_matches_header(tmp_path, cname, pystruct):
                                           text=True).stdout.split()]
     assert got[0] == ctypes.sizeof(cls)
     assert got[1:] == [getattr(cls, f).offset for f, _ in cls._fields_]
+
+
+def test_vector_placement_rule(tmp_path):
+    """The rule by which spc5_spmv and spc5_spmv_noalloc classify a vector
+    (spc5_pointer.h), compiled and checked on the host: host memory is
+    staged, the matrix's own device memory and managed memory are read
+    directly, another GPU's device memory is rejected."""
+    import shutil
+    import subprocess
+    if shutil.which("g++") is None:
+        pytest.skip("no C++ compiler")
+    csrc = os.path.join(os.path.dirname(os.path.dirname(__file__)), "paper_2307_14774_gb300",
+                        "csrc")
+    src = tmp_path / "placement.cpp"
+    src.write_text('#include <cstdio>\n#include "spc5_pointer.h"\nusing namespace spc5;\n'
+                   "int main() {\n"
+                   "  int bad = 0;\n"
+                   "  bad += placement_of(-1, -1, 0) != Placement::kHost;\n"
+                   "  bad += placement_of(0, -2, 1) != Placement::kHost;\n"
+                   "  bad += placement_of(1, 0, 1) != Placement::kHost;\n"
+                   "  bad += placement_of(2, 1, 1) != Placement::kDevice;\n"
+                   "  bad += placement_of(2, 0, 1) != Placement::kOtherDevice;\n"
+                   "  bad += placement_of(2, 3, 0) != Placement::kOtherDevice;\n"
+                   "  bad += placement_of(3, 0, 1) != Placement::kDevice;\n"
+                   '  std::printf("%d\\n", bad);\n  return 0;\n}\n')
+    exe = tmp_path / "placement"
+    subprocess.run(["g++", "-std=c++17", "-I", csrc, str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
+    assert out.strip() == "0"

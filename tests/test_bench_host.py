@@ -64,16 +64,76 @@ def test_source_hash_ignores_comments_only(bench, tmp_path, monkeypatch):
     assert bench.kernel_source_hash() != h0
 
 
-def test_committed_dram_table_parses(bench, monkeypatch):
-    """profiles/spc5_spmv_dram.txt holds one DRAM figure per benchmark case;
-    bench.py uses it only while its source hash is the kernels' (else the
-    roofline's traffic is null)."""
+def test_dram_ratio_table_parses_and_is_guarded_by_the_source_hash(bench, tmp_path,
+                                                                  monkeypatch):
+    """profiles/spc5_spmv_dram.txt holds, per benchmark case, the ncu DRAM
+    bytes of one launch on the profile-scale instance, its algorithmic bytes
+    and their ratio; bench.py applies the ratio only while the table's source
+    hash is the kernels' (else the roofline's traffic is null)."""
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    rows = ["# matrix beta dram_bytes algorithmic_bytes ratio", "source_sha256: abcd"]
+    rows += [f"{m} {r}x{c} 1000 900 {1000 / 900:.4f}" for m in bench.MATRICES
+             for r, c in bench.BETAS]
+    (prof / "spc5_spmv_dram.txt").write_text("\n".join(rows) + "\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda: "abcd")
+    table = bench.ncu_traffic_ratios()
+    assert set(table) == {(m, f"{r}x{c}") for m in bench.MATRICES for r, c in bench.BETAS}
+    assert all(v == pytest.approx(1000 / 900, abs=1e-4) for v in table.values())
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda: "0" * 16)
+    assert bench.ncu_traffic_ratios() is None
+
+
+def test_committed_dram_table_if_present_covers_every_case(bench, monkeypatch):
     path = os.path.join(ROOT, "profiles", "spc5_spmv_dram.txt")
+    if not os.path.exists(path):
+        pytest.skip("no committed DRAM table")
     stored = [ln.split(":", 1)[1].strip() for ln in open(path) if ln.startswith("source_sha256:")]
     assert len(stored) == 1
     monkeypatch.setattr(bench, "kernel_source_hash", lambda: stored[0])
-    table = bench.ncu_traffic()
-    assert set(table) == {(m, f"{r}x{c}") for m in bench.MATRICES for r, c in bench.BETAS}
-    assert all(v > 1e8 for v in table.values())
-    monkeypatch.setattr(bench, "kernel_source_hash", lambda: "0" * 16)
-    assert bench.ncu_traffic() is None
+    table = bench.ncu_traffic_ratios()
+    assert table and all(0.5 < v < 3.0 for v in table.values())
+
+
+def test_err_over_tol(bench):
+    import numpy as np
+    y_ref = np.array([1.0, 2.0, 0.0, 5.0])
+    scale = np.array([10.0, 20.0, 0.0, 1.0])
+    y = y_ref + np.array([1e-13, -1e-12, 0.0, 0.0])
+    assert bench.err_over_tol(y, y_ref, scale, 1e-13) == pytest.approx(0.5, rel=1e-3)
+    y[2] = 1e-300  # an error on a row whose scale is zero
+    assert bench.err_over_tol(y, y_ref, scale, 1e-13) == float("inf")
+
+
+def test_roofline_reports_the_longest_launch_against_hbm(bench):
+    rows = [{"matrix": "stencil27", "beta": "4x8", "us": 50.0, "bytes": 247_500_000,
+             "nnz": 26_463_592, "plan": "rows/G1"},
+            {"matrix": "fem3d", "beta": "4x8", "us": 600.0, "bytes": 2_092_500_000,
+             "nnz": 238_367_592, "plan": "rows/G1"}]
+    ro = bench.roofline_object(rows, 6687.5, "measured", 1.25, "measured",
+                               {("fem3d", "4x8"): 1.05}, {"frac": 0.5})
+    assert ro["bound"] == "hbm" and ro["unit"] == "GB/s"
+    assert ro["kernel"].startswith("FP64 SpMV fem3d beta(4x8)")
+    assert ro["achieved"] == pytest.approx(2_092_500_000 / 600e-6 / 1e9, rel=1e-3)
+    assert ro["frac"] == pytest.approx(ro["achieved"] / 6687.5, rel=1e-3)
+    assert ro["traffic"] == pytest.approx(1.05 * 2_092_500_000, rel=1e-6)
+    assert ro["fp64_pipe"]["frac"] == pytest.approx(2 * 238_367_592 / 600e-6 / 1e12 / 1.25,
+                                                    rel=1e-3)
+
+
+def test_cpu_baseline_references_do_not_depend_on_the_thread_count(bench):
+    """The OpenMP build of the oracle, timed by the CPU baseline, gives the
+    same products bit for bit as the single-threaded oracle the tests use."""
+    import numpy as np
+
+    import oracle
+    import synth
+    hosts = {"a": (synth.powerlaw(3000, seed=5), None), "b": (synth.fem3d(500, seed=1), None)}
+    hosts = {k: (A, synth.vector_uniform(A.ncols, seed=2)) for k, (A, _) in hosts.items()}
+    rec, refs = bench.cpu_baseline(hosts, lambda m: None, reps=1)
+    assert rec["oracle_all"]["gflops"] > 0 and rec["plain_one"]["threads"] == 1
+    assert isinstance(rec["cpu_model"], str) and rec["cpu_model"]
+    for name, (A, x) in hosts.items():
+        y, s = oracle.csr_spmv(A, x)
+        assert np.array_equal(refs[name][0], y) and np.array_equal(refs[name][1], s)

@@ -65,12 +65,19 @@ def test_batched_matches_oracle(monkeypatch, k, dtype):
     spc5.spc5_spmv_batched(Ms, dX, dY, k)
     for A, X, Y in zip(mats, Xs, dY):
         Yh = Y.double().cpu().numpy()
-        Xq = X.astype(np.float32).astype(np.float64) if dtype == "f32" else X
+        if dtype == "f32":
+            # the kernel's own FP32 arithmetic, against the oracle on the
+            # stored (rounded) values and the FP32 x it was given
+            Xq = X.astype(np.float32).astype(np.float64)
+            Adq = synth.CSR(A.nrows, A.ncols, A.rowptr, A.colidx,
+                            oracle.quantize(A.vals, "f32").astype(np.float64))
+            nrow = np.diff(A.rowptr).astype(np.float64)
         for j in range(k):
             y_ref, scale = oracle.csr_spmv(A, X[:, j])
-            if dtype == "f32":
-                y_ref_q, _ = oracle.csr_spmv(A, Xq[:, j])
             assert_within_tol(Yh[:, j], y_ref, scale, tol=tol)
+            if dtype == "f32":
+                y_dq, scale_dq = oracle.csr_spmv(Adq, Xq[:, j])
+                assert np.all(np.abs(Yh[:, j] - y_dq) <= (nrow + 2) * 2.0 ** -24 * scale_dq)
 
 
 def test_batch_reuse_alpha_beta_and_graph_capture():

@@ -70,6 +70,7 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
     bench = _bench()
     monkeypatch.setenv("RANK", "1")
     monkeypatch.setenv("WORLD_SIZE", "2")
-    args = type("Args", (), {"matrices": "stencil27", "steps": 1, "warmup": 0})()
+    args = type("Args", (), {"matrices": "stencil27", "steps": 1, "warmup": 0, "scale": "full",
+                             "betas": "4x8"})()
     assert bench.run_reference(args) is None
     assert capsys.readouterr().out == ""

@@ -1,6 +1,7 @@
 """spc5_spmv_noalloc, the entry point for callers that cannot allocate device
-memory during a product (e.g. while capturing a CUDA graph): its partial
-sums live in a fixed array inside the library.  Checked through the C ABI
+memory during a product (a loop that must never reach the allocator, a
+library limited to the memory its application hands it): its partial sums
+live in a fixed array inside the library.  Checked through the C ABI
 against spc5_spmv on two calls in a row, plus its size limit."""
 from __future__ import annotations
 
@@ -38,6 +39,10 @@ def test_noalloc_matches_spmv_twice(monkeypatch, plan):
         M = convert(A, 4, 8)
     info = M.info()
     assert info["long_panels"] > 0               # the scratch array is used
+    assert info["pieces"] > 0
+    if plan == "hybrid":                         # and its region after the blocks' sums
+        assert info["scalar_pieces"] > 0
+    assert info["pieces"] * 4 + info["scalar_pieces"] <= 131072
     assert info["flat"] == {"flat": 1, "expanded": 2, "vflat": 3, "hybrid": 1}.get(plan, 0)
     for call, seed in enumerate((1, 2)):         # two calls in a row, different x
         x = synth.vector_uniform(A.ncols, seed=seed)
@@ -61,6 +66,7 @@ def test_noalloc_rejects_oversized_scratch_and_host_vectors(monkeypatch):
     M = convert(A, 8, 4)
     info = M.info()
     assert info["long_panels"] > 0
+    assert info["pieces"] * 8 > 131072           # more partial sums than the array holds
     x = torch.from_numpy(synth.vector_uniform(A.ncols, seed=3)).cuda()
     y = torch.zeros(A.nrows, dtype=torch.float64, device="cuda")
     with pytest.raises(spc5.SPC5Error) as ei:
