@@ -6,12 +6,17 @@
 // arrays and vectors and a map from a global tile index to its matrix; the
 // global tile list is the concatenation of the matrices' own work plans.
 // spc5_batch_run then launches the persistent kernel over all tiles: a warp
-// takes global tiles in turn, reads the tile's matrix from the table and
-// runs the SpMV lane mapping for that matrix's block shape (a warp-uniform
-// switch over the six shapes) with k accumulators per lane: every stored
-// value meets k x values, read as one contiguous run (X row-major [n][k]).
-// Running allocates nothing and copies nothing from the host, so it can be
-// captured in a CUDA graph.
+// takes chunks of consecutive global tiles from a counter (consecutive tiles
+// mostly belong to one matrix, so the warp reads the matrix's table entry
+// once per chunk, and uneven matrices are balanced across the warps), and
+// runs each tile with the lane mapping of that matrix's row-group plan: the
+// matrix's block shape (a warp-uniform switch over the six shapes) and its
+// tuned body (the row stream for one lane per row, else the per-block loop),
+// with k accumulators per lane: every stored value meets k x values, read as
+// one contiguous run (X row-major [n][k]) with vector loads when the vectors
+// are 16-byte aligned.  Running allocates nothing and copies nothing from
+// the host, so it can be captured in a CUDA graph; the tile counter is left
+// at zero by every launch.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -40,11 +45,92 @@ struct MatDesc {
   int64_t nrows;
   int64_t tile_base;
   int32_t r, c, ntiles, nlong;
+  int32_t body, pad;  // the matrix's row-group body (2: row stream)
 };
+
+constexpr int kBatchChunk = 8;  // consecutive tiles per counter grab
+
+// The K values of one row of a row-major [n][K] vector block: vector loads
+// when the block is 16-byte aligned (VEC), else K scalar loads.
+template <int K, bool VEC, typename AT>
+__device__ __forceinline__ void load_row(const AT *__restrict__ p, AT (&v)[K]) {
+  if constexpr (VEC && sizeof(AT) == 4 && K % 4 == 0) {
+#pragma unroll
+    for (int i = 0; i < K / 4; ++i) {
+      const float4 t = __ldg(reinterpret_cast<const float4 *>(p) + i);
+      v[4 * i] = t.x;
+      v[4 * i + 1] = t.y;
+      v[4 * i + 2] = t.z;
+      v[4 * i + 3] = t.w;
+    }
+  } else if constexpr (VEC && sizeof(AT) == 4 && K == 2) {
+    const float2 t = __ldg(reinterpret_cast<const float2 *>(p));
+    v[0] = t.x;
+    v[1] = t.y;
+  } else if constexpr (VEC && sizeof(AT) == 8 && K % 2 == 0) {
+#pragma unroll
+    for (int i = 0; i < K / 2; ++i) {
+      const double2 t = __ldg(reinterpret_cast<const double2 *>(p) + i);
+      v[2 * i] = t.x;
+      v[2 * i + 1] = t.y;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < K; ++i) v[i] = __ldg(p + i);
+  }
+}
+
+// Row-stream body with K right-hand sides (one lane per row): the lane walks
+// its row's values across the panel's blocks, one value (K FMAs) per trip,
+// entering the next block when its row bits in the current one are used up;
+// the next block's mask and start column are loaded one block ahead.
+template <int R, int C, int K, bool VEC, typename VT, typename AT, typename MaskT>
+__device__ __forceinline__ void row_stream_k(const MaskT *__restrict__ masks,
+                                             const int32_t *__restrict__ colidx,
+                                             const VT *__restrict__ vals,
+                                             const AT *__restrict__ x, int32_t bl, int32_t nbp,
+                                             int32_t v, int q, AT (&acc)[K]) {
+  const int qc = q * C;
+  const uint32_t row_low = (1u << qc) - 1u;
+  const uint32_t cmask = (1u << C) - 1u;
+  uint32_t m1 = 0u;
+  int32_t c1 = 0;
+  if (nbp > 0) {
+    m1 = (uint32_t)masks[bl];
+    c1 = colidx[bl];
+  }
+  int32_t b = 0;
+  uint32_t mq = 0u;
+  int32_t off = 0, col = 0;
+  while (__any_sync(kFull, mq != 0u || b < nbp)) {
+    if (mq == 0u && b < nbp) {
+      mq = (m1 >> qc) & cmask;
+      off = v + __popc(m1 & row_low);
+      v += __popc(m1);
+      col = c1;
+      ++b;
+      m1 = 0u;
+      if (b < nbp) {
+        m1 = (uint32_t)masks[bl + b];
+        c1 = colidx[bl + b];
+      }
+    }
+    if (mq) {
+      const int k = __ffs(mq) - 1;
+      const AT a = (AT)widen(vals[off]);
+      AT xv[K];
+      load_row<K, VEC>(x + (int64_t)(col + k) * K, xv);
+#pragma unroll
+      for (int i = 0; i < K; ++i) acc[i] = fma(a, xv[i], acc[i]);
+      mq &= mq - 1u;
+      ++off;
+    }
+  }
+}
 
 
 // One tile of one matrix with K right-hand sides.
-template <int R, int C, int K, typename VT, typename AT>
+template <int R, int C, int K, bool VEC, typename VT, typename AT>
 __device__ __forceinline__ void batch_tile(const MatDesc &d, const Tile &cur, int lane, AT alpha,
                                            AT beta) {
   using MT = typename MaskType<R, C>::T;
@@ -75,10 +161,13 @@ __device__ __forceinline__ void batch_tile(const MatDesc &d, const Tile &cur, in
     nbp = pvalid ? d.brp[p + 1] - bl : 0;
     v = pvalid ? d.vptr[p] : 0;
   }
-  const int32_t maxnb = __reduce_max_sync(kFull, nbp);
   AT acc[K];
 #pragma unroll
   for (int i = 0; i < K; ++i) acc[i] = 0;
+  if (d.body == 2 && G == 1) {
+    row_stream_k<R, C, K, VEC>(masks, d.colidx, vals, x, bl, nbp, v, q, acc);
+  } else {
+  const int32_t maxnb = __reduce_max_sync(kFull, nbp);
   for (int32_t it = 0; it < maxnb; it += G) {
     const int32_t idx = it + g;
     const bool valid = idx < nbp;
@@ -97,11 +186,13 @@ __device__ __forceinline__ void batch_tile(const MatDesc &d, const Tile &cur, in
       const int k = __ffs(mq) - 1;
       mq &= mq - 1u;
       const AT a = (AT)widen(vals[off++]);
-      const AT *xr = x + (int64_t)(col + k) * K;
+      AT xv[K];
+      load_row<K, VEC>(x + (int64_t)(col + k) * K, xv);
 #pragma unroll
-      for (int i = 0; i < K; ++i) acc[i] = fma(a, __ldg(xr + i), acc[i]);
+      for (int i = 0; i < K; ++i) acc[i] = fma(a, xv[i], acc[i]);
     }
     v += total;
+  }
   }
 #pragma unroll
   for (int i = 0; i < K; ++i)
@@ -126,23 +217,46 @@ __device__ __forceinline__ void batch_tile(const MatDesc &d, const Tile &cur, in
   }
 }
 
-template <int K, typename VT, typename AT>
+template <int K, bool VEC, typename VT, typename AT>
 __global__ void __launch_bounds__(kThreads)
     k_batch(const MatDesc *__restrict__ table, const int32_t *__restrict__ tile_mat,
-            int64_t ntiles, AT alpha, AT beta) {
+            int64_t ntiles, uint32_t *sched, AT alpha, AT beta) {
   const int lane = threadIdx.x & 31;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < ntiles;
-       t += nwarps) {
-    const MatDesc d = table[tile_mat[t]];
-    const Tile cur = d.tiles[t - d.tile_base];
-    switch (d.r * 100 + d.c) {
-      case 108: batch_tile<1, 8, K, VT, AT>(d, cur, lane, alpha, beta); break;
-      case 204: batch_tile<2, 4, K, VT, AT>(d, cur, lane, alpha, beta); break;
-      case 208: batch_tile<2, 8, K, VT, AT>(d, cur, lane, alpha, beta); break;
-      case 404: batch_tile<4, 4, K, VT, AT>(d, cur, lane, alpha, beta); break;
-      case 408: batch_tile<4, 8, K, VT, AT>(d, cur, lane, alpha, beta); break;
-      default: batch_tile<8, 4, K, VT, AT>(d, cur, lane, alpha, beta); break;
+  const int64_t nchunks = (ntiles + kBatchChunk - 1) / kBatchChunk;
+  // chunks come from the counter one ahead: the grab for the next chunk is
+  // issued when a chunk starts
+  uint32_t grab = 0;
+  if (lane == 0) grab = atomicAdd(&sched[0], 1u);
+  int64_t ch = (int64_t)__shfl_sync(kFull, grab, 0);
+  int cur_m = -1;
+  MatDesc d;
+  while (ch < nchunks) {
+    if (lane == 0) grab = atomicAdd(&sched[0], 1u);
+    const int64_t t1 = min((ch + 1) * kBatchChunk, ntiles);
+    for (int64_t t = ch * kBatchChunk; t < t1; ++t) {
+      const int m = tile_mat[t];
+      if (m != cur_m) {  // uniform over the warp
+        d = table[m];
+        cur_m = m;
+      }
+      const Tile cur = d.tiles[t - d.tile_base];
+      switch (d.r * 100 + d.c) {
+        case 108: batch_tile<1, 8, K, VEC, VT, AT>(d, cur, lane, alpha, beta); break;
+        case 204: batch_tile<2, 4, K, VEC, VT, AT>(d, cur, lane, alpha, beta); break;
+        case 208: batch_tile<2, 8, K, VEC, VT, AT>(d, cur, lane, alpha, beta); break;
+        case 404: batch_tile<4, 4, K, VEC, VT, AT>(d, cur, lane, alpha, beta); break;
+        case 408: batch_tile<4, 8, K, VEC, VT, AT>(d, cur, lane, alpha, beta); break;
+        default: batch_tile<8, 4, K, VEC, VT, AT>(d, cur, lane, alpha, beta); break;
+      }
+    }
+    ch = (int64_t)__shfl_sync(kFull, grab, 0);
+  }
+  // every warp has made its last grab: the last one to finish resets the counter
+  if (lane == 0) {
+    const uint32_t nwarps = gridDim.x * (blockDim.x >> 5);
+    if (atomicAdd(&sched[1], 1u) == nwarps - 1) {
+      atomicExch(&sched[0], 0u);
+      atomicExch(&sched[1], 0u);
     }
   }
 }
@@ -207,6 +321,8 @@ using namespace spc5;
 
 struct spc5_batch {
   int nmat = 0, k = 0, device = 0;
+  int vec = 0;              // every X and Y 16-byte aligned: vector loads of the k values
+  uint32_t *sched = nullptr;  // [2] tile-chunk counter and finished warps (reset by the kernel)
   spc5_dtype dtype = SPC5_F64;
   int64_t ntiles = 0, nlong = 0;
   MatDesc *table = nullptr;
@@ -224,16 +340,22 @@ void free_batch(spc5_batch *B) {
   cudaFree(B->lp_mat);
   cudaFree(B->lp_idx);
   cudaFree(B->partial);
+  cudaFree(B->sched);
   delete B;
 }
 
 template <int K, typename VT, typename AT>
 cudaError_t run_batch(const spc5_batch *B, double alpha, double beta, cudaStream_t s) {
   if (B->ntiles > 0) {
-    int64_t blocks = (B->ntiles + (kThreads / 32) - 1) / (kThreads / 32);
+    const int64_t nchunks = (B->ntiles + kBatchChunk - 1) / kBatchChunk;
+    int64_t blocks = (nchunks + (kThreads / 32) - 1) / (kThreads / 32);
     blocks = std::min<int64_t>(blocks, (int64_t)sm_count() * 8);
-    k_batch<K, VT, AT><<<(unsigned)blocks, kThreads, 0, s>>>(B->table, B->tile_mat, B->ntiles,
-                                                              (AT)alpha, (AT)beta);
+    if (B->vec)
+      k_batch<K, true, VT, AT><<<(unsigned)blocks, kThreads, 0, s>>>(
+          B->table, B->tile_mat, B->ntiles, B->sched, (AT)alpha, (AT)beta);
+    else
+      k_batch<K, false, VT, AT><<<(unsigned)blocks, kThreads, 0, s>>>(
+          B->table, B->tile_mat, B->ntiles, B->sched, (AT)alpha, (AT)beta);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -316,6 +438,8 @@ extern "C" spc5_status spc5_batch_create(int nmat, const spc5_matrix *const *A,
     d.c = M->c;
     d.ntiles = (int32_t)M->ntiles;
     d.nlong = (int32_t)M->nlong;
+    d.body = M->body;
+    d.pad = 0;
     pbase[m] = pslots;
     pslots += M->npieces * M->r * k;
     tiles += M->ntiles;
@@ -323,8 +447,15 @@ extern "C" spc5_status spc5_batch_create(int nmat, const spc5_matrix *const *A,
   }
   B->ntiles = tiles;
   B->nlong = nlong;
+  B->vec = 1;
+  for (int m = 0; m < nmat; ++m)
+    if ((reinterpret_cast<uintptr_t>(X[m]) | reinterpret_cast<uintptr_t>(Y[m])) & 15u) B->vec = 0;
   spc5_status st = cuda_check(cudaMalloc(&B->partial, (size_t)std::max<int64_t>(pslots, 1) * slot),
                               "alloc batch partials");
+  if (st == SPC5_OK)
+    st = cuda_check(cudaMalloc((void **)&B->sched, 2 * sizeof(uint32_t)), "alloc batch counter");
+  if (st == SPC5_OK)
+    st = cuda_check(cudaMemsetAsync(B->sched, 0, 2 * sizeof(uint32_t), s), "zero batch counter");
   for (int m = 0; m < nmat; ++m) table[m].partial = (char *)B->partial + pbase[m] * slot;
   if (st == SPC5_OK)
     st = cuda_check(cudaMalloc((void **)&B->table, sizeof(MatDesc) * nmat), "alloc batch table");

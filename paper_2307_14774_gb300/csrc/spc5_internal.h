@@ -110,6 +110,7 @@ struct spc5_matrix {
   int body = 0;                     // consumer body: bit 0 = predicated loop over the c
                                     // bits (else set-bit loop), bit 1 = x staged in smem
   int kernel = 0;                   // 0: direct tile kernel, 1: staged tile kernel
+  int dynamic = 0;                  // row-group kernel: tiles from a counter (else grid-stride)
   double tuned_us = 0.0;            // SpMV time of the plan chosen by spc5_tune (0 = untuned)
   double tuned_rows_us = 0.0;       // SpMV time of the best row-group plan it found
   uint32_t *dev_error = nullptr;    // set by kernels on a timed-out wait
@@ -177,6 +178,7 @@ struct PlanOptions {
   int bcap = -1;    // tile capacity in blocks
   int body = -1;    // consumer body
   int flat = -1;    // 0: row groups, 1: block-balanced plan, 2: expanded plan
+  int dynamic = -1; // row groups: 1 = tiles taken from a counter, 0 = dealt grid-stride
 };
 
 // Work plan of the SpMV kernels; called by the converter while the

@@ -101,21 +101,56 @@ __global__ void __launch_bounds__(kScanThreads)
   }
 }
 
+// Element access of the tile-sum array when the tile sums are themselves
+// scanned by the three passes (more tile sums than one block scans quickly).
+template <typename T>
+struct ArrIn {
+  const T *a;
+  __device__ T operator()(int64_t i) const { return a[i]; }
+};
+template <typename T>
+struct ArrOut {
+  T *a;
+  __device__ void operator()(int64_t i, T v) const { a[i] = v; }
+};
+
+// Tile sums up to this count are scanned by one block (pass 2 above);
+// beyond it, by the three passes again, recursively.
+constexpr int64_t kScanOneBlock = (int64_t)kScanThreads * 32;
+
+// Elements of T that device_scan needs in `tmp` for n elements: the tile
+// sums of every level of the recursion.
+inline int64_t scan_tmp_elems(int64_t n) {
+  int64_t total = 0, m = n <= 0 ? 1 : n;
+  do {
+    m = (m + kScanTile - 1) / kScanTile;
+    total += m;
+  } while (m > kScanOneBlock);
+  return total + 1;
+}
+
 // Host driver: scan n elements read through `in(i)`, written through
-// `out(i, v)`; `tmp` must hold ceil(n / kScanTile) elements of T.
+// `out(i, v)`; `tmp` must hold scan_tmp_elems(n) elements of T.  Pass 2 runs
+// in one block while the tile sums are few; for more tile sums (a conversion
+// of 10^8 entries has about 10^5 tiles) they are scanned in place by the same
+// three passes, so no pass walks more than kScanOneBlock elements serially.
 template <typename T, typename In, typename Out, typename Op>
 cudaError_t device_scan(int64_t n, In in, Out out, Op op, T identity, bool inclusive, T *tmp,
                         cudaStream_t stream) {
   if (n <= 0) return cudaSuccess;
   int64_t ntiles = (n + kScanTile - 1) / kScanTile;
   scan_reduce_tiles<T><<<(unsigned)ntiles, kScanThreads, 0, stream>>>(n, in, op, identity, tmp);
-  scan_tile_sums<T><<<1, kScanThreads, 0, stream>>>(ntiles, op, identity, tmp);
+  if (ntiles <= kScanOneBlock) {
+    scan_tile_sums<T><<<1, kScanThreads, 0, stream>>>(ntiles, op, identity, tmp);
+  } else {
+    cudaError_t e = device_scan<T>(ntiles, ArrIn<T>{tmp}, ArrOut<T>{tmp}, op, identity, false,
+                                   tmp + ntiles, stream);
+    if (e != cudaSuccess) return e;
+  }
   scan_tiles<T><<<(unsigned)ntiles, kScanThreads, 0, stream>>>(n, in, out, op, identity, tmp,
                                                                inclusive);
   return cudaGetLastError();
 }
-
-inline int64_t scan_tmp_elems(int64_t n) { return n <= 0 ? 1 : (n + kScanTile - 1) / kScanTile; }
 
 struct AddI32 {
   __device__ int32_t operator()(int32_t a, int32_t b) const { return a + b; }

@@ -185,7 +185,7 @@ __device__ __forceinline__ void put_empty_row(const Scale<AT> &sc, AT *y, int64_
 // block when its row bits in the current one are used up; the metadata of
 // the block after it is loaded, and its values prefetched to L1, one block
 // ahead.
-template <int R, int C, typename VT, typename AT, typename MaskT>
+template <int R, int C, bool SKIP, typename VT, typename AT, typename MaskT>
 __device__ __forceinline__ AT row_stream(const MaskT *__restrict__ masks,
                                          const int32_t *__restrict__ block_colidx,
                                          const VT *__restrict__ vals, const AT *__restrict__ x,
@@ -207,7 +207,9 @@ __device__ __forceinline__ AT row_stream(const MaskT *__restrict__ masks,
   while (__any_sync(kFull, mq != 0u || b < nbp)) {
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
-      if (mq == 0u && b < nbp) {
+      // SKIP: blocks in which the row has no value are passed within the
+      // trip (the lane does not spend an FMA slot on them)
+      for (int e = 0; mq == 0u && b < nbp && (SKIP || e < 1); ++e) {
         mq = (m1 >> qc) & cmask;
         off = v + __popc(m1 & row_low);
         v += __popc(m1);
@@ -357,21 +359,108 @@ __device__ __forceinline__ AT row_rounds4(const MaskT *__restrict__ masks,
   return acc;
 }
 
+// Block lanes (body 6): the lanes take the r*c bit slots of a block
+// (32 / (r*c) blocks per step, consecutive blocks of one panel), so a step
+// reads the blocks' values as one contiguous run (lanes whose bit is set
+// read consecutive addresses) and the x window of each block once; lane
+// (slot, q, k) adds values[...] * x[start + k] for its bit when it is set,
+// keeps its sum over the panel's blocks, and the panel's r row sums are
+// reduced over the k lanes and block slots by shuffles at the panel's end.
+// The mask and start column of a slot's next block are loaded one step
+// ahead.  The FMA count per step is fixed whatever the filling, so the body
+// suits FP32/BF16 values (FP32 FMAs are cheap) and well-filled blocks.
+template <int R, int C, typename VT, typename AT, typename MaskT>
+__device__ __forceinline__ void block_lanes(const Tile &cur, bool segment, int lane,
+                                            const int32_t *__restrict__ block_rowptr,
+                                            const int32_t *__restrict__ panel_vptr,
+                                            const MaskT *__restrict__ masks,
+                                            const int32_t *__restrict__ block_colidx,
+                                            const VT *__restrict__ vals, const AT *__restrict__ x,
+                                            AT *__restrict__ y, AT *__restrict__ partial,
+                                            const Scale<AT> &sc, int64_t nrows) {
+  constexpr int S = R * C;   // bit slots per block
+  constexpr int B = 32 / S;  // blocks per step
+  constexpr int LOG2C = C == 8 ? 3 : 2;
+  const int bs = lane / S;   // block slot of the step
+  const int j = lane % S;    // bit: row q = j / c, column k = j % c
+  const int q = j >> LOG2C, k = j & (C - 1);
+  const uint32_t below = (1u << j) - 1u;
+  const int np = segment ? 1 : cur.p1 - cur.p0;
+  int32_t nb0 = 0, nb1 = 0, nv = 0;  // the next panel's blocks and first value
+  if (segment) {
+    nb0 = cur.b0;
+    nb1 = cur.b1;
+    nv = cur.v0;
+  } else if (np > 0) {
+    nb0 = block_rowptr[cur.p0];
+    nb1 = block_rowptr[cur.p0 + 1];
+    nv = panel_vptr[cur.p0];
+  }
+  for (int pi = 0; pi < np; ++pi) {
+    const int32_t b0 = nb0, b1 = nb1;
+    int32_t v = nv;
+    if (!segment && pi + 1 < np) {
+      nb0 = b1;
+      nb1 = block_rowptr[cur.p0 + pi + 2];
+      nv = panel_vptr[cur.p0 + pi + 1];
+    }
+    AT acc = 0;
+    int32_t bb = b0 + bs;
+    uint32_t mn = bb < b1 ? (uint32_t)masks[bb] : 0u;
+    int32_t cn = bb < b1 ? block_colidx[bb] : 0;
+    for (int32_t base = b0; base < b1; base += B) {
+      const uint32_t m = mn;
+      const int32_t col = cn;
+      bb = base + B + bs;
+      mn = bb < b1 ? (uint32_t)masks[bb] : 0u;
+      cn = bb < b1 ? block_colidx[bb] : 0;
+      const int pc = __popc(m);
+      int pre = 0, total = pc;
+      if (B > 1) {  // value offset of the slot's block within the step
+        int incl = pc;
+#pragma unroll
+        for (int o = 1; o < B; o <<= 1) {
+          const int t = __shfl_up_sync(kFull, incl, o * S);
+          if (bs >= o) incl += t;
+        }
+        pre = incl - pc;
+        total = __shfl_sync(kFull, incl, 31);
+      }
+      if ((m >> j) & 1u)
+        acc = fma((AT)widen(vals[v + pre + __popc(m & below)]), __ldg(x + col + k), acc);
+      v += total;
+    }
+#pragma unroll
+    for (int o = 1; o < C; o <<= 1) acc += __shfl_xor_sync(kFull, acc, o);
+#pragma unroll
+    for (int o = S; o < 32; o <<= 1) acc += __shfl_xor_sync(kFull, acc, o);
+    if (bs == 0 && k == 0) {
+      if (cur.mode & kPartial) {
+        partial[(int64_t)cur.slot * R + q] = acc;
+      } else {
+        const int64_t row = ((int64_t)cur.p0 + pi) * R + q;
+        if (row < nrows) put_row(sc, y, row, acc);
+      }
+    }
+  }
+}
+
 // Launch shape of the row-group kernel: two CTAs of 24 warps per SM, so
 // that 24 consecutive tiles (neighbouring rows, which share x) run on one
-// SM's L1 at a time (the four-block body holds more registers: 5 x 8 warps).
+// SM's L1 at a time (the four-block body holds more registers: 5 x 8 warps;
+// the block-lane body 3 x 12 warps).
 template <int BODY>
 struct TileThreads {
-  static constexpr int v = BODY == 4 ? 256 : 768;
+  static constexpr int v = BODY == 4 ? 256 : (BODY == 6 ? 384 : 768);
 };
 template <int BODY>
 struct TileBlocksPerSM {
-  static constexpr int v = BODY == 4 ? 5 : 2;
+  static constexpr int v = BODY == 4 ? 5 : (BODY == 6 ? 3 : 2);
 };
 
 template <int R, int C, int BODY, typename VT, typename AT>
 __global__ void __launch_bounds__(TileThreads<BODY>::v, TileBlocksPerSM<BODY>::v)
-    k_spmv_tiles(const Tile *__restrict__ tiles, int64_t ntiles,
+    k_spmv_tiles(const Tile *__restrict__ tiles, int64_t ntiles, uint32_t *sched, int dyn,
                  const int32_t *__restrict__ block_rowptr, const int32_t *__restrict__ panel_vptr,
                  const int32_t *__restrict__ block_colidx,
                  const typename MaskType<R, C>::T *__restrict__ masks,
@@ -381,11 +470,30 @@ __global__ void __launch_bounds__(TileThreads<BODY>::v, TileBlocksPerSM<BODY>::v
   const int lane = threadIdx.x & 31;
   const uint32_t cmask = (1u << C) - 1u;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  // Tiles are dealt grid-stride (warp w takes w, w + nwarps, ...), or, with
+  // `dyn`, taken from a counter two ahead: the index of the tile after next
+  // is requested when a tile starts, so the atomic's latency is hidden; the
+  // last warp to finish resets the counter for the next launch.  The counter
+  // evens out uneven tiles but costs one atomic per tile on one address.
+  uint32_t grab = 0;
+  int64_t t;
+  if (dyn) {
+    if (lane == 0) grab = atomicAdd(&sched[0], 1u);
+    t = (int64_t)__shfl_sync(kFull, grab, 0);
+    if (lane == 0 && t < ntiles) grab = atomicAdd(&sched[0], 1u);
+  } else {
+    t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  }
   Tile cur{0, 0, 0, 0, 0, 0, 0, 0};
   if (t < ntiles) cur = tiles[t];
   while (t < ntiles) {
-    const int64_t tn = t + nwarps;
+    int64_t tn;
+    if (dyn) {
+      tn = (int64_t)__shfl_sync(kFull, grab, 0);
+      if (lane == 0 && tn < ntiles) grab = atomicAdd(&sched[0], 1u);
+    } else {
+      tn = t + nwarps;
+    }
     Tile nxt{0, 0, 0, 0, 0, 0, 0, 0};
     if (tn < ntiles) nxt = tiles[tn];
     {  // start bringing the first 2 KB of the tile's values and 1 KB of its
@@ -397,6 +505,13 @@ __global__ void __launch_bounds__(TileThreads<BODY>::v, TileBlocksPerSM<BODY>::v
         prefetch_l2(block_colidx + cur.b0 + (lane - 16) * 32);
     }
     const bool segment = (cur.mode & kSegment) != 0;
+    if (BODY == 6) {
+      block_lanes<R, C>(cur, segment, lane, block_rowptr, panel_vptr, masks, block_colidx, vals,
+                        x, y, partial, sc, nrows);
+      cur = nxt;
+      t = tn;
+      continue;
+    }
     const int log2G = cur.mode & 15;
     const int G = 1 << log2G;
     const int shift_j = LOG2R + log2G;
@@ -419,8 +534,8 @@ __global__ void __launch_bounds__(TileThreads<BODY>::v, TileBlocksPerSM<BODY>::v
       v = pvalid ? panel_vptr[p] : 0;
     }
     AT acc = 0;
-    if (BODY == 2 && G == 1) {
-      acc = row_stream<R, C>(masks, block_colidx, vals, x, bl, nbp, v, q);
+    if ((BODY == 2 || BODY == 5) && G == 1) {
+      acc = row_stream<R, C, BODY == 5>(masks, block_colidx, vals, x, bl, nbp, v, q);
     } else if (BODY == 3 && G == 1) {
       acc = row_queue<R, C>(masks, block_colidx, vals, x, bl, nbp, v, q);
     } else if (BODY == 4 && G == 1) {
@@ -464,6 +579,13 @@ __global__ void __launch_bounds__(TileThreads<BODY>::v, TileBlocksPerSM<BODY>::v
     }
     cur = nxt;
     t = tn;
+  }
+  // every warp has made its last grab: the last one to finish resets the counter
+  if (dyn && lane == 0) {
+    if (atomicAdd(&sched[1], 1u) == (uint32_t)nwarps - 1) {
+      atomicExch(&sched[0], 0u);
+      atomicExch(&sched[1], 0u);
+    }
   }
 }
 
@@ -1901,7 +2023,7 @@ cudaError_t launch_staged(const spc5_matrix *A, const double *x, double *y, doub
 
 template <int R, int C, int BODY, typename VT, typename AT>
 cudaError_t launch_direct(const spc5_matrix *A, const AT *x, AT *y, double alpha, double beta,
-                          cudaStream_t s, AT *partial) {
+                          cudaStream_t s, AT *partial, uint32_t *sched) {
   using MaskT = typename MaskType<R, C>::T;
   cudaError_t e = cudaSuccess;
   if (A->ntiles > 0) {
@@ -1910,7 +2032,7 @@ cudaError_t launch_direct(const spc5_matrix *A, const AT *x, AT *y, double alpha
     const int64_t resident = (int64_t)num_sms() * TileBlocksPerSM<BODY>::v;
     if (blocks > resident) blocks = resident;
     k_spmv_tiles<R, C, BODY, VT, AT><<<(unsigned)blocks, TileThreads<BODY>::v, 0, s>>>(
-        A->tiles, A->ntiles, A->block_rowptr, A->panel_vptr, A->block_colidx,
+        A->tiles, A->ntiles, sched, A->dynamic, A->block_rowptr, A->panel_vptr, A->block_colidx,
         (const MaskT *)A->masks, (const VT *)A->values, x, y, partial,
           make_scale<AT>(alpha, beta), A->nrows);
     e = cudaGetLastError();
@@ -2016,23 +2138,17 @@ cudaError_t launch_row_starts(spc5_matrix *A, cudaStream_t s) {
 
 template <int R, int C, typename VT, typename AT>
 cudaError_t launch_direct_body(const spc5_matrix *A, const void *x, void *y, double alpha,
-                               double beta, cudaStream_t s, void *partial) {
+                               double beta, cudaStream_t s, void *partial, uint32_t *sched) {
+  const AT *xa = (const AT *)x;
+  AT *ya = (AT *)y, *pa = (AT *)partial;
   switch (A->body) {
-    case 1:
-      return launch_direct<R, C, 1, VT, AT>(A, (const AT *)x, (AT *)y, alpha, beta, s,
-                                            (AT *)partial);
-    case 2:
-      return launch_direct<R, C, 2, VT, AT>(A, (const AT *)x, (AT *)y, alpha, beta, s,
-                                            (AT *)partial);
-    case 3:
-      return launch_direct<R, C, 3, VT, AT>(A, (const AT *)x, (AT *)y, alpha, beta, s,
-                                            (AT *)partial);
-    case 4:
-      return launch_direct<R, C, 4, VT, AT>(A, (const AT *)x, (AT *)y, alpha, beta, s,
-                                            (AT *)partial);
-    default:
-      return launch_direct<R, C, 0, VT, AT>(A, (const AT *)x, (AT *)y, alpha, beta, s,
-                                            (AT *)partial);
+    case 1: return launch_direct<R, C, 1, VT, AT>(A, xa, ya, alpha, beta, s, pa, sched);
+    case 2: return launch_direct<R, C, 2, VT, AT>(A, xa, ya, alpha, beta, s, pa, sched);
+    case 3: return launch_direct<R, C, 3, VT, AT>(A, xa, ya, alpha, beta, s, pa, sched);
+    case 4: return launch_direct<R, C, 4, VT, AT>(A, xa, ya, alpha, beta, s, pa, sched);
+    case 5: return launch_direct<R, C, 5, VT, AT>(A, xa, ya, alpha, beta, s, pa, sched);
+    case 6: return launch_direct<R, C, 6, VT, AT>(A, xa, ya, alpha, beta, s, pa, sched);
+    default: return launch_direct<R, C, 0, VT, AT>(A, xa, ya, alpha, beta, s, pa, sched);
   }
 }
 
@@ -2070,11 +2186,11 @@ cudaError_t launch(const spc5_matrix *A, const void *x, void *y, double alpha, d
                                                (double *)partial, sched);
   }
   if (A->value_dtype == SPC5_F32)
-    return launch_direct_body<R, C, float, float>(A, x, y, alpha, beta, s, partial);
+    return launch_direct_body<R, C, float, float>(A, x, y, alpha, beta, s, partial, sched);
   if (A->value_dtype == SPC5_BF16)
-    return launch_direct_body<R, C, uint16_t, float>(A, x, y, alpha, beta, s, partial);
+    return launch_direct_body<R, C, uint16_t, float>(A, x, y, alpha, beta, s, partial, sched);
   if (A->kernel == 0)
-    return launch_direct_body<R, C, double, double>(A, x, y, alpha, beta, s, partial);
+    return launch_direct_body<R, C, double, double>(A, x, y, alpha, beta, s, partial, sched);
   const double *xd = (const double *)x;
   double *yd = (double *)y, *pd = (double *)partial;
   switch (A->body) {

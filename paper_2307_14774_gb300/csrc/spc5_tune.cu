@@ -70,6 +70,8 @@ spc5_status tune(spc5_matrix *A, const void *x, void *y, int iters, cudaStream_t
   cands.push_back({0, 2, 0});
   cands.push_back({0, 3, 0});
   cands.push_back({0, 4, 0});
+  cands.push_back({0, 5, 0});
+  cands.push_back({0, 6, 0});
   for (int lg = 0; lg <= max_log2g; ++lg) cands.push_back({lg, 0, 0});
   // the predicated loop over the c bits spends an FMA on every bit: cheap
   // with FP32 arithmetic (64 FMAs per cycle per SM), not with FP64 (2)
@@ -109,6 +111,30 @@ spc5_status tune(spc5_matrix *A, const void *x, void *y, int iters, cudaStream_t
     o.flat = cands[best_i].flat;
     spc5_status st = replan(A, s, o);
     if (st != SPC5_OK) return st;
+  }
+  // When row groups win, also try taking their tiles from a counter instead
+  // of dealing them grid-stride (uneven tiles: a few percent either way).
+  if (!cands[best_i].flat) {
+    PlanOptions o;
+    o.kernel = 0;
+    o.log2g = cands[best_rows_i].log2g;
+    o.body = cands[best_rows_i].body;
+    o.flat = 0;
+    o.dynamic = 1;
+    spc5_status st = replan(A, s, o);
+    if (st != SPC5_OK) return st;
+    const double us = time_spmv(A, x, y, iters, s);
+    if (us < 0) {
+      set_error("timing a candidate plan failed");
+      return SPC5_ECUDA;
+    }
+    if (us < best) {
+      best = best_rows = us;
+    } else {
+      o.dynamic = 0;
+      st = replan(A, s, o);
+      if (st != SPC5_OK) return st;
+    }
   }
   A->tuned_us = best;
   A->tuned_rows_us = best_rows;

@@ -179,7 +179,8 @@ def test_invalid_csr_is_rejected_on_device():
 def test_direct_kernel_lane_mappings(monkeypatch, log2g):
     """The direct tile kernel with every lanes-per-row mapping and every row
     body (set-bit loop, predicated loop, row stream, queued row stream,
-    four-block rounds), with and without long-panel pieces."""
+    four-block rounds, row stream passing empty blocks within a trip, block
+    lanes), with and without long-panel pieces."""
     monkeypatch.setenv("SPC5_KERNEL", "0")
     monkeypatch.setenv("SPC5_FLAT", "0")
     monkeypatch.setenv("SPC5_LOG2G_GROUP", str(log2g))
@@ -187,7 +188,7 @@ def test_direct_kernel_lane_mappings(monkeypatch, log2g):
     x = synth.vector_uniform(A.ncols, seed=4)
     y_ref, scale = oracle.csr_spmv(A, x)
     for r, c in [(1, 8), (4, 4), (8, 4)]:
-        for body in ("0", "1", "2", "3", "4"):
+        for body in ("0", "1", "2", "3", "4", "5", "6"):
             for vcap in ("", "2048"):
                 monkeypatch.setenv("SPC5_BODY", body)
                 if vcap:
@@ -255,3 +256,37 @@ def test_integer_exact_with_pieces(monkeypatch, kernel):
         M = convert(A, r, c)
         assert M.info()["long_panels"] > 0
         assert np.array_equal(spmv(M, x), A.todense() @ x)
+
+
+@pytest.mark.parametrize("r,c", BETAS)
+def test_row_groups_from_the_tile_counter(monkeypatch, r, c):
+    """Row-group tiles taken from the self-resetting tile counter instead of
+    grid-stride: every body, with and without pieces, three products in a
+    row (the counter must be back at zero after each launch), through
+    spc5_spmv and spc5_spmv_noalloc (which counts on the library's own
+    counter)."""
+    monkeypatch.setenv("SPC5_KERNEL", "0")
+    monkeypatch.setenv("SPC5_FLAT", "0")
+    monkeypatch.setenv("SPC5_DYNAMIC", "1")
+    A = synth.powerlaw(30_000, seed=21)
+    x = synth.vector_uniform(A.ncols, seed=6)
+    y_ref, scale = oracle.csr_spmv(A, x)
+    torch = torch_cuda()
+    for body in ("0", "1", "2", "3", "4", "5", "6"):
+        for vcap in ("", "2048"):
+            monkeypatch.setenv("SPC5_BODY", body)
+            if vcap:
+                monkeypatch.setenv("SPC5_VCAP", vcap)
+                monkeypatch.setenv("SPC5_BCAP", "256")
+            else:
+                monkeypatch.delenv("SPC5_VCAP", raising=False)
+                monkeypatch.delenv("SPC5_BCAP", raising=False)
+            M = convert(A, r, c)
+            for _ in range(3):
+                assert_within_tol(spmv(M, x), y_ref, scale)
+            dx = torch.from_numpy(x).cuda()
+            dy = torch.full((A.nrows,), float("nan"), dtype=torch.float64, device="cuda")
+            for _ in range(2):
+                spc5.spc5_spmv_noalloc(M, dx, dy)
+                torch.cuda.synchronize()
+                assert_within_tol(dy.cpu().numpy(), y_ref, scale)
