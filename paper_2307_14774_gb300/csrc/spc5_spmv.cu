@@ -359,103 +359,16 @@ __device__ __forceinline__ AT row_rounds4(const MaskT *__restrict__ masks,
   return acc;
 }
 
-// Block lanes (body 6): the lanes take the r*c bit slots of a block
-// (32 / (r*c) blocks per step, consecutive blocks of one panel), so a step
-// reads the blocks' values as one contiguous run (lanes whose bit is set
-// read consecutive addresses) and the x window of each block once; lane
-// (slot, q, k) adds values[...] * x[start + k] for its bit when it is set,
-// keeps its sum over the panel's blocks, and the panel's r row sums are
-// reduced over the k lanes and block slots by shuffles at the panel's end.
-// The mask and start column of a slot's next block are loaded one step
-// ahead.  The FMA count per step is fixed whatever the filling, so the body
-// suits FP32/BF16 values (FP32 FMAs are cheap) and well-filled blocks.
-template <int R, int C, typename VT, typename AT, typename MaskT>
-__device__ __forceinline__ void block_lanes(const Tile &cur, bool segment, int lane,
-                                            const int32_t *__restrict__ block_rowptr,
-                                            const int32_t *__restrict__ panel_vptr,
-                                            const MaskT *__restrict__ masks,
-                                            const int32_t *__restrict__ block_colidx,
-                                            const VT *__restrict__ vals, const AT *__restrict__ x,
-                                            AT *__restrict__ y, AT *__restrict__ partial,
-                                            const Scale<AT> &sc, int64_t nrows) {
-  constexpr int S = R * C;   // bit slots per block
-  constexpr int B = 32 / S;  // blocks per step
-  constexpr int LOG2C = C == 8 ? 3 : 2;
-  const int bs = lane / S;   // block slot of the step
-  const int j = lane % S;    // bit: row q = j / c, column k = j % c
-  const int q = j >> LOG2C, k = j & (C - 1);
-  const uint32_t below = (1u << j) - 1u;
-  const int np = segment ? 1 : cur.p1 - cur.p0;
-  int32_t nb0 = 0, nb1 = 0, nv = 0;  // the next panel's blocks and first value
-  if (segment) {
-    nb0 = cur.b0;
-    nb1 = cur.b1;
-    nv = cur.v0;
-  } else if (np > 0) {
-    nb0 = block_rowptr[cur.p0];
-    nb1 = block_rowptr[cur.p0 + 1];
-    nv = panel_vptr[cur.p0];
-  }
-  for (int pi = 0; pi < np; ++pi) {
-    const int32_t b0 = nb0, b1 = nb1;
-    int32_t v = nv;
-    if (!segment && pi + 1 < np) {
-      nb0 = b1;
-      nb1 = block_rowptr[cur.p0 + pi + 2];
-      nv = panel_vptr[cur.p0 + pi + 1];
-    }
-    AT acc = 0;
-    int32_t bb = b0 + bs;
-    uint32_t mn = bb < b1 ? (uint32_t)masks[bb] : 0u;
-    int32_t cn = bb < b1 ? block_colidx[bb] : 0;
-    for (int32_t base = b0; base < b1; base += B) {
-      const uint32_t m = mn;
-      const int32_t col = cn;
-      bb = base + B + bs;
-      mn = bb < b1 ? (uint32_t)masks[bb] : 0u;
-      cn = bb < b1 ? block_colidx[bb] : 0;
-      const int pc = __popc(m);
-      int pre = 0, total = pc;
-      if (B > 1) {  // value offset of the slot's block within the step
-        int incl = pc;
-#pragma unroll
-        for (int o = 1; o < B; o <<= 1) {
-          const int t = __shfl_up_sync(kFull, incl, o * S);
-          if (bs >= o) incl += t;
-        }
-        pre = incl - pc;
-        total = __shfl_sync(kFull, incl, 31);
-      }
-      if ((m >> j) & 1u)
-        acc = fma((AT)widen(vals[v + pre + __popc(m & below)]), __ldg(x + col + k), acc);
-      v += total;
-    }
-#pragma unroll
-    for (int o = 1; o < C; o <<= 1) acc += __shfl_xor_sync(kFull, acc, o);
-#pragma unroll
-    for (int o = S; o < 32; o <<= 1) acc += __shfl_xor_sync(kFull, acc, o);
-    if (bs == 0 && k == 0) {
-      if (cur.mode & kPartial) {
-        partial[(int64_t)cur.slot * R + q] = acc;
-      } else {
-        const int64_t row = ((int64_t)cur.p0 + pi) * R + q;
-        if (row < nrows) put_row(sc, y, row, acc);
-      }
-    }
-  }
-}
-
 // Launch shape of the row-group kernel: two CTAs of 24 warps per SM, so
 // that 24 consecutive tiles (neighbouring rows, which share x) run on one
-// SM's L1 at a time (the four-block body holds more registers: 5 x 8 warps;
-// the block-lane body 3 x 12 warps).
+// SM's L1 at a time (the four-block body holds more registers: 5 x 8 warps).
 template <int BODY>
 struct TileThreads {
-  static constexpr int v = BODY == 4 ? 256 : (BODY == 6 ? 384 : 768);
+  static constexpr int v = BODY == 4 ? 256 : 768;
 };
 template <int BODY>
 struct TileBlocksPerSM {
-  static constexpr int v = BODY == 4 ? 5 : (BODY == 6 ? 3 : 2);
+  static constexpr int v = BODY == 4 ? 5 : 2;
 };
 
 template <int R, int C, int BODY, typename VT, typename AT>
@@ -505,13 +418,6 @@ __global__ void __launch_bounds__(TileThreads<BODY>::v, TileBlocksPerSM<BODY>::v
         prefetch_l2(block_colidx + cur.b0 + (lane - 16) * 32);
     }
     const bool segment = (cur.mode & kSegment) != 0;
-    if (BODY == 6) {
-      block_lanes<R, C>(cur, segment, lane, block_rowptr, panel_vptr, masks, block_colidx, vals,
-                        x, y, partial, sc, nrows);
-      cur = nxt;
-      t = tn;
-      continue;
-    }
     const int log2G = cur.mode & 15;
     const int G = 1 << log2G;
     const int shift_j = LOG2R + log2G;
@@ -2147,7 +2053,6 @@ cudaError_t launch_direct_body(const spc5_matrix *A, const void *x, void *y, dou
     case 3: return launch_direct<R, C, 3, VT, AT>(A, xa, ya, alpha, beta, s, pa, sched);
     case 4: return launch_direct<R, C, 4, VT, AT>(A, xa, ya, alpha, beta, s, pa, sched);
     case 5: return launch_direct<R, C, 5, VT, AT>(A, xa, ya, alpha, beta, s, pa, sched);
-    case 6: return launch_direct<R, C, 6, VT, AT>(A, xa, ya, alpha, beta, s, pa, sched);
     default: return launch_direct<R, C, 0, VT, AT>(A, xa, ya, alpha, beta, s, pa, sched);
   }
 }
