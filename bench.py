@@ -135,9 +135,15 @@ def fma_peaks(spc5, log):
 
 def plan_label(info):
     """The SpMV's work mapping: blocks (block-balanced), values (value-balanced
-    block rounds), expanded, or rows/G<lanes per row> (row groups)."""
-    return ({1: "blocks", 2: "expanded", 3: "values"}.get(info["flat"])
-            or f"rows/G{info['lanes_per_row']}")
+    block rounds), expanded, or rows/G<lanes per row>/b<body> (row groups,
+    with "/dyn" when tiles come from the counter)."""
+    flat = {1: "blocks", 2: "expanded", 3: "values"}.get(info["flat"])
+    if flat:
+        return flat
+    label = f"rows/G{info['lanes_per_row']}"
+    if "body" in info:
+        label += f"/b{info['body']}" + ("/dyn" if info.get("dynamic") else "")
+    return label
 
 
 def algorithmic_bytes(info: dict) -> int:

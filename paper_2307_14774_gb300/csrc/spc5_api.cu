@@ -280,6 +280,8 @@ spc5_status spc5_matrix_info(const spc5_matrix *A, spc5_info *info) {
   info->nscalars = A->nscalars;
   info->pieces = spmv_pieces(A);
   info->scalar_pieces = A->hybrid ? A->snpieces : 0;
+  info->body = A->body;
+  info->dynamic = A->dynamic;
   info->nnz = A->nnz + A->nscalars;
   info->filling = A->nblocks ? (double)A->nnz / ((double)A->nblocks * A->r * A->c) : 0.0;
   return SPC5_OK;

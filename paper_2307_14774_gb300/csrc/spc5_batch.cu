@@ -217,8 +217,16 @@ __device__ __forceinline__ void batch_tile(const MatDesc &d, const Tile &cur, in
   }
 }
 
+// CTAs of 256 threads per SM that the registers allow: 48 warps for one or
+// two FP32 right-hand sides, fewer as the k accumulators grow (and for FP64).
+template <int K, typename AT>
+struct BatchBlocksPerSM {
+  static constexpr int v = sizeof(AT) == 4 ? (K <= 2 ? 6 : (K <= 4 ? 5 : (K <= 8 ? 4 : 2)))
+                                           : (K <= 2 ? 5 : (K <= 4 ? 4 : (K <= 8 ? 3 : 2)));
+};
+
 template <int K, bool VEC, typename VT, typename AT>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, BatchBlocksPerSM<K, AT>::v)
     k_batch(const MatDesc *__restrict__ table, const int32_t *__restrict__ tile_mat,
             int64_t ntiles, uint32_t *sched, AT alpha, AT beta) {
   const int lane = threadIdx.x & 31;
@@ -228,15 +236,23 @@ __global__ void __launch_bounds__(kThreads)
   uint32_t grab = 0;
   if (lane == 0) grab = atomicAdd(&sched[0], 1u);
   int64_t ch = (int64_t)__shfl_sync(kFull, grab, 0);
+  // the current matrix's table entry, kept in shared memory (registers are
+  // needed for the k accumulators)
+  __shared__ MatDesc s_desc[kThreads / 32];
+  static_assert(sizeof(MatDesc) % 4 == 0 && sizeof(MatDesc) <= 128, "table entry size");
+  MatDesc &d = s_desc[threadIdx.x >> 5];
   int cur_m = -1;
-  MatDesc d;
   while (ch < nchunks) {
     if (lane == 0) grab = atomicAdd(&sched[0], 1u);
     const int64_t t1 = min((ch + 1) * kBatchChunk, ntiles);
     for (int64_t t = ch * kBatchChunk; t < t1; ++t) {
       const int m = tile_mat[t];
       if (m != cur_m) {  // uniform over the warp
-        d = table[m];
+        __syncwarp();
+        if (lane < (int)(sizeof(MatDesc) / 4))
+          reinterpret_cast<uint32_t *>(&d)[lane] =
+              reinterpret_cast<const uint32_t *>(table + m)[lane];
+        __syncwarp();
         cur_m = m;
       }
       const Tile cur = d.tiles[t - d.tile_base];
@@ -349,7 +365,7 @@ cudaError_t run_batch(const spc5_batch *B, double alpha, double beta, cudaStream
   if (B->ntiles > 0) {
     const int64_t nchunks = (B->ntiles + kBatchChunk - 1) / kBatchChunk;
     int64_t blocks = (nchunks + (kThreads / 32) - 1) / (kThreads / 32);
-    blocks = std::min<int64_t>(blocks, (int64_t)sm_count() * 8);
+    blocks = std::min<int64_t>(blocks, (int64_t)sm_count() * BatchBlocksPerSM<K, AT>::v);
     if (B->vec)
       k_batch<K, true, VT, AT><<<(unsigned)blocks, kThreads, 0, s>>>(
           B->table, B->tile_mat, B->ntiles, B->sched, (AT)alpha, (AT)beta);

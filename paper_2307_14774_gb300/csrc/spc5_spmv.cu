@@ -371,9 +371,9 @@ struct TileBlocksPerSM {
   static constexpr int v = BODY == 4 ? 5 : 2;
 };
 
-template <int R, int C, int BODY, typename VT, typename AT>
+template <int R, int C, int BODY, bool DYN, typename VT, typename AT>
 __global__ void __launch_bounds__(TileThreads<BODY>::v, TileBlocksPerSM<BODY>::v)
-    k_spmv_tiles(const Tile *__restrict__ tiles, int64_t ntiles, uint32_t *sched, int dyn,
+    k_spmv_tiles(const Tile *__restrict__ tiles, int64_t ntiles, uint32_t *sched,
                  const int32_t *__restrict__ block_rowptr, const int32_t *__restrict__ panel_vptr,
                  const int32_t *__restrict__ block_colidx,
                  const typename MaskType<R, C>::T *__restrict__ masks,
@@ -384,13 +384,13 @@ __global__ void __launch_bounds__(TileThreads<BODY>::v, TileBlocksPerSM<BODY>::v
   const uint32_t cmask = (1u << C) - 1u;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   // Tiles are dealt grid-stride (warp w takes w, w + nwarps, ...), or, with
-  // `dyn`, taken from a counter two ahead: the index of the tile after next
+  // DYN, taken from a counter two ahead: the index of the tile after next
   // is requested when a tile starts, so the atomic's latency is hidden; the
   // last warp to finish resets the counter for the next launch.  The counter
   // evens out uneven tiles but costs one atomic per tile on one address.
   uint32_t grab = 0;
   int64_t t;
-  if (dyn) {
+  if (DYN) {
     if (lane == 0) grab = atomicAdd(&sched[0], 1u);
     t = (int64_t)__shfl_sync(kFull, grab, 0);
     if (lane == 0 && t < ntiles) grab = atomicAdd(&sched[0], 1u);
@@ -401,7 +401,7 @@ __global__ void __launch_bounds__(TileThreads<BODY>::v, TileBlocksPerSM<BODY>::v
   if (t < ntiles) cur = tiles[t];
   while (t < ntiles) {
     int64_t tn;
-    if (dyn) {
+    if (DYN) {
       tn = (int64_t)__shfl_sync(kFull, grab, 0);
       if (lane == 0 && tn < ntiles) grab = atomicAdd(&sched[0], 1u);
     } else {
@@ -487,7 +487,7 @@ __global__ void __launch_bounds__(TileThreads<BODY>::v, TileBlocksPerSM<BODY>::v
     t = tn;
   }
   // every warp has made its last grab: the last one to finish resets the counter
-  if (dyn && lane == 0) {
+  if (DYN && lane == 0) {
     if (atomicAdd(&sched[1], 1u) == (uint32_t)nwarps - 1) {
       atomicExch(&sched[0], 0u);
       atomicExch(&sched[1], 0u);
@@ -1937,9 +1937,15 @@ cudaError_t launch_direct(const spc5_matrix *A, const AT *x, AT *y, double alpha
     int64_t blocks = (A->ntiles + warps_per_block - 1) / warps_per_block;
     const int64_t resident = (int64_t)num_sms() * TileBlocksPerSM<BODY>::v;
     if (blocks > resident) blocks = resident;
-    k_spmv_tiles<R, C, BODY, VT, AT><<<(unsigned)blocks, TileThreads<BODY>::v, 0, s>>>(
-        A->tiles, A->ntiles, sched, A->dynamic, A->block_rowptr, A->panel_vptr, A->block_colidx,
-        (const MaskT *)A->masks, (const VT *)A->values, x, y, partial,
+    if (A->dynamic)
+      k_spmv_tiles<R, C, BODY, true, VT, AT><<<(unsigned)blocks, TileThreads<BODY>::v, 0, s>>>(
+          A->tiles, A->ntiles, sched, A->block_rowptr, A->panel_vptr, A->block_colidx,
+          (const MaskT *)A->masks, (const VT *)A->values, x, y, partial,
+          make_scale<AT>(alpha, beta), A->nrows);
+    else
+      k_spmv_tiles<R, C, BODY, false, VT, AT><<<(unsigned)blocks, TileThreads<BODY>::v, 0, s>>>(
+          A->tiles, A->ntiles, sched, A->block_rowptr, A->panel_vptr, A->block_colidx,
+          (const MaskT *)A->masks, (const VT *)A->values, x, y, partial,
           make_scale<AT>(alpha, beta), A->nrows);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
