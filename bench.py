@@ -825,6 +825,7 @@ def run_native(args):
                    + "; ".join(DESCR[n] for n in names),
                    "matrices": names, "betas": [f"{r}x{c}" for r, c in BETAS],
                    "spmv_per_step": nlaunch, "nnz_per_step": int(flops_per_step / 2),
+                   "scale": args.scale,
                    "l2": "inputs larger than L2: every SpMV streams >= "
                          f"{min(cs['bytes'] for cs in cases) / 1e6:.0f} MB (L2 129 MB)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",

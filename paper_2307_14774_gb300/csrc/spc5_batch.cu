@@ -45,7 +45,7 @@ struct MatDesc {
   int64_t nrows;
   int64_t tile_base;
   int32_t r, c, ntiles, nlong;
-  int32_t body, pad;  // the matrix's row-group body (2: row stream)
+  int32_t body, pad;  // the matrix's row-group body (2, 6: row stream; 5: passing empty blocks)
 };
 
 constexpr int kBatchChunk = 8;  // consecutive tiles per counter grab
@@ -89,7 +89,7 @@ __device__ __forceinline__ void row_stream_k(const MaskT *__restrict__ masks,
                                              const int32_t *__restrict__ colidx,
                                              const VT *__restrict__ vals,
                                              const AT *__restrict__ x, int32_t bl, int32_t nbp,
-                                             int32_t v, int q, AT (&acc)[K]) {
+                                             int32_t v, int q, bool skip, AT (&acc)[K]) {
   const int qc = q * C;
   const uint32_t row_low = (1u << qc) - 1u;
   const uint32_t cmask = (1u << C) - 1u;
@@ -103,7 +103,8 @@ __device__ __forceinline__ void row_stream_k(const MaskT *__restrict__ masks,
   uint32_t mq = 0u;
   int32_t off = 0, col = 0;
   while (__any_sync(kFull, mq != 0u || b < nbp)) {
-    if (mq == 0u && b < nbp) {
+    // with `skip`, blocks in which the row has no value are passed in one trip
+    for (int e = 0; mq == 0u && b < nbp && (skip || e < 1); ++e) {
       mq = (m1 >> qc) & cmask;
       off = v + __popc(m1 & row_low);
       v += __popc(m1);
@@ -164,8 +165,8 @@ __device__ __forceinline__ void batch_tile(const MatDesc &d, const Tile &cur, in
   AT acc[K];
 #pragma unroll
   for (int i = 0; i < K; ++i) acc[i] = 0;
-  if (d.body == 2 && G == 1) {
-    row_stream_k<R, C, K, VEC>(masks, d.colidx, vals, x, bl, nbp, v, q, acc);
+  if ((d.body == 2 || d.body == 5 || d.body == 6) && G == 1) {
+    row_stream_k<R, C, K, VEC>(masks, d.colidx, vals, x, bl, nbp, v, q, d.body == 5, acc);
   } else {
   const int32_t maxnb = __reduce_max_sync(kFull, nbp);
   for (int32_t it = 0; it < maxnb; it += G) {

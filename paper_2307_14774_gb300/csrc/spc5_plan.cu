@@ -704,7 +704,7 @@ spc5_status plan_tiles(spc5_matrix *A, const uint32_t *mask32, const int32_t *bo
   // 4 four-block rounds (2 to 4 on row-group tiles with one lane per row;
   // other tiles use body 0)
   A->body = staged ? body
-                   : std::min(std::max(opt.body >= 0 ? opt.body : env_int("SPC5_BODY", 0), 0), 5);
+                   : std::min(std::max(opt.body >= 0 ? opt.body : env_int("SPC5_BODY", 0), 0), 6);
   A->dynamic = (opt.dynamic >= 0 ? opt.dynamic : env_int("SPC5_DYNAMIC", 0)) != 0 ? 1 : 0;
 
   if (np == 0) return SPC5_OK;

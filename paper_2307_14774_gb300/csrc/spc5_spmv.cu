@@ -361,10 +361,12 @@ __device__ __forceinline__ AT row_rounds4(const MaskT *__restrict__ masks,
 
 // Launch shape of the row-group kernel: two CTAs of 24 warps per SM, so
 // that 24 consecutive tiles (neighbouring rows, which share x) run on one
-// SM's L1 at a time (the four-block body holds more registers: 5 x 8 warps).
+// SM's L1 at a time (the four-block body holds more registers: 5 x 8 warps;
+// body 6 is the row stream at 2 x 32 warps, 32 registers, for matrices whose
+// products wait on memory more than on issue).
 template <int BODY>
 struct TileThreads {
-  static constexpr int v = BODY == 4 ? 256 : 768;
+  static constexpr int v = BODY == 4 ? 256 : (BODY == 6 ? 1024 : 768);
 };
 template <int BODY>
 struct TileBlocksPerSM {
@@ -383,6 +385,8 @@ __global__ void __launch_bounds__(TileThreads<BODY>::v, TileBlocksPerSM<BODY>::v
   const int lane = threadIdx.x & 31;
   const uint32_t cmask = (1u << C) - 1u;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  __shared__ Tile s_next_all[TileThreads<BODY>::v / 32];
+  Tile *s_next = &s_next_all[threadIdx.x >> 5];
   // Tiles are dealt grid-stride (warp w takes w, w + nwarps, ...), or, with
   // DYN, taken from a counter two ahead: the index of the tile after next
   // is requested when a tile starts, so the atomic's latency is hidden; the
@@ -407,8 +411,11 @@ __global__ void __launch_bounds__(TileThreads<BODY>::v, TileBlocksPerSM<BODY>::v
     } else {
       tn = t + nwarps;
     }
-    Tile nxt{0, 0, 0, 0, 0, 0, 0, 0};
-    if (tn < ntiles) nxt = tiles[tn];
+    // the next tile's descriptor waits in shared memory, not in registers
+    __syncwarp();
+    if (lane < 8)
+      reinterpret_cast<int32_t *>(s_next)[lane] =
+          tn < ntiles ? reinterpret_cast<const int32_t *>(tiles + tn)[lane] : 0;
     {  // start bringing the first 2 KB of the tile's values and 1 KB of its
        // block columns to L2: the tile's first rounds wait on them (more
        // would evict x from L2 on large tiles)
@@ -440,7 +447,7 @@ __global__ void __launch_bounds__(TileThreads<BODY>::v, TileBlocksPerSM<BODY>::v
       v = pvalid ? panel_vptr[p] : 0;
     }
     AT acc = 0;
-    if ((BODY == 2 || BODY == 5) && G == 1) {
+    if ((BODY == 2 || BODY == 5 || BODY == 6) && G == 1) {
       acc = row_stream<R, C, BODY == 5>(masks, block_colidx, vals, x, bl, nbp, v, q);
     } else if (BODY == 3 && G == 1) {
       acc = row_queue<R, C>(masks, block_colidx, vals, x, bl, nbp, v, q);
@@ -483,7 +490,8 @@ __global__ void __launch_bounds__(TileThreads<BODY>::v, TileBlocksPerSM<BODY>::v
         if (row < nrows) put_row(sc, y, row, acc);
       }
     }
-    cur = nxt;
+    __syncwarp();
+    cur = *s_next;
     t = tn;
   }
   // every warp has made its last grab: the last one to finish resets the counter
@@ -2059,6 +2067,7 @@ cudaError_t launch_direct_body(const spc5_matrix *A, const void *x, void *y, dou
     case 3: return launch_direct<R, C, 3, VT, AT>(A, xa, ya, alpha, beta, s, pa, sched);
     case 4: return launch_direct<R, C, 4, VT, AT>(A, xa, ya, alpha, beta, s, pa, sched);
     case 5: return launch_direct<R, C, 5, VT, AT>(A, xa, ya, alpha, beta, s, pa, sched);
+    case 6: return launch_direct<R, C, 6, VT, AT>(A, xa, ya, alpha, beta, s, pa, sched);
     default: return launch_direct<R, C, 0, VT, AT>(A, xa, ya, alpha, beta, s, pa, sched);
   }
 }

@@ -179,8 +179,8 @@ def test_invalid_csr_is_rejected_on_device():
 def test_direct_kernel_lane_mappings(monkeypatch, log2g):
     """The direct tile kernel with every lanes-per-row mapping and every row
     body (set-bit loop, predicated loop, row stream, queued row stream,
-    four-block rounds, row stream passing empty blocks within a trip), with
-    and without long-panel pieces."""
+    four-block rounds, row stream passing empty blocks within a trip, row
+    stream at 64 warps per SM), with and without long-panel pieces."""
     monkeypatch.setenv("SPC5_KERNEL", "0")
     monkeypatch.setenv("SPC5_FLAT", "0")
     monkeypatch.setenv("SPC5_LOG2G_GROUP", str(log2g))
@@ -188,7 +188,7 @@ def test_direct_kernel_lane_mappings(monkeypatch, log2g):
     x = synth.vector_uniform(A.ncols, seed=4)
     y_ref, scale = oracle.csr_spmv(A, x)
     for r, c in [(1, 8), (4, 4), (8, 4)]:
-        for body in ("0", "1", "2", "3", "4", "5"):
+        for body in ("0", "1", "2", "3", "4", "5", "6"):
             for vcap in ("", "2048"):
                 monkeypatch.setenv("SPC5_BODY", body)
                 if vcap:
@@ -272,7 +272,7 @@ def test_row_groups_from_the_tile_counter(monkeypatch, r, c):
     x = synth.vector_uniform(A.ncols, seed=6)
     y_ref, scale = oracle.csr_spmv(A, x)
     torch = torch_cuda()
-    for body in ("0", "1", "2", "3", "4", "5"):
+    for body in ("0", "1", "2", "3", "4", "5", "6"):
         for vcap in ("", "2048"):
             monkeypatch.setenv("SPC5_BODY", body)
             if vcap:

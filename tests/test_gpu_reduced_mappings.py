@@ -2,7 +2,7 @@
 the row-group plan with every lanes-per-row count G in {1, 2, 4, 8} and every
 row body (set-bit loop, predicated loop over the c bits, row stream, queued
 row stream, four-block rounds, row stream passing empty blocks within a
-trip), with and without long panels cut into
+trip, row stream at 64 warps per SM), with and without long panels cut into
 pieces, and the block-balanced, expanded and value-balanced plans, for every
 beta(r,c).  Each product is checked against the FP64 oracle on the original
 values at the stated tolerance (2e-6 / 1e-2 * sum_j |a_ij x_j|) and, for the
@@ -63,7 +63,7 @@ def test_row_groups_every_lane_count_and_body(monkeypatch, case, dtype, log2g):
     monkeypatch.setenv("SPC5_FLAT", "0")
     monkeypatch.setenv("SPC5_LOG2G_GROUP", str(log2g))
     for r, c in BETAS:
-        for body in ("0", "1", "2", "3", "4", "5"):
+        for body in ("0", "1", "2", "3", "4", "5", "6"):
             for vcap in ("", "2048"):
                 monkeypatch.setenv("SPC5_BODY", body)
                 if vcap:
