@@ -222,7 +222,7 @@ __device__ __forceinline__ void batch_tile(const MatDesc &d, const Tile &cur, in
 // two FP32 right-hand sides, fewer as the k accumulators grow (and for FP64).
 template <int K, typename AT>
 struct BatchBlocksPerSM {
-  static constexpr int v = sizeof(AT) == 4 ? (K <= 2 ? 6 : (K <= 4 ? 5 : (K <= 8 ? 4 : 2)))
+  static constexpr int v = sizeof(AT) == 4 ? (K <= 2 ? 6 : (K <= 4 ? 5 : (K <= 8 ? 4 : 3)))
                                            : (K <= 2 ? 5 : (K <= 4 ? 4 : (K <= 8 ? 3 : 2)));
 };
 
