@@ -19,7 +19,9 @@ event-timed duration) with its fraction of the measured FP64 FMA rate
 beside it, every case's error against the CPU oracle, an end-to-end figure
 through the C-ABI with host vectors (pinned x and y copied every step), and
 the oracle's CSR product timed on the host cores (one thread and all
-cores, whole matrices).
+cores, whole matrices).  Extra sections (outside the step): FP32/BF16
+storage, the batched kernel, mixed-precision CG, the autograd backward,
+the hybrid form, and the paper's dense 2048 x 2048 matrix.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 """
@@ -72,6 +74,7 @@ def parse_args():
     ap.add_argument("--no-cg", action="store_true")
     ap.add_argument("--no-grad", action="store_true")
     ap.add_argument("--no-hybrid", action="store_true")
+    ap.add_argument("--no-dense", action="store_true")
     ap.add_argument("--no-tune", action="store_true",
                     help="keep the planner's default mapping instead of autotuning it")
     ap.add_argument("--cases-out", default=None, help="write the per-case table here")
@@ -426,6 +429,50 @@ def hybrid_section(hosts, torch, spc5, stream, hbm, case_rows, log, reps=10, tun
         torch.cuda.synchronize()
         log(f"hybrid rows for {name} done")
     return rows
+
+
+def dense_section(torch, spc5, synth, stream, hbm, log, n=2048, reps=20, tune=True):
+    """The paper's dense n x n matrix (filling 100%: every block full), every
+    beta, FP64: time per SpMV against the HBM roofline and the FP64 FMA
+    floor.  Its 33.6 MB of values fit in the 129 MB L2, so a buffer larger
+    than L2 is written before every timed launch (each launch starts cold)."""
+    A = synth.dense(n, n, values="normal")
+    x = synth.vector_uniform(n, seed=0)
+    dev = [torch.from_numpy(a).cuda() for a in (A.rowptr, A.colidx, A.vals)]
+    dx = torch.from_numpy(x).cuda()
+    dy = torch.empty(n, dtype=torch.float64, device="cuda")
+    flush = torch.empty(256 * 2**20, dtype=torch.uint8, device="cuda")
+    rows = []
+    for r, c in BETAS:
+        M = spc5.spc5_convert_csr(A.nrows, A.ncols, A.nnz, *dev, r=r, c=c)
+        if tune:
+            spc5.spc5_tune(M, dx, dy, iters=3)
+        info = M.info()
+        for _ in range(3):
+            spc5.spc5_spmv(M, dx, dy, 1.0, 0.0, stream)
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            spc5.spc5_spmv(M, dx, dy, 1.0, 0.0, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1) * 1e3)
+        us = statistics.median(ts)
+        b = algorithmic_bytes(info)
+        rows.append({"beta": f"{r}x{c}", "us": round(us, 2), "nblocks": info["nblocks"],
+                     "filling": round(info["filling"], 4),
+                     "gflops": round(2.0 * A.nnz / (us * 1e-6) / 1e9, 1),
+                     "gbs": round(b / (us * 1e-6) / 1e9, 1),
+                     "frac": round(b / (us * 1e-6) / 1e9 / hbm, 3),
+                     "plan": plan_label(info)})
+        del M
+    del dev, flush
+    torch.cuda.synchronize()
+    log("dense rows done")
+    return {"n": n, "nnz": A.nnz, "note": "the paper's dense matrix, FP64, L2 flushed (a 256 MB "
+            "write) before every timed launch; median of " + str(reps), "rows": rows}
 
 
 def cg_section(torch, spc5, synth, stream, hbm, log):
@@ -874,6 +921,9 @@ def run_native(args):
         result["ircg"] = cg_section(torch, spc5, synth, stream, hbm, log)
     if not args.no_grad and rank == 0:
         result["autograd"] = grad_section(torch, spc5, synth, hbm, log)
+    if not args.no_dense and rank == 0:
+        result["dense"] = dense_section(torch, spc5, synth, stream, hbm, log,
+                                        tune=not args.no_tune)
     if not args.no_hybrid and rank == 0:
         result["hybrid"] = {
             "note": "single-value blocks stored as scalar CSR entries (FP64); algorithmic bytes "

@@ -100,7 +100,8 @@ typedef struct {
   int32_t body;            /* row-group plan's loop: 0 per-block set-bit loop, 1 predicated
                               loop over the c bits, 2 row stream, 3 queued row stream,
                               4 four-block rounds, 5 row stream passing empty blocks,
-                              6 row stream at 64 warps per SM */
+                              6 row stream at 64 warps per SM, 7 pipelined row stream
+                              passing empty blocks */
   int32_t dynamic;         /* 1 if row-group tiles are taken from a counter, 0 grid-stride */
 } spc5_info;
 

@@ -45,7 +45,8 @@ struct MatDesc {
   int64_t nrows;
   int64_t tile_base;
   int32_t r, c, ntiles, nlong;
-  int32_t body, pad;  // the matrix's row-group body (2, 6: row stream; 5: passing empty blocks)
+  int32_t body, pad;  // the matrix's row-group body (2, 6: row stream; 5, 7: passing empty
+                      // blocks)
 };
 
 constexpr int kBatchChunk = 8;  // consecutive tiles per counter grab
@@ -165,8 +166,9 @@ __device__ __forceinline__ void batch_tile(const MatDesc &d, const Tile &cur, in
   AT acc[K];
 #pragma unroll
   for (int i = 0; i < K; ++i) acc[i] = 0;
-  if ((d.body == 2 || d.body == 5 || d.body == 6) && G == 1) {
-    row_stream_k<R, C, K, VEC>(masks, d.colidx, vals, x, bl, nbp, v, q, d.body == 5, acc);
+  if ((d.body == 2 || d.body == 5 || d.body == 6 || d.body == 7) && G == 1) {
+    row_stream_k<R, C, K, VEC>(masks, d.colidx, vals, x, bl, nbp, v, q,
+                               d.body == 5 || d.body == 7, acc);
   } else {
   const int32_t maxnb = __reduce_max_sync(kFull, nbp);
   for (int32_t it = 0; it < maxnb; it += G) {

@@ -658,6 +658,17 @@ spc5_status plan_tiles(spc5_matrix *A, const uint32_t *mask32, const int32_t *bo
   } else {
     vcap = std::min(std::max(round_up((int)(2.0 * gp * avg_v) + 64, 64), 2048), 8192);
     bcap = std::min(std::max(round_up((int)(2.0 * gp * avg_b) + 32, 32), 256), 2048);
+    // A small matrix with long rows (the dense 2048 x 2048 has 64 groups of
+    // eight 4-row panels, 65536 values each) gives far fewer tiles than the
+    // GPU holds warps: lower the caps until its long panels are cut into
+    // about four pieces per resident warp.  (Small matrices with short rows
+    // keep their groups: they are cheap, and batches supply the parallelism.)
+    const int64_t warps = (int64_t)device_sm_count() * 48;
+    if ((np + gp - 1) / gp < 2 * warps && gp * avg_v >= 4096.0) {
+      const int64_t vper = A->nnz / (4 * warps), bper = nb / (4 * warps);
+      vcap = (int)std::min<int64_t>(vcap, std::max<int64_t>(round_up((int)vper, 64), 256));
+      bcap = (int)std::min<int64_t>(bcap, std::max<int64_t>(round_up((int)bper, 32), 32));
+    }
   }
   vcap = opt.vcap > 0 ? opt.vcap : env_int("SPC5_VCAP", vcap);
   bcap = opt.bcap > 0 ? opt.bcap : env_int("SPC5_BCAP", bcap);
@@ -701,10 +712,11 @@ spc5_status plan_tiles(spc5_matrix *A, const uint32_t *mask32, const int32_t *bo
   A->stage_bytes = stage;
   // direct kernel bodies: 0 per-block set-bit loop, 1 per-block predicated
   // loop over the c bits, 2 row stream across blocks, 3 queued row stream,
-  // 4 four-block rounds (2 to 4 on row-group tiles with one lane per row;
-  // other tiles use body 0)
+  // 4 four-block rounds, 5 row stream passing empty blocks, 6 row stream at
+  // 64 warps per SM, 7 pipelined row stream passing empty blocks (2 to 7 on
+  // row-group tiles with one lane per row; other tiles use body 0)
   A->body = staged ? body
-                   : std::min(std::max(opt.body >= 0 ? opt.body : env_int("SPC5_BODY", 0), 0), 6);
+                   : std::min(std::max(opt.body >= 0 ? opt.body : env_int("SPC5_BODY", 0), 0), 7);
   A->dynamic = (opt.dynamic >= 0 ? opt.dynamic : env_int("SPC5_DYNAMIC", 0)) != 0 ? 1 : 0;
 
   if (np == 0) return SPC5_OK;

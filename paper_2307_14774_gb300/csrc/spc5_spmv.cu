@@ -233,6 +233,77 @@ __device__ __forceinline__ AT row_stream(const MaskT *__restrict__ masks,
   return acc;
 }
 
+// Pipelined row stream (passing empty blocks): the walk of row_stream, but
+// the operands of a product (the value and its x) are loaded two trips
+// before its FMA, into two register slots used in turn.  In row_stream a
+// trip's FMA waits for loads issued in the same trip; here every warp keeps
+// three trips of loads in flight, which pays off where the rows are regular
+// (stencils) and the FMA waits on memory.
+template <int R, int C, typename VT, typename AT, typename MaskT>
+__device__ __forceinline__ AT row_pipe(const MaskT *__restrict__ masks,
+                                       const int32_t *__restrict__ block_colidx,
+                                       const VT *__restrict__ vals, const AT *__restrict__ x,
+                                       int32_t bl, int32_t nbp, int32_t v, int q) {
+  const int qc = q * C;
+  const uint32_t row_low = (1u << qc) - 1u;
+  const uint32_t cmask = (1u << C) - 1u;
+  uint32_t m1 = 0u;  // next block to enter: mask word and start column
+  int32_t c1 = 0;
+  if (nbp > 0) {
+    m1 = (uint32_t)masks[bl];
+    c1 = block_colidx[bl];
+  }
+  int32_t b = 0;  // blocks entered
+  uint32_t mq = 0u;
+  int32_t off = 0, col = 0;
+  // Moves the cursor to the row's next value (entering as many blocks as it
+  // takes) and loads its operands into (pv, px); false when the row is done.
+  auto fetch = [&](VT &pv, AT &px) -> bool {
+    while (mq == 0u && b < nbp) {
+      mq = (m1 >> qc) & cmask;
+      off = v + __popc(m1 & row_low);
+      v += __popc(m1);
+      col = c1;
+      ++b;
+      m1 = 0u;
+      if (b < nbp) {
+        m1 = (uint32_t)masks[bl + b];
+        c1 = block_colidx[bl + b];
+        prefetch_l1(vals + v);
+      }
+    }
+    if (mq == 0u) return false;
+    const int k = __ffs(mq) - 1;
+    mq &= mq - 1u;
+    pv = vals[off];
+    px = __ldg(x + col + k);
+    ++off;
+    return true;
+  };
+  VT va = VT(0), vb = VT(0);
+  AT xa = AT(0), xb = AT(0);
+  bool ha = fetch(va, xa);
+  bool hb = fetch(vb, xb);
+  AT acc = 0;
+  while (__any_sync(kFull, ha || hb)) {
+    {  // slot a was filled two trips ago
+      const VT cv = va;
+      const AT cx = xa;
+      const bool ch = ha;
+      ha = fetch(va, xa);
+      if (ch) acc = fma((AT)widen(cv), cx, acc);
+    }
+    {  // slot b one trip ago
+      const VT cv = vb;
+      const AT cx = xb;
+      const bool ch = hb;
+      hb = fetch(vb, xb);
+      if (ch) acc = fma((AT)widen(cv), cx, acc);
+    }
+  }
+  return acc;
+}
+
 // Queued row-stream body (one lane per row): the lane loads the metadata of
 // its panel's next four blocks at once and packs its row's bits of the four
 // blocks into one word (block i at bits [i*c, (i+1)*c)), with each block's
@@ -449,6 +520,8 @@ __global__ void __launch_bounds__(TileThreads<BODY>::v, TileBlocksPerSM<BODY>::v
     AT acc = 0;
     if ((BODY == 2 || BODY == 5 || BODY == 6) && G == 1) {
       acc = row_stream<R, C, BODY == 5>(masks, block_colidx, vals, x, bl, nbp, v, q);
+    } else if (BODY == 7 && G == 1) {
+      acc = row_pipe<R, C>(masks, block_colidx, vals, x, bl, nbp, v, q);
     } else if (BODY == 3 && G == 1) {
       acc = row_queue<R, C>(masks, block_colidx, vals, x, bl, nbp, v, q);
     } else if (BODY == 4 && G == 1) {
@@ -2068,6 +2141,7 @@ cudaError_t launch_direct_body(const spc5_matrix *A, const void *x, void *y, dou
     case 4: return launch_direct<R, C, 4, VT, AT>(A, xa, ya, alpha, beta, s, pa, sched);
     case 5: return launch_direct<R, C, 5, VT, AT>(A, xa, ya, alpha, beta, s, pa, sched);
     case 6: return launch_direct<R, C, 6, VT, AT>(A, xa, ya, alpha, beta, s, pa, sched);
+    case 7: return launch_direct<R, C, 7, VT, AT>(A, xa, ya, alpha, beta, s, pa, sched);
     default: return launch_direct<R, C, 0, VT, AT>(A, xa, ya, alpha, beta, s, pa, sched);
   }
 }

@@ -72,6 +72,7 @@ spc5_status tune(spc5_matrix *A, const void *x, void *y, int iters, cudaStream_t
   cands.push_back({0, 4, 0});
   cands.push_back({0, 5, 0});
   cands.push_back({0, 6, 0});
+  cands.push_back({0, 7, 0});
   for (int lg = 0; lg <= max_log2g; ++lg) cands.push_back({lg, 0, 0});
   // the predicated loop over the c bits spends an FMA on every bit: cheap
   // with FP32 arithmetic (64 FMAs per cycle per SM), not with FP64 (2)

@@ -50,6 +50,7 @@ def test_plan_labels(bench):
     assert bench.plan_label(_info(flat=0, lanes_per_row=4)) == "rows/G4"
     assert bench.plan_label(_info(flat=0, lanes_per_row=1, body=2, dynamic=1)) == "rows/G1/b2/dyn"
     assert bench.plan_label(_info(flat=0, lanes_per_row=2, body=0, dynamic=0)) == "rows/G2/b0"
+    assert bench.plan_label(_info(flat=0, lanes_per_row=1, body=7, dynamic=1)) == "rows/G1/b7/dyn"
 
 
 def test_source_hash_ignores_comments_only(bench, tmp_path, monkeypatch):

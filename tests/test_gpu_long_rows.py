@@ -11,7 +11,7 @@ import pytest
 import oracle
 import paper_2307_14774_gb300 as spc5
 import synth
-from gpuhelpers import assert_within_tol, spmv, to_device, torch_cuda
+from gpuhelpers import assert_within_tol, convert, spmv, to_device, torch_cuda
 
 pytestmark = pytest.mark.gpu
 
@@ -80,3 +80,23 @@ def test_long_rows_batched(long_rows, k):
         for j in range(k):
             y_ref, scale = oracle.csr_spmv(A, X[:, j])
             assert_within_tol(Yh[:, j], y_ref, scale)
+
+
+@pytest.mark.parametrize("r,c", [(1, 8), (2, 4), (2, 8), (4, 4), (4, 8), (8, 4)])
+def test_small_dense_matrix_is_cut_into_pieces(monkeypatch, r, c):
+    """A small matrix with long rows (dense 600 x 700) gives few row groups;
+    the planner cuts its panels into pieces so that every SM gets work, and
+    the pieces' partial sums are added by the fixup kernel: same result as
+    the oracle, every row written (y starts as NaN)."""
+    monkeypatch.setenv("SPC5_KERNEL", "0")
+    monkeypatch.setenv("SPC5_FLAT", "0")
+    for key in ("SPC5_VCAP", "SPC5_BCAP", "SPC5_BODY", "SPC5_LOG2G_GROUP"):
+        monkeypatch.delenv(key, raising=False)
+    A = synth.dense(600, 700, values="normal")
+    x = synth.vector_uniform(A.ncols, seed=9)
+    y_ref, scale = oracle.csr_spmv(A, x)
+    M = convert(A, r, c)
+    info = M.info()
+    assert info["long_panels"] == info["npanels"] and info["pieces"] >= 2 * info["npanels"]
+    for _ in range(2):
+        assert_within_tol(spmv(M, x), y_ref, scale)

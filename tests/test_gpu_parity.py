@@ -180,7 +180,8 @@ def test_direct_kernel_lane_mappings(monkeypatch, log2g):
     """The direct tile kernel with every lanes-per-row mapping and every row
     body (set-bit loop, predicated loop, row stream, queued row stream,
     four-block rounds, row stream passing empty blocks within a trip, row
-    stream at 64 warps per SM), with and without long-panel pieces."""
+    stream at 64 warps per SM, pipelined row stream), with and without
+    long-panel pieces."""
     monkeypatch.setenv("SPC5_KERNEL", "0")
     monkeypatch.setenv("SPC5_FLAT", "0")
     monkeypatch.setenv("SPC5_LOG2G_GROUP", str(log2g))
@@ -188,7 +189,7 @@ def test_direct_kernel_lane_mappings(monkeypatch, log2g):
     x = synth.vector_uniform(A.ncols, seed=4)
     y_ref, scale = oracle.csr_spmv(A, x)
     for r, c in [(1, 8), (4, 4), (8, 4)]:
-        for body in ("0", "1", "2", "3", "4", "5", "6"):
+        for body in ("0", "1", "2", "3", "4", "5", "6", "7"):
             for vcap in ("", "2048"):
                 monkeypatch.setenv("SPC5_BODY", body)
                 if vcap:
@@ -272,7 +273,7 @@ def test_row_groups_from_the_tile_counter(monkeypatch, r, c):
     x = synth.vector_uniform(A.ncols, seed=6)
     y_ref, scale = oracle.csr_spmv(A, x)
     torch = torch_cuda()
-    for body in ("0", "1", "2", "3", "4", "5", "6"):
+    for body in ("0", "1", "2", "3", "4", "5", "6", "7"):
         for vcap in ("", "2048"):
             monkeypatch.setenv("SPC5_BODY", body)
             if vcap:
@@ -290,3 +291,4 @@ def test_row_groups_from_the_tile_counter(monkeypatch, r, c):
                 spc5.spc5_spmv_noalloc(M, dx, dy)
                 torch.cuda.synchronize()
                 assert_within_tol(dy.cpu().numpy(), y_ref, scale)
+

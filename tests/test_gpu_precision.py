@@ -90,7 +90,7 @@ def test_reduced_precision_spmv_error(mats, dtype, r, c):
         assert np.all(np.abs(y - y_dq) <= (k + 2) * 2.0 ** -24 * scale_dq)
 
 
-@pytest.mark.parametrize("body", ["0", "1", "2", "3", "4", "5", "6"])
+@pytest.mark.parametrize("body", ["0", "1", "2", "3", "4", "5", "6", "7"])
 @pytest.mark.parametrize("dtype", list(DTYPES))
 def test_reduced_precision_integer_exact(monkeypatch, dtype, body):
     monkeypatch.setenv("SPC5_FLAT", "0")

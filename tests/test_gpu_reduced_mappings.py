@@ -63,7 +63,7 @@ def test_row_groups_every_lane_count_and_body(monkeypatch, case, dtype, log2g):
     monkeypatch.setenv("SPC5_FLAT", "0")
     monkeypatch.setenv("SPC5_LOG2G_GROUP", str(log2g))
     for r, c in BETAS:
-        for body in ("0", "1", "2", "3", "4", "5", "6"):
+        for body in ("0", "1", "2", "3", "4", "5", "6", "7"):
             for vcap in ("", "2048"):
                 monkeypatch.setenv("SPC5_BODY", body)
                 if vcap:
