@@ -661,11 +661,13 @@ spc5_status plan_tiles(spc5_matrix *A, const uint32_t *mask32, const int32_t *bo
     // A small matrix with long rows (the dense 2048 x 2048 has 64 groups of
     // eight 4-row panels, 65536 values each) gives far fewer tiles than the
     // GPU holds warps: lower the caps until its long panels are cut into
-    // about four pieces per resident warp.  (Small matrices with short rows
-    // keep their groups: they are cheap, and batches supply the parallelism.)
+    // about one piece per two resident warps (measured on the dense matrix:
+    // finer pieces cost more in partial sums than they gain in balance).
+    // Small matrices with short rows keep their groups: they are cheap, and
+    // batches supply the parallelism.
     const int64_t warps = (int64_t)device_sm_count() * 48;
     if ((np + gp - 1) / gp < 2 * warps && gp * avg_v >= 4096.0) {
-      const int64_t vper = A->nnz / (4 * warps), bper = nb / (4 * warps);
+      const int64_t vper = 2 * A->nnz / warps, bper = 2 * nb / warps;
       vcap = (int)std::min<int64_t>(vcap, std::max<int64_t>(round_up((int)vper, 64), 256));
       bcap = (int)std::min<int64_t>(bcap, std::max<int64_t>(round_up((int)bper, 32), 32));
     }

@@ -1177,9 +1177,12 @@ __device__ __forceinline__ uint64_t packed_counts(uint32_t m) {
 
 template <int R>
 __device__ __forceinline__ int32_t packed_field(uint64_t w, int q) {
-  if (R == 1) return (int32_t)w;
-  constexpr int F = 64 / R;
-  return (int32_t)((w >> (q * F)) & ((1ull << F) - 1ull));
+  if constexpr (R == 1) {
+    return (int32_t)w;
+  } else {
+    constexpr int F = 64 / R;
+    return (int32_t)((w >> (q * F)) & ((1ull << F) - 1ull));
+  }
 }
 
 // Inclusive scan of `w` over lanes with the same key (keys ascend with the lane).
