@@ -158,7 +158,8 @@ __device__ __forceinline__ void batch_tile(const MatDesc &d, const Tile &cur, in
     v = cur.v0;
   } else {
     const int64_t p = (int64_t)cur.p0 + j;
-    pvalid = p < cur.p1;
+    // a heavy panel (kSkip) has tiles of its own
+    pvalid = p < cur.p1 && !((cur.mode & kSkip) && (((uint32_t)cur.slot >> j) & 1u));
     bl = pvalid ? d.brp[p] : 0;
     nbp = pvalid ? d.brp[p + 1] - bl : 0;
     v = pvalid ? d.vptr[p] : 0;

@@ -56,7 +56,8 @@ __device__ __forceinline__ void walk_tile(const Tile &cur, int lane,
     v = cur.v0;
   } else {
     p = (int64_t)cur.p0 + j;
-    pvalid = p < cur.p1;
+    // a heavy panel (kSkip) has tiles of its own
+    pvalid = p < cur.p1 && !((cur.mode & kSkip) && (((uint32_t)cur.slot >> j) & 1u));
     bl = pvalid ? brp[p] : 0;
     nbp = pvalid ? brp[p + 1] - bl : 0;
     v = pvalid ? vptr[p] : 0;

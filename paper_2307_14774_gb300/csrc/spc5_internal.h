@@ -12,7 +12,10 @@ namespace spc5 {
 
 // One unit of SpMV work, produced by the planner at conversion time.
 //   group tile:   whole panels [p0, p1), lanes-per-row 2^(mode & 15); the
-//                 kernel stages the tile's block_rowptr and panel_vptr slices
+//                 kernel stages the tile's block_rowptr and panel_vptr slices;
+//                 with mode & kSkip, bit j of `slot` marks panel p0 + j as
+//                 handled by tiles of its own (a heavy panel), so the group
+//                 tile leaves its rows alone
 //   segment tile: blocks [b0, b1) of the single panel p0 (mode & kSegment),
 //                 32/r lanes per row; with mode & kPartial the r row sums go
 //                 to partial[slot * r + q] and a fixup adds the pieces.
@@ -34,6 +37,7 @@ constexpr int32_t kSegment = 16;
 constexpr int32_t kPartial = 32;
 constexpr int32_t kFlat = 64;
 constexpr int32_t kExpand = 128;
+constexpr int32_t kSkip = 256;
 
 // Expanded tiles: at most kExpandCap values and kExpandRows rows (shared
 // memory of the expanded SpMV kernel); panels are packed by windows of

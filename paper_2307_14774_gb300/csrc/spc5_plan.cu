@@ -9,7 +9,13 @@
 //     its own segment tile (32 / r lanes per row) when it fits, otherwise a
 //     long panel, cut at block boundaries into pieces that fit; a piece's
 //     row sums go to a partial buffer and a fixup kernel adds the pieces of
-//     each long panel in order (deterministic, no atomics).
+//     each long panel in order (deterministic, no atomics);
+//   - direct kernel: only the group's heavy panels (more than eight times
+//     the mean panel's values or blocks, and every panel that fits no tile)
+//     leave it, as segment tiles or long panels; the group tile keeps the
+//     other panels and skips the heavy ones (mode & kSkip, a mask in
+//     `slot`), so one long row of a skewed matrix neither holds up the 31
+//     rows around it nor turns them into 31 tiles of one panel each.
 // Piece boundaries are where the block's value offset or block index enters
 // a new window of (vcap - 32) values or bcap blocks; a block holds at most
 // 32 values, so every piece fits a stage.
@@ -45,6 +51,8 @@ struct PlanParams {
   int32_t vcap, bcap, vwin;
   int32_t log2g_group, log2g_segment;
   const int32_t *brp, *vptr;
+  int32_t skip;     // direct kernel: heavy panels leave their group tile
+  int32_t hv, hb;   // a panel is heavy above hv values or hb blocks
 };
 
 __device__ __forceinline__ bool group_fat(const PlanParams &P, int64_t g) {
@@ -52,9 +60,46 @@ __device__ __forceinline__ bool group_fat(const PlanParams &P, int64_t g) {
   return (P.vptr[b] - P.vptr[a]) > P.vcap || (P.brp[b] - P.brp[a]) > P.bcap;
 }
 
+__device__ __forceinline__ bool panel_heavy(const PlanParams &P, int64_t p) {
+  return (P.vptr[p + 1] - P.vptr[p]) > P.hv || (P.brp[p + 1] - P.brp[p]) > P.hb;
+}
+
+// Panels with tiles of their own: with skip, the heavy panels; otherwise
+// every panel of a fat group.
+__device__ __forceinline__ bool panel_own(const PlanParams &P, int64_t p) {
+  return P.skip ? panel_heavy(P, p) : group_fat(P, p / P.gp);
+}
+
+// A panel cut into pieces (it fits no stage or tile).  hv <= vcap and
+// hb <= bcap, so a long panel is always heavy (skip) and its group fat.
 __device__ __forceinline__ bool panel_long(const PlanParams &P, int64_t p) {
-  return group_fat(P, p / P.gp) &&
+  return panel_own(P, p) &&
          ((P.vptr[p + 1] - P.vptr[p]) > P.vcap || (P.brp[p + 1] - P.brp[p]) > P.bcap);
+}
+
+// Heavy panels of group g (bit j = panel g * gp + j).
+__device__ __forceinline__ uint32_t group_heavy(const PlanParams &P, int64_t g) {
+  const int64_t a = g * P.gp, b = (a + P.gp < P.npanels) ? a + P.gp : P.npanels;
+  uint32_t h = 0;
+  for (int64_t p = a; p < b; ++p)
+    if (panel_heavy(P, p)) h |= 1u << (p - a);
+  return h;
+}
+
+// Whether the group of panel p (p % gp == 0) has a group tile: always
+// without skip (unless its panels have their own tiles, see panel_own);
+// with skip, unless every panel of the group is heavy.
+__device__ __forceinline__ bool has_group_tile(const PlanParams &P, int64_t p) {
+  const int64_t n = (p + P.gp < P.npanels) ? P.gp : P.npanels - p;
+  const uint32_t all = n >= 32 ? 0xffffffffu : ((1u << n) - 1u);
+  return group_heavy(P, p / P.gp) != all;
+}
+
+// Index of a panel's first own tile: with skip, the first panel of a group
+// comes after the group tile.
+__device__ __forceinline__ int32_t own_base(const PlanParams &P, const int32_t *tbase,
+                                            int64_t p) {
+  return tbase[p] + ((P.skip && p % P.gp == 0 && has_group_tile(P, p)) ? 1 : 0);
 }
 
 // mark[b] counts the panels p >= 1 whose first block is b; an inclusive scan
@@ -91,7 +136,15 @@ __global__ void k_piece_flags(PlanParams P, const int32_t *bpanel, const int32_t
 __global__ void k_tile_counts(PlanParams P, const int32_t *pscan, int32_t *tc, int32_t *lf) {
   GRID_STRIDE(p, P.npanels) {
     int32_t t = 0, l = 0;
-    if (!group_fat(P, p / P.gp)) {
+    if (P.skip) {  // the group tile, then the panel's own tiles
+      t = (p % P.gp == 0 && has_group_tile(P, p)) ? 1 : 0;
+      if (panel_long(P, p)) {
+        t += pscan[P.brp[p + 1]] - pscan[P.brp[p]];
+        l = 1;
+      } else if (panel_heavy(P, p)) {
+        t += 1;
+      }
+    } else if (!group_fat(P, p / P.gp)) {
       t = (p % P.gp == 0) ? 1 : 0;
     } else if (panel_long(P, p)) {
       t = pscan[P.brp[p + 1]] - pscan[P.brp[p]];
@@ -108,16 +161,19 @@ __global__ void k_write_panel_tiles(PlanParams P, const int32_t *tbase, const in
                                     const int32_t *pscan, Tile *tiles, int32_t *long_panels,
                                     int32_t *long_slots) {
   GRID_STRIDE(p, P.npanels) {
-    bool fat = group_fat(P, p / P.gp);
-    if (!fat) {
-      if (p % P.gp == 0) {
-        int64_t p1 = (p + P.gp < P.npanels) ? p + P.gp : P.npanels;
-        tiles[tbase[p]] = Tile{(int32_t)p, (int32_t)p1, P.brp[p], P.brp[p1], P.vptr[p],
-                               P.vptr[p1], -1, P.log2g_group};
-      }
+    const bool own = panel_own(P, p);
+    if (p % P.gp == 0 && (P.skip ? has_group_tile(P, p) : !own)) {  // the group tile
+      int64_t p1 = (p + P.gp < P.npanels) ? p + P.gp : P.npanels;
+      const uint32_t heavy = P.skip ? group_heavy(P, p / P.gp) : 0u;
+      tiles[tbase[p]] = Tile{(int32_t)p, (int32_t)p1, P.brp[p], P.brp[p1], P.vptr[p],
+                             P.vptr[p1], heavy ? (int32_t)heavy : -1,
+                             P.log2g_group | (heavy ? kSkip : 0)};
+    }
+    if (!own) {
     } else if (!panel_long(P, p)) {
-      tiles[tbase[p]] = Tile{(int32_t)p, (int32_t)p + 1, P.brp[p], P.brp[p + 1], P.vptr[p],
-                             P.vptr[p + 1], -1, P.log2g_segment | kSegment};
+      tiles[own_base(P, tbase, p)] =
+          Tile{(int32_t)p, (int32_t)p + 1, P.brp[p], P.brp[p + 1], P.vptr[p], P.vptr[p + 1], -1,
+               P.log2g_segment | kSegment};
     } else {
       int32_t l = lbase[p];
       long_panels[l] = (int32_t)p;
@@ -135,7 +191,7 @@ __global__ void k_write_piece_tiles(PlanParams P, const int32_t *bpanel, const i
     if (!panel_long(P, p)) continue;
     int32_t first = P.brp[p];
     int32_t piece = pscan[b] + pf[b] - 1;  // global index of the piece holding b
-    Tile *t = &tiles[tbase[p] + piece - pscan[first]];
+    Tile *t = &tiles[own_base(P, tbase, p) + piece - pscan[first]];
     if (pf[b]) {
       t->p0 = p;
       t->p1 = p + 1;
@@ -361,6 +417,7 @@ __global__ void k_group_efficiency(const Tile *tiles, int64_t ntiles, const int3
     } else {
       int64_t mx = 0;
       for (int32_t p = T.p0; p < T.p1; ++p) {
+        if ((T.mode & kSkip) && ((T.slot >> (p - T.p0)) & 1)) continue;
         const int64_t nbp = brp[p + 1] - brp[p];
         used += nbp;
         mx = nbp > mx ? nbp : mx;
@@ -723,7 +780,9 @@ spc5_status plan_tiles(spc5_matrix *A, const uint32_t *mask32, const int32_t *bo
 
   if (np == 0) return SPC5_OK;
   PlanParams P{np, nb, gp, vcap, bcap, vcap - 32, log2g, log2g_segment,
-               A->block_rowptr, A->panel_vptr};
+               A->block_rowptr, A->panel_vptr, staged ? 0 : 1,
+               (int32_t)std::min<double>(std::max(8.0 * avg_v, 64.0), (double)vcap),
+               (int32_t)std::min<double>(std::max(8.0 * avg_b, 8.0), (double)bcap)};
 
   Tmp<int32_t> bpanel(s), pf(s), pscan(s), tc(s), tbase(s), lf(s), lbase(s), tmp(s);
   CK(bpanel.alloc(nb), "alloc");

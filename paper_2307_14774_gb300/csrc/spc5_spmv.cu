@@ -512,7 +512,8 @@ __global__ void __launch_bounds__(TileThreads<BODY>::v, TileBlocksPerSM<BODY>::v
       v = cur.v0;
     } else {
       const int64_t p = (int64_t)cur.p0 + j;
-      pvalid = p < cur.p1;
+      // a heavy panel (kSkip) has tiles of its own
+      pvalid = p < cur.p1 && !((cur.mode & kSkip) && (((uint32_t)cur.slot >> j) & 1u));
       bl = pvalid ? block_rowptr[p] : 0;
       nbp = pvalid ? block_rowptr[p + 1] - bl : 0;
       v = pvalid ? panel_vptr[p] : 0;
