@@ -25,8 +25,10 @@
 // of the same rule (the CPU oracle checks it byte for byte).
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <stdlib.h>
 
 #include <algorithm>
+#include <climits>
 #include <vector>
 
 #include "spc5_internal.h"
@@ -153,6 +155,11 @@ struct ReadI32 {
 struct WriteI32 {
   int32_t *o;
   __device__ void operator()(int64_t i, int32_t v) const { o[i] = v; }
+};
+struct ReadI32Pad {  // m[i] for i < n, 0 at i == n (an exclusive scan of n + 1 gives the total)
+  const int32_t *m;
+  int64_t n;
+  __device__ int32_t operator()(int64_t i) const { return i < n ? m[i] : 0; }
 };
 
 // U[k] = column of the k-th first occurrence; ustart[k] = panel start flag.
@@ -436,6 +443,246 @@ __global__ void k_check_offsets(int64_t npanels, const int32_t *block_rowptr,
   }
 }
 
+// ------------------------------------------------ panel-local conversion --
+//
+// When no panel holds more than kPanelCap entries (stencils, FEM meshes,
+// uniform rows: every matrix whose rows are not very long), one warp
+// converts a whole panel in shared memory, with the rule of the flat passes
+// above: the merged rank of every entry among the panel's rows (binary
+// searches in the other rows, now in shared memory), the union U in merged
+// order, the greedy block starts over U (a ballot finds the first union
+// column not covered by the previous block, one step per block), then masks,
+// the blocks' value offsets (prefix sum of popcounts) and the value scatter.
+// Two passes over the panels: the first counts blocks (and checks the
+// columns), a prefix sum of the counts places every panel's blocks, the
+// second writes them.  Nothing global is built per entry, so the
+// conversion reads the CSR twice and writes the beta(r,c) arrays once.
+constexpr int kPanelCap = 1024;      // entries of a panel
+constexpr int kPanelBlockCap = 256;  // blocks of a panel (the filling pass)
+
+// Shared memory of one warp (the counting pass needs the first two arrays
+// only, and runs more warps per CTA).
+template <bool FILL>
+struct PanelSmem {
+  int32_t col[kPanelCap];     // the panel's columns, row after row (CSR order)
+  int32_t uni[kPanelCap];     // merged columns (-1: not the first occurrence),
+                              // then the union U, then the blocks' value offsets
+  int32_t bst[FILL ? kPanelBlockCap : 1];     // block starts
+  uint32_t bmask[FILL ? kPanelBlockCap : 1];  // block masks
+};
+template <bool FILL>
+struct PanelWarps {
+  static constexpr int v = FILL ? 3 : 4;  // 30 / 32 KB of shared memory per CTA
+};
+
+// Row q of panel entry t (ro[q] <= t < ro[q + 1]) and ro[q].
+__device__ __forceinline__ int panel_row(int32_t t, const int32_t (&ro)[9], int nr,
+                                         int32_t *rstart) {
+  int q = 0;
+  int32_t st = ro[0];
+#pragma unroll
+  for (int qq = 1; qq < 8; ++qq) {
+    if (qq < nr && t >= ro[qq]) {
+      q = qq;
+      st = ro[qq];
+    }
+  }
+  *rstart = st;
+  return q;
+}
+
+// Largest entry count of a panel.
+__global__ void k_panel_max_entries(int64_t np, int64_t nrows, int r, const int32_t *rowptr,
+                                    int32_t *out) {
+  int32_t mx = 0;
+  GRID_STRIDE(p, np) {
+    const int64_t a = p * r, b = (a + r < nrows) ? a + r : nrows;
+    const int32_t ne = rowptr[b] - rowptr[a];
+    mx = ne > mx ? ne : mx;
+  }
+  for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, mx);
+}
+
+// FILL = false: cnt[p] = blocks of panel p, and the column checks.
+// FILL = true: block columns, masks (as 32-bit words), block value offsets,
+// values and value sources of every panel (brp = block_rowptr).
+template <bool FILL, typename Store>
+__global__ void __launch_bounds__(32 * PanelWarps<FILL>::v)
+    k_panel_convert(int64_t np, int64_t nrows, int64_t ncols, int r, int c,
+                    const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
+                    const double *__restrict__ vals, int32_t *cnt, const int32_t *brp,
+                    int32_t *block_colidx, uint32_t *mask32, int32_t *boff,
+                    typename Store::T *values, int32_t *value_src, uint32_t *err) {
+  constexpr int kW = PanelWarps<FILL>::v;
+  __shared__ PanelSmem<FILL> sm_all[kW];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t lt = (1u << lane) - 1u;
+  PanelSmem<FILL> &S = sm_all[warp];
+  const int64_t nw = (int64_t)gridDim.x * kW;
+  for (int64_t p = (int64_t)blockIdx.x * kW + warp; p < np; p += nw) {
+    const int64_t r0 = p * r;
+    const int nr = (int)((r0 + r <= nrows) ? r : nrows - r0);
+    const int32_t rp = (lane <= nr) ? rowptr[r0 + lane] : 0;
+    const int32_t e0 = __shfl_sync(0xffffffffu, rp, 0);
+    int32_t ro[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) ro[q] = __shfl_sync(0xffffffffu, rp, q < nr ? q : nr) - e0;
+    const int32_t ne = ro[8];
+    __syncwarp();
+    // eight loads in flight per lane (a loop that stores each load before
+    // issuing the next waits one memory latency per 32 entries)
+    for (int32_t t0 = 0; t0 < ne; t0 += 256) {
+      int32_t v[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int32_t t = t0 + i * 32 + lane;
+        v[i] = t < ne ? colidx[e0 + t] : 0;
+      }
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int32_t t = t0 + i * 32 + lane;
+        if (t < ne) S.col[t] = v[i];
+      }
+    }
+    __syncwarp();
+    // merged ranks: an entry's index in its row plus, for every other row,
+    // the entries with a smaller column (later rows) or a column not larger
+    // (earlier rows); a column already in an earlier row is a duplicate
+    uint32_t bad = 0;
+    for (int32_t t = lane; t < ne; t += 32) {
+      int32_t st;
+      const int q = panel_row(t, ro, nr, &st);
+      const int32_t x = S.col[t];
+      if (!FILL) {
+        if (x < 0 || x >= ncols) bad |= kErrRange;
+        if (t > st && S.col[t - 1] >= x) bad |= kErrUnsorted;
+      }
+      int32_t rank = t - st;
+      bool dup = false;
+#pragma unroll
+      for (int qq = 0; qq < 8; ++qq) {
+        if (qq >= nr || qq == q) continue;
+        const int32_t lo = ro[qq], hi = ro[qq + 1];
+        const int32_t lb = lower_bound_i32(S.col, lo, hi, x);
+        int32_t k = lb - lo;
+        if (qq < q) {
+          const bool has = lb < hi && S.col[lb] == x;
+          k += has ? 1 : 0;
+          dup |= has;
+        }
+        rank += k;
+      }
+      S.uni[rank] = dup ? -1 : x;
+    }
+    if (!FILL && bad) atomicOr(err, bad);
+    __syncwarp();
+    // the union U: merged columns without duplicates, in place
+    int32_t nu = 0;
+    for (int32_t base = 0; base < ne; base += 32) {
+      const int32_t v = (base + lane < ne) ? S.uni[base + lane] : -1;
+      const bool keep = base + lane < ne && v >= 0;
+      const uint32_t ball = __ballot_sync(0xffffffffu, keep);
+      __syncwarp();
+      if (keep) S.uni[nu + __popc(ball & lt)] = v;
+      nu += __popc(ball);
+      __syncwarp();
+    }
+    // greedy block starts: the first union column not covered opens a block
+    int32_t nbk = 0;
+    long long thr = LLONG_MIN;
+    for (int32_t base = 0; base < nu; base += 32) {
+      const bool in = base + lane < nu;
+      const int32_t u = in ? S.uni[base + lane] : 0;
+      while (true) {
+        const uint32_t ball = __ballot_sync(0xffffffffu, in && (long long)u >= thr);
+        if (!ball) break;
+        const int32_t sb = __shfl_sync(0xffffffffu, u, __ffs(ball) - 1);
+        if (FILL && lane == 0 && nbk < kPanelBlockCap) S.bst[nbk] = sb;
+        ++nbk;
+        thr = (long long)sb + c;
+      }
+    }
+    if (!FILL) {
+      if (lane == 0) {
+        cnt[p] = nbk;
+        if (nbk > kPanelBlockCap) atomicMax((int32_t *)err + 1, nbk);
+      }
+      continue;
+    }
+    __syncwarp();
+    const int32_t gb0 = brp[p];
+    if (gb0 + nbk != brp[p + 1] || nbk > kPanelBlockCap) {  // cannot happen: both passes
+                                                            // count alike, the host checked
+      if (lane == 0) atomicOr(err, kErrInternal);
+      continue;
+    }
+    for (int32_t i = lane; i < nbk; i += 32) {
+      block_colidx[gb0 + i] = S.bst[i];
+      S.bmask[i] = 0u;
+    }
+    __syncwarp();
+    // masks: an entry's block is the last start not after its column
+    for (int32_t t = lane; t < ne; t += 32) {
+      int32_t st;
+      const int q = panel_row(t, ro, nr, &st);
+      const int32_t x = S.col[t];
+      const int32_t b = lower_bound_i32(S.bst, 0, nbk, x + 1) - 1;
+      atomicOr(&S.bmask[b], 1u << (q * c + (x - S.bst[b])));
+    }
+    __syncwarp();
+    // the blocks' value offsets: exclusive prefix of the popcounts
+    int32_t run = 0;
+    for (int32_t base = 0; base < nbk; base += 32) {
+      const bool in = base + lane < nbk;
+      const uint32_t m = in ? S.bmask[base + lane] : 0u;
+      const int pc = __popc(m);
+      int incl = pc;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int t2 = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t2;
+      }
+      if (in) {
+        S.uni[base + lane] = run + incl - pc;
+        mask32[gb0 + base + lane] = m;
+        boff[gb0 + base + lane] = e0 + run + incl - pc;
+      }
+      run += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    __syncwarp();
+    // values in (block, row, column) order, eight loads in flight per lane
+    for (int32_t t0 = 0; t0 < ne; t0 += 256) {
+      double v[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int32_t t = t0 + i * 32 + lane;
+        v[i] = t < ne ? vals[e0 + t] : 0.0;
+      }
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int32_t t = t0 + i * 32 + lane;
+        if (t < ne) {
+          int32_t st;
+          const int q = panel_row(t, ro, nr, &st);
+          const int32_t x = S.col[t];
+          const int32_t b = lower_bound_i32(S.bst, 0, nbk, x + 1) - 1;
+          const int bit = q * c + (x - S.bst[b]);
+          const int32_t dst = e0 + S.uni[b] + __popc(S.bmask[b] & ((1u << bit) - 1u));
+          values[dst] = Store::cvt(v[i]);
+          value_src[dst] = e0 + t;
+        }
+      }
+    }
+    __syncwarp();
+  }
+}
+
+__global__ void k_panel_vptr(int64_t np, int64_t nrows, int r, const int32_t *rowptr,
+                             int32_t *panel_vptr) {
+  GRID_STRIDE(p, np + 1) { panel_vptr[p] = rowptr[(p * r < nrows) ? p * r : nrows]; }
+}
+
 template <typename T>
 struct DevBuf {
   T *p = nullptr;
@@ -475,6 +722,107 @@ spc5_status err_to_status(uint32_t err) {
     if (_st != SPC5_OK) return _st;                 \
   } while (0)
 
+namespace {
+
+// Output arrays of a conversion with nb blocks (every array padded by 16
+// bytes: the staged SpMV copies 16-byte aligned windows that may end up to
+// 15 bytes past the last element).
+spc5_status alloc_outputs(spc5_matrix *A, int64_t nb, cudaStream_t s) {
+  const int64_t nnz = A->nnz, np = A->npanels;
+  const int mask_bytes = A->r * A->c / 8;
+  const size_t vsize = A->value_dtype == SPC5_F64 ? 8 : A->value_dtype == SPC5_F32 ? 4 : 2;
+  CK(cudaMalloc(&A->values, (size_t)nnz * vsize + 16), "alloc values");
+  CK(cudaMalloc((void **)&A->value_src, (size_t)nnz * sizeof(int32_t) + 16), "alloc value_src");
+  CK(cudaMalloc((void **)&A->dev_error, sizeof(uint32_t)), "alloc error word");
+  CK(cudaMemsetAsync(A->dev_error, 0, sizeof(uint32_t), s), "zero error word");
+  CK(cudaMalloc((void **)&A->block_colidx, (size_t)nb * sizeof(int32_t) + 16), "alloc colidx");
+  CK(cudaMalloc(&A->masks, (size_t)nb * mask_bytes + 16), "alloc masks");
+  CK(cudaMemsetAsync(A->block_colidx, 0, (size_t)nb * sizeof(int32_t) + 16, s), "zero colidx");
+  CK(cudaMemsetAsync(A->masks, 0, (size_t)nb * mask_bytes + 16, s), "zero masks");
+  A->nblocks = nb;
+  A->device_bytes = (int64_t)(2 * (np + 1) * sizeof(int32_t) + 32 + nnz * vsize + 16 +
+                             nnz * sizeof(int32_t) + 16) +
+                    (int64_t)(nb * sizeof(int32_t) + nb * mask_bytes + 32);
+  return SPC5_OK;
+}
+
+// The panel-local conversion (every panel at most kPanelCap entries; the
+// row pointers already checked).  *flat is set, and nothing converted, when
+// some panel has more than kPanelBlockCap blocks.
+spc5_status convert_panels(spc5_matrix *A, const int32_t *rowptr, const int32_t *colidx,
+                           const double *vals, uint32_t *err, cudaStream_t s, bool *flat) {
+  *flat = false;
+  const int64_t n = A->nrows, np = A->npanels;
+  const int r = A->r, c = A->c;
+  const int mask_bytes = r * c / 8;
+  // six CTAs of 32 KB per SM
+  auto grid_of = [&](int warps) {
+    const int64_t b = (np + warps - 1) / warps;
+    return (unsigned)std::min<int64_t>(std::max<int64_t>(b, 1), (int64_t)device_sm_count() * 6);
+  };
+  DevBuf<int32_t> cnt(s), scan_tmp(s);
+  CK(cnt.alloc(np + 1), "alloc block counts");
+  CK(scan_tmp.alloc(scan_tmp_elems(np + 1)), "alloc scan tmp");
+  k_panel_convert<false, StoreF64><<<grid_of(PanelWarps<false>::v), 32 * PanelWarps<false>::v, 0,
+                                      s>>>(
+      np, n, A->ncols, r, c, rowptr, colidx, vals, cnt.p, nullptr, nullptr, nullptr, nullptr,
+      nullptr, nullptr, err);
+  uint32_t h[2] = {0, 0};
+  CK(cudaMemcpyAsync(h, err, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s), "read err");
+  CK(cudaStreamSynchronize(s), "sync validation");
+  if (h[0]) return err_to_status(h[0]);
+  if ((int32_t)h[1] > kPanelBlockCap) {
+    *flat = true;
+    return SPC5_OK;
+  }
+  uint32_t herr = 0;
+  CK(cudaMalloc((void **)&A->block_rowptr, (size_t)(np + 1) * sizeof(int32_t) + 16),
+     "alloc block_rowptr");
+  CK(cudaMalloc((void **)&A->panel_vptr, (size_t)(np + 1) * sizeof(int32_t) + 16),
+     "alloc panel_vptr");
+  CK(device_scan<int32_t>(np + 1, ReadI32Pad{cnt.p, np}, WriteI32{A->block_rowptr}, AddI32{}, 0,
+                          false, scan_tmp.p, s),
+     "scan block counts");
+  int32_t nb32 = 0;
+  CK(cudaMemcpyAsync(&nb32, A->block_rowptr + np, sizeof(int32_t), cudaMemcpyDeviceToHost, s),
+     "read nb");
+  CK(cudaStreamSynchronize(s), "sync nb");
+  const int64_t nb = nb32;
+  spc5_status st = alloc_outputs(A, nb, s);
+  if (st != SPC5_OK) return st;
+  k_panel_vptr<<<grid_for(np + 1), kThreads, 0, s>>>(np, n, r, rowptr, A->panel_vptr);
+  DevBuf<uint32_t> mask32(s);
+  DevBuf<int32_t> boff(s);
+  CK(mask32.alloc(nb), "alloc mask32");
+  CK(boff.alloc(nb), "alloc boff");
+#define PANEL_FILL(STORE, T)                                                                  \
+  k_panel_convert<true, STORE><<<grid_of(PanelWarps<true>::v), 32 * PanelWarps<true>::v, 0, s>>>( \
+      np, n, A->ncols, r, c, rowptr, colidx, vals, nullptr, A->block_rowptr, A->block_colidx, \
+      mask32.p, boff.p, (T *)A->values, A->value_src, err)
+  if (A->value_dtype == SPC5_F64)
+    PANEL_FILL(StoreF64, double);
+  else if (A->value_dtype == SPC5_F32)
+    PANEL_FILL(StoreF32, float);
+  else
+    PANEL_FILL(StoreBF16, uint16_t);
+#undef PANEL_FILL
+  if (mask_bytes == 1)
+    k_pack_masks<uint8_t><<<grid_for(nb), kThreads, 0, s>>>(nb, mask32.p, (uint8_t *)A->masks);
+  else if (mask_bytes == 2)
+    k_pack_masks<uint16_t><<<grid_for(nb), kThreads, 0, s>>>(nb, mask32.p, (uint16_t *)A->masks);
+  else
+    k_pack_masks<uint32_t><<<grid_for(nb), kThreads, 0, s>>>(nb, mask32.p, (uint32_t *)A->masks);
+  spc5_status pst = plan_tiles(A, mask32.p, boff.p, s);
+  if (pst != SPC5_OK) return pst;
+  CK(cudaGetLastError(), "conversion kernels");
+  CK(cudaMemcpyAsync(&herr, err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s), "read err");
+  CK(cudaStreamSynchronize(s), "sync conversion");
+  if (herr) return err_to_status(herr);
+  return SPC5_OK;
+}
+
+}  // namespace
+
 spc5_status convert_device(spc5_matrix *A, const int32_t *rowptr, const int32_t *colidx,
                            const double *vals, cudaStream_t s) {
   const int64_t n = A->nrows, nnz = A->nnz, np = A->npanels;
@@ -482,8 +830,30 @@ spc5_status convert_device(spc5_matrix *A, const int32_t *rowptr, const int32_t 
   const int mask_bytes = r * c / 8;
 
   DevBuf<uint32_t> err(s);
-  CK(err.alloc(1), "alloc err");
-  CK(cudaMemsetAsync(err.p, 0, sizeof(uint32_t), s), "memset err");
+  CK(err.alloc(2), "alloc err");
+  CK(cudaMemsetAsync(err.p, 0, 2 * sizeof(uint32_t), s), "memset err");
+
+  // 0. panel-local conversion when no panel is longer than a warp's share
+  //    of shared memory (SPC5_CONVERT=flat forces the flat passes)
+  if (nnz > 0 && np > 0) {
+    const char *mode = getenv("SPC5_CONVERT");
+    if (!(mode && mode[0] == 'f')) {
+      k_check_rowptr<<<grid_for(std::max<int64_t>(n, 1)), kThreads, 0, s>>>(n, nnz, rowptr,
+                                                                             err.p);
+      k_panel_max_entries<<<grid_for(np), kThreads, 0, s>>>(np, n, r, rowptr,
+                                                           (int32_t *)err.p + 1);
+      uint32_t h[2] = {0, 0};
+      CK(cudaMemcpyAsync(h, err.p, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s), "read");
+      CK(cudaStreamSynchronize(s), "sync rowptr check");
+      if (h[0]) return err_to_status(h[0]);
+      if ((int32_t)h[1] <= kPanelCap) {
+        CK(cudaMemsetAsync(err.p + 1, 0, sizeof(uint32_t), s), "memset");
+        bool flat = false;
+        spc5_status st = convert_panels(A, rowptr, colidx, vals, err.p, s, &flat);
+        if (st != SPC5_OK || !flat) return st;
+      }
+    }
+  }
 
   // 1. row ids and validation
   DevBuf<int32_t> rowid(s), scan_tmp(s);

@@ -39,13 +39,43 @@ def mats():
     return _mats()
 
 
+@pytest.mark.parametrize("conv", ["auto", "flat"])
 @pytest.mark.parametrize("r,c", BETAS)
-def test_conversion_bit_exact(mats, r, c):
+def test_conversion_bit_exact(monkeypatch, mats, r, c, conv):
+    """Both converters: the panel-local one (taken when no panel holds more
+    than 1024 entries) and the flat passes (the other matrices, or forced)."""
+    if conv == "flat":
+        monkeypatch.setenv("SPC5_CONVERT", "flat")
     for A in mats:
         M = convert(A, r, c)
         S = oracle.convert(A, r, c)
         assert_conversion_equal(M, S, A)
         assert M.info()["filling"] == pytest.approx(S.filling(), rel=0, abs=1e-15)
+
+
+@pytest.mark.parametrize("r,c", BETAS)
+def test_conversion_many_blocks_per_panel(r, c):
+    """Panels of a few hundred entries, each entry a block of its own (columns
+    nine apart): more blocks per panel than the panel-local converter keeps
+    in shared memory (256), so the conversion falls back to the flat passes
+    after counting; bit-exact all the same."""
+    torch_cuda()
+    rng = np.random.default_rng(12)
+    rp, ci = [0], []
+    for i in range(40):
+        k = 300 if i % 3 else 20
+        cols = np.sort(rng.choice(5000, k, replace=False)) * 9
+        ci.append(cols.astype(np.int32))
+        rp.append(rp[-1] + k)
+    colidx = np.concatenate(ci)
+    A = synth.CSR(40, 45_000, np.array(rp, np.int32), colidx, rng.normal(size=len(colidx)),
+                  "spread")
+    M = convert(A, r, c)
+    assert M.info()["nblocks"] > 256
+    assert_conversion_equal(M, oracle.convert(A, r, c), A)
+    x = synth.vector_uniform(A.ncols, seed=5)
+    y_ref, scale = oracle.csr_spmv(A, x)
+    assert_within_tol(spmv(M, x), y_ref, scale)
 
 
 @pytest.mark.parametrize("r,c", BETAS)
@@ -148,8 +178,11 @@ def test_explicit_zeros_are_kept():
     assert_conversion_equal(convert(A, 4, 8), S, A)
 
 
-def test_invalid_csr_is_rejected_on_device():
+@pytest.mark.parametrize("conv", ["auto", "flat"])
+def test_invalid_csr_is_rejected_on_device(monkeypatch, conv):
     torch = torch_cuda()
+    if conv == "flat":
+        monkeypatch.setenv("SPC5_CONVERT", "flat")
     A = synth.bernoulli(40, 40, 0.3, seed=5)
     row = int(np.argmax(np.diff(A.rowptr) >= 2))
     a = A.rowptr[row]
