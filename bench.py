@@ -165,7 +165,7 @@ def kernel_source_hash() -> str:
     so that editing a comment keeps the committed ncu figures valid."""
     import re
     h = hashlib.sha256()
-    for name in ("spc5_spmv.cu",):
+    for name in ("spc5_spmv.cu", "spc5_flat.cuh"):
         with open(os.path.join(ROOT, "paper_2307_14774_gb300", "csrc", name)) as f:
             text = re.sub(r"/\*.*?\*/", "", f.read(), flags=re.S)
         code = [re.sub(r"//.*$", "", ln).rstrip() for ln in text.splitlines()]

@@ -25,6 +25,7 @@
 #include <type_traits>
 #include <vector>
 
+#include "spc5_flat.cuh"
 #include "spc5_internal.h"
 #include "spc5_reduce.cuh"
 
@@ -45,8 +46,8 @@ struct MatDesc {
   int64_t nrows;
   int64_t tile_base;
   int32_t r, c, ntiles, nlong;
-  int32_t body, pad;  // the matrix's row-group body (2, 6: row stream; 5, 7: passing empty
-                      // blocks)
+  int32_t body;  // the matrix's row-group body (2, 6: row stream; 5, 7: passing empty blocks)
+  int32_t flat;  // 1: the tiles are the matrix's block-balanced plan (k = 1, r <= 2)
 };
 
 constexpr int kBatchChunk = 8;  // consecutive tiles per counter grab
@@ -281,6 +282,83 @@ __global__ void __launch_bounds__(kThreads, BatchBlocksPerSM<K, AT>::v)
   }
 }
 
+// The members whose product runs the block-balanced plan (one right-hand
+// side, r <= 2): a second persistent launch over their tiles, with the
+// standalone kernel's tile body.  A warp takes chunks of kBatchChunk tiles
+// from its own counter and runs consecutive whole-panel tiles of one matrix
+// as one range (the plan cuts a small matrix into tiles of 64 blocks, sized
+// for a launch of its own; the tile body takes any run of whole panels).
+template <typename VT, typename AT>
+__global__ void __launch_bounds__(kThreads, 4)
+    k_batch_flat(const MatDesc *__restrict__ table, const int32_t *__restrict__ tile_mat,
+                 int64_t ntiles, uint32_t *sched, AT alpha, AT beta) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nchunks = (ntiles + kBatchChunk - 1) / kBatchChunk;
+  __shared__ MatDesc s_desc[kThreads / 32];
+  __shared__ int32_t s_pid[kThreads / 32][kFlatRound];
+  MatDesc &d = s_desc[threadIdx.x >> 5];
+  int32_t *pid = s_pid[threadIdx.x >> 5];
+  const Scale<AT> sc{alpha, beta, beta != (AT)0 ? 2 : (alpha != (AT)1 ? 1 : 0)};
+  uint32_t grab = 0;
+  if (lane == 0) grab = atomicAdd(&sched[0], 1u);
+  int64_t ch = (int64_t)__shfl_sync(kFull, grab, 0);
+  int cur_m = -1;
+  while (ch < nchunks) {
+    if (lane == 0) grab = atomicAdd(&sched[0], 1u);
+    const int64_t t1 = min((ch + 1) * kBatchChunk, ntiles);
+    for (int64_t t = ch * kBatchChunk; t < t1;) {
+      const int m = tile_mat[t];
+      if (m != cur_m) {
+        __syncwarp();
+        if (lane < (int)(sizeof(MatDesc) / 4))
+          reinterpret_cast<uint32_t *>(&d)[lane] =
+              reinterpret_cast<const uint32_t *>(table + m)[lane];
+        __syncwarp();
+        cur_m = m;
+      }
+      Tile cur = d.tiles[t - d.tile_base];
+      ++t;
+      while (!(cur.mode & kPartial) && t < t1 && tile_mat[t] == m) {
+        const Tile nx = d.tiles[t - d.tile_base];
+        if (nx.mode & kPartial) break;
+        cur.p1 = nx.p1;
+        cur.b1 = nx.b1;
+        cur.v1 = nx.v1;
+        ++t;
+      }
+      const VT *vals = (const VT *)d.values;
+      const AT *x = (const AT *)d.x;
+      AT *y = (AT *)d.y, *part = (AT *)d.partial;
+      switch (d.r * 100 + d.c) {
+        case 108:
+          flat_tile<1, 8>(cur, lane, pid, d.brp, d.colidx,
+                          (const typename MaskType<1, 8>::T *)d.masks, vals, x, y, part, sc,
+                          d.nrows);
+          break;
+        case 204:
+          flat_tile<2, 4>(cur, lane, pid, d.brp, d.colidx,
+                          (const typename MaskType<2, 4>::T *)d.masks, vals, x, y, part, sc,
+                          d.nrows);
+          break;
+        default:
+          flat_tile<2, 8>(cur, lane, pid, d.brp, d.colidx,
+                          (const typename MaskType<2, 8>::T *)d.masks, vals, x, y, part, sc,
+                          d.nrows);
+          break;
+      }
+    }
+    ch = (int64_t)__shfl_sync(kFull, grab, 0);
+  }
+  // every warp has made its last grab: the last one to finish resets the counter
+  if (lane == 0) {
+    const uint32_t nwarps = gridDim.x * (blockDim.x >> 5);
+    if (atomicAdd(&sched[1], 1u) == nwarps - 1) {
+      atomicExch(&sched[0], 0u);
+      atomicExch(&sched[1], 0u);
+    }
+  }
+}
+
 // Split panels, one warp per panel: the panel's partials are W = r * k
 // values per slot (slot-major, row q and RHS j at q * k + j).  For W <= 32
 // lane t adds elements t, t + 32, ... (all of element t % W) and the lanes of
@@ -342,10 +420,13 @@ using namespace spc5;
 struct spc5_batch {
   int nmat = 0, k = 0, device = 0;
   int vec = 0;              // every X and Y 16-byte aligned: vector loads of the k values
-  uint32_t *sched = nullptr;  // [2] tile-chunk counter and finished warps (reset by the kernel)
+  uint32_t *sched = nullptr;  // [4] tile-chunk counter and finished warps of the row-group
+                              // launch, then of the block-balanced launch (reset by them)
   spc5_dtype dtype = SPC5_F64;
   int64_t ntiles = 0, nlong = 0;
+  int64_t fntiles = 0;               // tiles of the block-balanced members
   MatDesc *table = nullptr;
+  int32_t *ftile_mat = nullptr;      // their tile -> matrix map
   int32_t *tile_mat = nullptr;
   int32_t *lp_mat = nullptr, *lp_idx = nullptr;
   void *partial = nullptr;
@@ -357,6 +438,7 @@ void free_batch(spc5_batch *B) {
   if (!B) return;
   cudaFree(B->table);
   cudaFree(B->tile_mat);
+  cudaFree(B->ftile_mat);
   cudaFree(B->lp_mat);
   cudaFree(B->lp_idx);
   cudaFree(B->partial);
@@ -378,6 +460,17 @@ cudaError_t run_batch(const spc5_batch *B, double alpha, double beta, cudaStream
           B->table, B->tile_mat, B->ntiles, B->sched, (AT)alpha, (AT)beta);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+  }
+  if constexpr (K == 1) {
+    if (B->fntiles > 0) {
+      const int64_t nchunks = (B->fntiles + kBatchChunk - 1) / kBatchChunk;
+      int64_t blocks = (nchunks + (kThreads / 32) - 1) / (kThreads / 32);
+      blocks = std::min<int64_t>(blocks, (int64_t)sm_count() * 4);
+      k_batch_flat<VT, AT><<<(unsigned)blocks, kThreads, 0, s>>>(
+          B->table, B->ftile_mat, B->fntiles, B->sched + 2, (AT)alpha, (AT)beta);
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+    }
   }
   if (B->nlong > 0) {
     const int blocks = (int)std::min<int64_t>((B->nlong + 7) / 8, (int64_t)sm_count() * 8);
@@ -437,12 +530,15 @@ extern "C" spc5_status spc5_batch_create(int nmat, const spc5_matrix *const *A,
   B->dtype = A[0]->value_dtype;
   const size_t slot = B->dtype == SPC5_F64 ? 8 : 4;
   std::vector<MatDesc> table(nmat);
-  int64_t tiles = 0, nlong = 0, pslots = 0;
+  int64_t tiles = 0, ftiles = 0, nlong = 0, pslots = 0;
   std::vector<int64_t> pbase(nmat);
   for (int m = 0; m < nmat; ++m) {
     const spc5_matrix *M = A[m];
     MatDesc &d = table[m];
-    d.tiles = M->tiles;
+    // one right-hand side: a matrix whose product runs the block-balanced
+    // plan (skewed rows, r <= 2) runs it in the batch's second launch
+    const bool fl = k == 1 && M->flat == 1 && M->r <= 2;
+    d.tiles = fl ? M->ftiles : M->tiles;
     d.brp = M->block_rowptr;
     d.vptr = M->panel_vptr;
     d.colidx = M->block_colidx;
@@ -450,22 +546,23 @@ extern "C" spc5_status spc5_batch_create(int nmat, const spc5_matrix *const *A,
     d.values = M->values;
     d.x = X[m];
     d.y = Y[m];
-    d.long_panels = M->long_panels;
-    d.long_slots = M->long_slots;
+    d.long_panels = fl ? M->flong_panels : M->long_panels;
+    d.long_slots = fl ? M->flong_slots : M->long_slots;
     d.nrows = M->nrows;
-    d.tile_base = tiles;
     d.r = M->r;
     d.c = M->c;
-    d.ntiles = (int32_t)M->ntiles;
-    d.nlong = (int32_t)M->nlong;
+    d.ntiles = (int32_t)(fl ? M->fntiles : M->ntiles);
+    d.nlong = (int32_t)(fl ? M->fnlong : M->nlong);
     d.body = M->body;
-    d.pad = 0;
+    d.flat = fl ? 1 : 0;
+    d.tile_base = fl ? ftiles : tiles;
     pbase[m] = pslots;
-    pslots += M->npieces * M->r * k;
-    tiles += M->ntiles;
-    nlong += M->nlong;
+    pslots += (fl ? M->fnpieces : M->npieces) * M->r * k;
+    (fl ? ftiles : tiles) += d.ntiles;
+    nlong += d.nlong;
   }
   B->ntiles = tiles;
+  B->fntiles = ftiles;
   B->nlong = nlong;
   B->vec = 1;
   for (int m = 0; m < nmat; ++m)
@@ -473,15 +570,19 @@ extern "C" spc5_status spc5_batch_create(int nmat, const spc5_matrix *const *A,
   spc5_status st = cuda_check(cudaMalloc(&B->partial, (size_t)std::max<int64_t>(pslots, 1) * slot),
                               "alloc batch partials");
   if (st == SPC5_OK)
-    st = cuda_check(cudaMalloc((void **)&B->sched, 2 * sizeof(uint32_t)), "alloc batch counter");
+    st = cuda_check(cudaMalloc((void **)&B->sched, 4 * sizeof(uint32_t)), "alloc batch counter");
   if (st == SPC5_OK)
-    st = cuda_check(cudaMemsetAsync(B->sched, 0, 2 * sizeof(uint32_t), s), "zero batch counter");
+    st = cuda_check(cudaMemsetAsync(B->sched, 0, 4 * sizeof(uint32_t), s), "zero batch counter");
   for (int m = 0; m < nmat; ++m) table[m].partial = (char *)B->partial + pbase[m] * slot;
   if (st == SPC5_OK)
     st = cuda_check(cudaMalloc((void **)&B->table, sizeof(MatDesc) * nmat), "alloc batch table");
   if (st == SPC5_OK)
     st = cuda_check(cudaMalloc((void **)&B->tile_mat, sizeof(int32_t) * std::max<int64_t>(tiles, 1)),
                     "alloc tile map");
+  if (st == SPC5_OK)
+    st = cuda_check(
+        cudaMalloc((void **)&B->ftile_mat, sizeof(int32_t) * std::max<int64_t>(ftiles, 1)),
+        "alloc flat tile map");
   if (st == SPC5_OK)
     st = cuda_check(cudaMalloc((void **)&B->lp_mat, sizeof(int32_t) * std::max<int64_t>(nlong, 1)),
                     "alloc long map");
@@ -494,16 +595,16 @@ extern "C" spc5_status spc5_batch_create(int nmat, const spc5_matrix *const *A,
                     "copy batch table");
   int64_t lbase = 0;
   for (int m = 0; st == SPC5_OK && m < nmat; ++m) {
-    const spc5_matrix *M = A[m];
-    if (M->ntiles > 0)
-      k_fill<<<(unsigned)std::min<int64_t>((M->ntiles + 255) / 256, 4096), 256, 0, s>>>(
-          B->tile_mat + table[m].tile_base, M->ntiles, m);
-    if (M->nlong > 0) {
-      k_fill<<<(unsigned)std::min<int64_t>((M->nlong + 255) / 256, 4096), 256, 0, s>>>(
-          B->lp_mat + lbase, M->nlong, m);
-      k_iota<<<(unsigned)std::min<int64_t>((M->nlong + 255) / 256, 4096), 256, 0, s>>>(
-          B->lp_idx + lbase, M->nlong);
-      lbase += M->nlong;
+    const int64_t mt = table[m].ntiles, ml = table[m].nlong;
+    if (mt > 0)
+      k_fill<<<(unsigned)std::min<int64_t>((mt + 255) / 256, 4096), 256, 0, s>>>(
+          (table[m].flat ? B->ftile_mat : B->tile_mat) + table[m].tile_base, mt, m);
+    if (ml > 0) {
+      k_fill<<<(unsigned)std::min<int64_t>((ml + 255) / 256, 4096), 256, 0, s>>>(
+          B->lp_mat + lbase, ml, m);
+      k_iota<<<(unsigned)std::min<int64_t>((ml + 255) / 256, 4096), 256, 0, s>>>(
+          B->lp_idx + lbase, ml);
+      lbase += ml;
     }
   }
   if (st == SPC5_OK) st = cuda_check(cudaStreamSynchronize(s), "sync batch create");

@@ -54,16 +54,21 @@ def test_plan_labels(bench):
 
 
 def test_source_hash_ignores_comments_only(bench, tmp_path, monkeypatch):
-    src = os.path.join(ROOT, "paper_2307_14774_gb300", "csrc", "spc5_spmv.cu")
-    text = open(src).read()
+    csrc = os.path.join(ROOT, "paper_2307_14774_gb300", "csrc")
+    text = open(os.path.join(csrc, "spc5_spmv.cu")).read()
+    flat = open(os.path.join(csrc, "spc5_flat.cuh")).read()
     fake = tmp_path / "paper_2307_14774_gb300" / "csrc"
     fake.mkdir(parents=True)
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     (fake / "spc5_spmv.cu").write_text(text)
+    (fake / "spc5_flat.cuh").write_text(flat)
     h0 = bench.kernel_source_hash()
     (fake / "spc5_spmv.cu").write_text("// a new comment\n" + text.replace("\n\n", "\n\n\n", 3))
     assert bench.kernel_source_hash() == h0
     (fake / "spc5_spmv.cu").write_text(text.replace("kVRound = 256", "kVRound = 128", 1))
+    assert bench.kernel_source_hash() != h0
+    (fake / "spc5_spmv.cu").write_text(text)
+    (fake / "spc5_flat.cuh").write_text(flat.replace("kFlatKB = 4", "kFlatKB = 8", 1))
     assert bench.kernel_source_hash() != h0
 
 
