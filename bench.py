@@ -529,7 +529,9 @@ def grad_section(torch, spc5, synth, hbm, log, reps=10):
     matrix, then the SpMV) and backward (dx = A^T g and dvals = g[row] x[col]
     over the stored entries), timed with CUDA events; each of the four
     kernels (value update, SpMV, transposed SpMV, value gradient) is also
-    timed alone, with its algorithmic bytes and HBM fraction."""
+    timed alone, with its algorithmic bytes and HBM fraction.  Then again
+    with the transposed copy (spc5_build_transpose): the transposed product
+    as a plain SpMV over A^T, and the value update refreshing both copies."""
     from paper_2307_14774_gb300.autograd import SpMVFunction
     A = synth.workload("stencil27")
     dev = [torch.from_numpy(a).cuda() for a in (A.rowptr, A.colidx, A.vals)]
@@ -588,11 +590,28 @@ def grad_section(torch, spc5, synth, hbm, log, reps=10):
                         meta + 4 * A.nrows + 4 * A.ncols + 4 * A.nnz + 4 * A.nnz),
     }
     out["kernels"] = {}
-    for name, (fn, b) in kernels.items():
-        ms = timed(fn)
-        out["kernels"][name] = {"us": round(ms * 1e3, 2), "bytes": int(b),
-                                "gbs": round(b / (ms * 1e-3) / 1e9, 1),
-                                "frac": round(b / (ms * 1e-3) / 1e9 / hbm, 3)}
+
+    def run_kernels(ks):
+        for name, (fn, b) in ks.items():
+            ms = timed(fn)
+            out["kernels"][name] = {"us": round(ms * 1e3, 2), "bytes": int(b),
+                                    "gbs": round(b / (ms * 1e-3) / 1e9, 1),
+                                    "frac": round(b / (ms * 1e-3) / 1e9 / hbm, 3)}
+    run_kernels(kernels)
+    # the transposed copy: spc5_spmv_t becomes a product over A^T (the
+    # 27-point pattern is symmetric, so A^T has A's blocks and bytes), and
+    # spc5_set_values refreshes it too
+    t0 = time.perf_counter()
+    spc5.spc5_build_transpose(M)
+    torch.cuda.synchronize()
+    out["build_transpose_ms"] = round((time.perf_counter() - t0) * 1e3, 2)
+    ms = timed(lambda: step(True))
+    out["forward_backward_transposed"] = {"ms": round(ms, 4),
+                                          "gflops": round(5 * A.nnz / (ms * 1e-3) / 1e9, 1)}
+    run_kernels({"spmv_t_transposed": (lambda: spc5.spc5_spmv_t(M, g, dx),
+                                       algorithmic_bytes(info)),
+                 "set_values_with_transposed": (lambda: spc5.spc5_set_values(M, vals64),
+                                                2 * (8 + 4 + 4) * A.nnz)})
     log(f"autograd: {out}")
     del M, dev, flush
     return out

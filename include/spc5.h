@@ -103,6 +103,7 @@ typedef struct {
                               6 row stream at 64 warps per SM, 7 pipelined row stream
                               passing empty blocks */
   int32_t dynamic;         /* 1 if row-group tiles are taken from a counter, 0 grid-stride */
+  int32_t transposed;      /* 1 if spc5_build_transpose attached a transposed copy */
 } spc5_info;
 
 /*
@@ -220,15 +221,35 @@ spc5_status spc5_spmv(const spc5_matrix *A, const void *x, void *y, double alpha
 
 /*
  * spc5_spmv_t -- dx = alpha * A^T g + beta * dx, the product with the
- * transposed matrix (the input gradient of y = A x: dx = A^T dy).  Walks
- * the stored blocks of Algorithm 1's layout and scatters
- * values[idxVal] * g[row] into dx[idxCol + k] with atomic additions, so the
- * summation order (and the last bits of the result) may differ from run to
- * run.  g[nrows] and dx[ncols] are device vectors typed as for spc5_spmv.
- * With beta == 0, dx is not read.  Asynchronous on `stream`.
+ * transposed matrix (the input gradient of y = A x: dx = A^T dy).  With a
+ * transposed copy (spc5_build_transpose) it is spc5_spmv over that copy:
+ * deterministic.  Without one it walks the stored blocks of Algorithm 1's
+ * layout and scatters values[idxVal] * g[row] into dx[idxCol + k] with
+ * atomic additions, so the summation order (and the last bits of the
+ * result) may differ from run to run.  g[nrows] and dx[ncols] are device
+ * vectors typed as for spc5_spmv.  With beta == 0, dx is not read.
+ * Asynchronous on `stream`.
  */
 spc5_status spc5_spmv_t(const spc5_matrix *A, const void *g, void *dx, double alpha, double beta,
                         void *stream);
+
+/*
+ * spc5_build_transpose -- attach to A its transpose A^T, converted to
+ * beta(r,c) with A's block shape and storage type (Section 2.4's rule
+ * applied to the columns of A), so that spc5_spmv_t becomes an ordinary
+ * product over A^T (Algorithm 1): deterministic, and as fast as a forward
+ * product.  The paper transposes nothing; this is the backward product of
+ * the differentiation extension.  Built on the device from A's stored blocks
+ * (the CSR A came from is not needed); the copy belongs to A (released by
+ * spc5_destroy(A)), spc5_set_values(A, vals) updates it too, and calling
+ * again rebuilds it.  A must be a plain (not hybrid) matrix on the current
+ * device.  Errors: SPC5_EUNSUPPORTED for a hybrid matrix or when a column
+ * of A holds more than 65536 entries (spc5_spmv_t then keeps its atomic
+ * scatter), SPC5_EDEVICE, SPC5_ECUDA / SPC5_ENOMEM from the conversion.
+ * Synchronises `stream`; allocates about 5 times A's value bytes of
+ * temporaries while it runs and a second matrix of A's size.
+ */
+spc5_status spc5_build_transpose(spc5_matrix *A, void *stream);
 
 /*
  * spc5_values_grad -- dvals[e] = alpha * g[row(e)] * x[col(e)] for every

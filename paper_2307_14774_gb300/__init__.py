@@ -8,8 +8,8 @@ from . import autograd, partition
 from .spc5 import (EXPORTS, SPC5_BF16, SPC5_F32, SPC5_F64, STATUS, SUPPORTED_RC, Matrix,
                    SPC5Error, export_tensors, load, spc5_convert_csr, spc5_destroy, spc5_export,
                    spc5_last_error, spc5_matrix_info, spc5_spmv, spc5_spmv_noalloc,
-                   spc5_spmv_t, spc5_values_grad, spc5_set_values, spc5_tune,
-                   spc5_convert_tuned, spc5_convert_tuned_ex, spc5_spmv_batched, Batch,
+                   spc5_spmv_t, spc5_build_transpose, spc5_values_grad, spc5_set_values,
+                   spc5_tune, spc5_convert_tuned, spc5_convert_tuned_ex, spc5_spmv_batched, Batch,
                    spc5_ircg,
                    spc5_convert_hybrid, spc5_export_hybrid, spc5_status_str,
                    spc5_measure_fma_peak)
@@ -17,7 +17,8 @@ from .spc5 import (EXPORTS, SPC5_BF16, SPC5_F32, SPC5_F64, STATUS, SUPPORTED_RC,
 __all__ = ["EXPORTS", "SPC5_BF16", "SPC5_F32", "SPC5_F64", "STATUS", "SUPPORTED_RC", "Matrix",
            "SPC5Error", "export_tensors", "load", "spc5_convert_csr", "spc5_destroy",
            "spc5_export", "spc5_last_error", "spc5_matrix_info", "spc5_spmv",
-           "spc5_spmv_noalloc", "spc5_spmv_t", "spc5_values_grad", "spc5_set_values",
+           "spc5_spmv_noalloc", "spc5_spmv_t", "spc5_build_transpose", "spc5_values_grad",
+           "spc5_set_values",
            "spc5_tune", "spc5_convert_tuned", "spc5_convert_tuned_ex", "spc5_spmv_batched",
            "Batch", "spc5_ircg",
            "spc5_convert_hybrid", "spc5_export_hybrid", "spc5_status_str",

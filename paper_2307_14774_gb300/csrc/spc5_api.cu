@@ -82,6 +82,7 @@ struct DeviceGuard {
 void free_matrix(spc5_matrix *A) {
   if (!A) return;
   DeviceGuard g(A->device);
+  free_matrix(A->transpose);
   cudaFree(A->block_rowptr);
   cudaFree(A->panel_vptr);
   cudaFree(A->block_colidx);
@@ -282,6 +283,7 @@ spc5_status spc5_matrix_info(const spc5_matrix *A, spc5_info *info) {
   info->scalar_pieces = A->hybrid ? A->snpieces : 0;
   info->body = A->body;
   info->dynamic = A->dynamic;
+  info->transposed = A->transpose ? 1 : 0;
   info->nnz = A->nnz + A->nscalars;
   info->filling = A->nblocks ? (double)A->nnz / ((double)A->nblocks * A->r * A->c) : 0.0;
   return SPC5_OK;

@@ -241,6 +241,8 @@ extern "C" spc5_status spc5_spmv_t(const spc5_matrix *A, const void *g, void *dx
     return SPC5_EINVAL;
   }
   cudaStream_t s = (cudaStream_t)stream;
+  // with a transposed copy the product is an ordinary SpMV over A^T
+  if (A->transpose) return spmv_device(A->transpose, g, dx, alpha, beta, s);
   cudaError_t e = cudaSuccess;
   switch (A->r * 100 + A->c) {
     case 108: e = dispatch_t<1, 8>(A, g, dx, alpha, beta, s); break;
@@ -308,5 +310,8 @@ extern "C" spc5_status spc5_set_values(spc5_matrix *A, const double *vals, void 
   else
     k_set_values<uint16_t><<<grid, kThreads, 0, s>>>(A->nnz, A->value_src, vals,
                                                      (uint16_t *)A->values);
-  return cuda_check(cudaGetLastError(), "set_values launch");
+  spc5_status st = cuda_check(cudaGetLastError(), "set_values launch");
+  // the transposed copy's value sources index the same CSR
+  if (st == SPC5_OK && A->transpose) st = spc5_set_values(A->transpose, vals, stream);
+  return st;
 }

@@ -151,6 +151,11 @@ struct spc5_matrix {
   // staging for host vectors in spc5_spmv
   void *x_stage = nullptr;
   void *y_stage = nullptr;
+
+  // A^T in beta(r,c), built by spc5_build_transpose (owned; its value_src
+  // holds CSR indices of this matrix's conversion, so that
+  // spc5_set_values refreshes both)
+  spc5_matrix *transpose = nullptr;
 };
 
 namespace spc5 {

@@ -24,7 +24,8 @@ SUPPORTED_RC = ((1, 8), (2, 4), (2, 8), (4, 4), (4, 8), (8, 4))
 
 # Exported symbols declared in include/spc5.h.
 EXPORTS = ("spc5_convert_csr", "spc5_matrix_info", "spc5_export", "spc5_spmv", "spc5_destroy",
-           "spc5_status_str", "spc5_last_error", "spc5_spmv_t", "spc5_values_grad",
+           "spc5_status_str", "spc5_last_error", "spc5_spmv_t", "spc5_build_transpose",
+           "spc5_values_grad",
            "spc5_set_values", "spc5_tune", "spc5_convert_tuned", "spc5_convert_tuned_ex",
            "spc5_spmv_batched",
            "spc5_batch_create", "spc5_batch_run", "spc5_batch_destroy", "spc5_ircg",
@@ -53,7 +54,7 @@ class Info(ctypes.Structure):
                 ("hybrid", ctypes.c_int32), ("nscalars", ctypes.c_int64),
                 ("tuned_rows_us", ctypes.c_double), ("pieces", ctypes.c_int64),
                 ("scalar_pieces", ctypes.c_int64), ("body", ctypes.c_int32),
-                ("dynamic", ctypes.c_int32)]
+                ("dynamic", ctypes.c_int32), ("transposed", ctypes.c_int32)]
 
 
 class CGReport(ctypes.Structure):
@@ -87,6 +88,8 @@ def load(path: str | None = None):
         lib.spc5_export.argtypes = [vp] + [ctypes.POINTER(vp)] * 5
         lib.spc5_spmv.argtypes = [vp, vp, vp, dbl, dbl, vp]
         lib.spc5_spmv_t.argtypes = [vp, vp, vp, dbl, dbl, vp]
+        lib.spc5_build_transpose.argtypes = [vp, vp]
+        lib.spc5_build_transpose.restype = ci
         lib.spc5_values_grad.argtypes = [vp, vp, vp, vp, dbl, vp]
         lib.spc5_set_values.argtypes = [vp, vp, vp]
         for f in (lib.spc5_spmv_t, lib.spc5_values_grad, lib.spc5_set_values):
@@ -318,6 +321,11 @@ def spc5_spmv_t(A: Matrix, g, dx, alpha: float = 1.0, beta: float = 0.0, stream=
     """dx = alpha * A^T g + beta * dx (device vectors)."""
     _check(load().spc5_spmv_t(A.handle, _ptr(g), _ptr(dx), float(alpha), float(beta),
                               _stream_ptr(stream)))
+
+
+def spc5_build_transpose(A: Matrix, stream=None) -> None:
+    """Attach A^T in beta(r,c) to A: spc5_spmv_t then runs as a plain SpMV."""
+    _check(load().spc5_build_transpose(A.handle, _stream_ptr(stream)))
 
 
 def spc5_values_grad(A: Matrix, g, x, dvals, alpha: float = 1.0, stream=None) -> None:
