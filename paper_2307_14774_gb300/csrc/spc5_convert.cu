@@ -513,7 +513,8 @@ __global__ void __launch_bounds__(32 * PanelWarps<FILL>::v)
                     const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
                     const double *__restrict__ vals, int32_t *cnt, const int32_t *brp,
                     int32_t *block_colidx, uint32_t *mask32, int32_t *boff,
-                    typename Store::T *values, int32_t *value_src, uint32_t *err) {
+                    typename Store::T *values, int32_t *value_src, int32_t *ubuf, int32_t *unum,
+                    uint32_t *err) {
   constexpr int kW = PanelWarps<FILL>::v;
   __shared__ PanelSmem<FILL> sm_all[kW];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -546,47 +547,54 @@ __global__ void __launch_bounds__(32 * PanelWarps<FILL>::v)
       }
     }
     __syncwarp();
-    // merged ranks: an entry's index in its row plus, for every other row,
-    // the entries with a smaller column (later rows) or a column not larger
-    // (earlier rows); a column already in an earlier row is a duplicate
-    uint32_t bad = 0;
-    for (int32_t t = lane; t < ne; t += 32) {
-      int32_t st;
-      const int q = panel_row(t, ro, nr, &st);
-      const int32_t x = S.col[t];
-      if (!FILL) {
+    int32_t nu = 0;
+    if (FILL) {  // the union the counting pass left at the panel's CSR offset
+      nu = unum[p];
+      for (int32_t t = lane; t < nu; t += 32) S.uni[t] = ubuf[e0 + t];
+      __syncwarp();
+    } else {  // counting pass: merge the panel's rows
+      // merged ranks: an entry's index in its row plus, for every other row,
+      // the entries with a smaller column (later rows) or a column not larger
+      // (earlier rows); a column already in an earlier row is a duplicate
+      uint32_t bad = 0;
+      for (int32_t t = lane; t < ne; t += 32) {
+        int32_t st;
+        const int q = panel_row(t, ro, nr, &st);
+        const int32_t x = S.col[t];
         if (x < 0 || x >= ncols) bad |= kErrRange;
         if (t > st && S.col[t - 1] >= x) bad |= kErrUnsorted;
-      }
-      int32_t rank = t - st;
-      bool dup = false;
+        int32_t rank = t - st;
+        bool dup = false;
 #pragma unroll
-      for (int qq = 0; qq < 8; ++qq) {
-        if (qq >= nr || qq == q) continue;
-        const int32_t lo = ro[qq], hi = ro[qq + 1];
-        const int32_t lb = lower_bound_i32(S.col, lo, hi, x);
-        int32_t k = lb - lo;
-        if (qq < q) {
-          const bool has = lb < hi && S.col[lb] == x;
-          k += has ? 1 : 0;
-          dup |= has;
+        for (int qq = 0; qq < 8; ++qq) {
+          if (qq >= nr || qq == q) continue;
+          const int32_t lo = ro[qq], hi = ro[qq + 1];
+          const int32_t lb = lower_bound_i32(S.col, lo, hi, x);
+          int32_t k = lb - lo;
+          if (qq < q) {
+            const bool has = lb < hi && S.col[lb] == x;
+            k += has ? 1 : 0;
+            dup |= has;
+          }
+          rank += k;
         }
-        rank += k;
+        S.uni[rank] = dup ? -1 : x;
       }
-      S.uni[rank] = dup ? -1 : x;
-    }
-    if (!FILL && bad) atomicOr(err, bad);
-    __syncwarp();
-    // the union U: merged columns without duplicates, in place
-    int32_t nu = 0;
-    for (int32_t base = 0; base < ne; base += 32) {
-      const int32_t v = (base + lane < ne) ? S.uni[base + lane] : -1;
-      const bool keep = base + lane < ne && v >= 0;
-      const uint32_t ball = __ballot_sync(0xffffffffu, keep);
+      if (bad) atomicOr(err, bad);
       __syncwarp();
-      if (keep) S.uni[nu + __popc(ball & lt)] = v;
-      nu += __popc(ball);
-      __syncwarp();
+      // the union U: merged columns without duplicates, in place
+      for (int32_t base = 0; base < ne; base += 32) {
+        const int32_t v = (base + lane < ne) ? S.uni[base + lane] : -1;
+        const bool keep = base + lane < ne && v >= 0;
+        const uint32_t ball = __ballot_sync(0xffffffffu, keep);
+        __syncwarp();
+        if (keep) S.uni[nu + __popc(ball & lt)] = v;
+        nu += __popc(ball);
+        __syncwarp();
+      }
+      // kept for the filling pass (the union is no longer than the panel)
+      for (int32_t t = lane; t < nu; t += 32) ubuf[e0 + t] = S.uni[t];
+      if (lane == 0) unum[p] = nu;
     }
     // greedy block starts: the first union column not covered opens a block
     int32_t nbk = 0;
@@ -760,13 +768,15 @@ spc5_status convert_panels(spc5_matrix *A, const int32_t *rowptr, const int32_t 
     const int64_t b = (np + warps - 1) / warps;
     return (unsigned)std::min<int64_t>(std::max<int64_t>(b, 1), (int64_t)device_sm_count() * 6);
   };
-  DevBuf<int32_t> cnt(s), scan_tmp(s);
+  DevBuf<int32_t> cnt(s), scan_tmp(s), ubuf(s), unum(s);
   CK(cnt.alloc(np + 1), "alloc block counts");
+  CK(ubuf.alloc(A->nnz), "alloc panel unions");
+  CK(unum.alloc(np), "alloc panel union sizes");
   CK(scan_tmp.alloc(scan_tmp_elems(np + 1)), "alloc scan tmp");
   k_panel_convert<false, StoreF64><<<grid_of(PanelWarps<false>::v), 32 * PanelWarps<false>::v, 0,
                                       s>>>(
       np, n, A->ncols, r, c, rowptr, colidx, vals, cnt.p, nullptr, nullptr, nullptr, nullptr,
-      nullptr, nullptr, err);
+      nullptr, nullptr, ubuf.p, unum.p, err);
   uint32_t h[2] = {0, 0};
   CK(cudaMemcpyAsync(h, err, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s), "read err");
   CK(cudaStreamSynchronize(s), "sync validation");
@@ -798,7 +808,7 @@ spc5_status convert_panels(spc5_matrix *A, const int32_t *rowptr, const int32_t 
 #define PANEL_FILL(STORE, T)                                                                  \
   k_panel_convert<true, STORE><<<grid_of(PanelWarps<true>::v), 32 * PanelWarps<true>::v, 0, s>>>( \
       np, n, A->ncols, r, c, rowptr, colidx, vals, nullptr, A->block_rowptr, A->block_colidx, \
-      mask32.p, boff.p, (T *)A->values, A->value_src, err)
+      mask32.p, boff.p, (T *)A->values, A->value_src, ubuf.p, unum.p, err)
   if (A->value_dtype == SPC5_F64)
     PANEL_FILL(StoreF64, double);
   else if (A->value_dtype == SPC5_F32)
