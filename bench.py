@@ -145,7 +145,8 @@ def plan_label(info):
         return flat
     label = f"rows/G{info['lanes_per_row']}"
     if "body" in info:
-        label += f"/b{info['body']}" + ("/dyn" if info.get("dynamic") else "")
+        label += (f"/b{info['body']}" + ("/dyn" if info.get("dynamic") else "") +
+                  ("/half" if info.get("halves") else ""))
     return label
 
 

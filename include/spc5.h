@@ -104,6 +104,10 @@ typedef struct {
                               passing empty blocks */
   int32_t dynamic;         /* 1 if row-group tiles are taken from a counter, 0 grid-stride */
   int32_t transposed;      /* 1 if spc5_build_transpose attached a transposed copy */
+  int32_t halves;          /* 1 if the row-group plan cut the groups of the last round of
+                              tiles into two half tiles (tried by spc5_tune, kept when
+                              faster; it applies when that round fills at most half the
+                              resident warps) */
 } spc5_info;
 
 /*

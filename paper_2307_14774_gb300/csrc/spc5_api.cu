@@ -284,6 +284,7 @@ spc5_status spc5_matrix_info(const spc5_matrix *A, spc5_info *info) {
   info->body = A->body;
   info->dynamic = A->dynamic;
   info->transposed = A->transpose ? 1 : 0;
+  info->halves = A->halves;
   info->nnz = A->nnz + A->nscalars;
   info->filling = A->nblocks ? (double)A->nnz / ((double)A->nblocks * A->r * A->c) : 0.0;
   return SPC5_OK;

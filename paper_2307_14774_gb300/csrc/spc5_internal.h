@@ -115,6 +115,7 @@ struct spc5_matrix {
                                     // bits (else set-bit loop), bit 1 = x staged in smem
   int kernel = 0;                   // 0: direct tile kernel, 1: staged tile kernel
   int dynamic = 0;                  // row-group kernel: tiles from a counter (else grid-stride)
+  int halves = 0;                   // row-group plan: the last round's groups cut in halves
   double tuned_us = 0.0;            // SpMV time of the plan chosen by spc5_tune (0 = untuned)
   double tuned_rows_us = 0.0;       // SpMV time of the best row-group plan it found
   uint32_t *dev_error = nullptr;    // set by kernels on a timed-out wait
@@ -188,6 +189,7 @@ struct PlanOptions {
   int body = -1;    // consumer body
   int flat = -1;    // 0: row groups, 1: block-balanced plan, 2: expanded plan
   int dynamic = -1; // row groups: 1 = tiles taken from a counter, 0 = dealt grid-stride
+  int halves = -1;  // row groups: 1 = the groups of the last round of tiles as two half tiles
 };
 
 // Work plan of the SpMV kernels; called by the converter while the

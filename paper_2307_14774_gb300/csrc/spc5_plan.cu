@@ -25,6 +25,7 @@
 #include <stdlib.h>
 
 #include <algorithm>
+#include <climits>
 
 #include "spc5_internal.h"
 #include "spc5_scan.cuh"
@@ -53,6 +54,8 @@ struct PlanParams {
   const int32_t *brp, *vptr;
   int32_t skip;     // direct kernel: heavy panels leave their group tile
   int32_t hv, hb;   // a panel is heavy above hv values or hb blocks
+  int64_t half_from;  // groups from this one on (without heavy panels) are
+                      // two tiles of gp / 2 panels, twice the lanes per row
 };
 
 __device__ __forceinline__ bool group_fat(const PlanParams &P, int64_t g) {
@@ -93,6 +96,13 @@ __device__ __forceinline__ bool has_group_tile(const PlanParams &P, int64_t p) {
   const int64_t n = (p + P.gp < P.npanels) ? P.gp : P.npanels - p;
   const uint32_t all = n >= 32 ? 0xffffffffu : ((1u << n) - 1u);
   return group_heavy(P, p / P.gp) != all;
+}
+
+// Group of panel p cut into two tiles of half the panels (the last round of
+// the tile dealing, see plan_tiles).
+__device__ __forceinline__ bool group_halved(const PlanParams &P, int64_t p) {
+  const int64_t g = p / P.gp;
+  return P.skip && P.gp >= 2 && g >= P.half_from && group_heavy(P, g) == 0u;
 }
 
 // Index of a panel's first own tile: with skip, the first panel of a group
@@ -136,7 +146,9 @@ __global__ void k_piece_flags(PlanParams P, const int32_t *bpanel, const int32_t
 __global__ void k_tile_counts(PlanParams P, const int32_t *pscan, int32_t *tc, int32_t *lf) {
   GRID_STRIDE(p, P.npanels) {
     int32_t t = 0, l = 0;
-    if (P.skip) {  // the group tile, then the panel's own tiles
+    if (P.skip && group_halved(P, p)) {
+      t = (p % (P.gp / 2) == 0) ? 1 : 0;
+    } else if (P.skip) {  // the group tile, then the panel's own tiles
       t = (p % P.gp == 0 && has_group_tile(P, p)) ? 1 : 0;
       if (panel_long(P, p)) {
         t += pscan[P.brp[p + 1]] - pscan[P.brp[p]];
@@ -161,6 +173,15 @@ __global__ void k_write_panel_tiles(PlanParams P, const int32_t *tbase, const in
                                     const int32_t *pscan, Tile *tiles, int32_t *long_panels,
                                     int32_t *long_slots) {
   GRID_STRIDE(p, P.npanels) {
+    if (group_halved(P, p)) {  // one of the group's two half tiles
+      const int32_t h = P.gp / 2;
+      if (p % h == 0) {
+        const int64_t p1 = (p + h < P.npanels) ? p + h : P.npanels;
+        tiles[tbase[p]] = Tile{(int32_t)p, (int32_t)p1, P.brp[p], P.brp[p1], P.vptr[p],
+                               P.vptr[p1], -1, P.log2g_group + 1};
+      }
+      continue;
+    }
     const bool own = panel_own(P, p);
     if (p % P.gp == 0 && (P.skip ? has_group_tile(P, p) : !own)) {  // the group tile
       int64_t p1 = (p + P.gp < P.npanels) ? p + P.gp : P.npanels;
@@ -402,10 +423,11 @@ __global__ void k_ex_write_pieces(ExpandParams E, const int32_t *bpanel, const i
   }
 }
 
-// Busy share of the row-group plan's block slots: a group tile keeps
-// group_panels * G slots busy for as many rounds as its longest panel needs.
-__global__ void k_group_efficiency(const Tile *tiles, int64_t ntiles, const int32_t *brp, int gp,
-                                   unsigned long long *acc) {
+// Busy share of the row-group plan's block slots: a group tile keeps its
+// panels * G = 32 / r slots busy for as many rounds as its longest panel
+// needs (per_round = 32 / r).
+__global__ void k_group_efficiency(const Tile *tiles, int64_t ntiles, const int32_t *brp,
+                                   int per_round, unsigned long long *acc) {
   unsigned long long used = 0, slots = 0;
   GRID_STRIDE(t, ntiles) {
     const Tile T = tiles[t];
@@ -422,7 +444,7 @@ __global__ void k_group_efficiency(const Tile *tiles, int64_t ntiles, const int3
         used += nbp;
         mx = nbp > mx ? nbp : mx;
       }
-      slots += (int64_t)gp * G * ((mx + G - 1) / G);
+      slots += (int64_t)per_round * ((mx + G - 1) / G);
     }
   }
   atomicAdd(&acc[0], used);
@@ -570,7 +592,7 @@ spc5_status plan_flat(spc5_matrix *A, const int32_t *boff, cudaStream_t s,
   CK(cudaMemsetAsync(acc.p, 0, 2 * sizeof(unsigned long long), s), "memset");
   if (A->ntiles > 0)
     k_group_efficiency<<<std::min<unsigned>(grid_for(A->ntiles), 1024u), kThreads, 0, s>>>(
-        A->tiles, A->ntiles, A->block_rowptr, A->group_panels, acc.p);
+        A->tiles, A->ntiles, A->block_rowptr, 32 / A->r, acc.p);
   unsigned long long hacc[2] = {0, 0};
   CK(cudaMemcpyAsync(hacc, acc.p, sizeof(hacc), cudaMemcpyDeviceToHost, s), "rd");
 
@@ -778,11 +800,13 @@ spc5_status plan_tiles(spc5_matrix *A, const uint32_t *mask32, const int32_t *bo
                    : std::min(std::max(opt.body >= 0 ? opt.body : env_int("SPC5_BODY", 0), 0), 7);
   A->dynamic = (opt.dynamic >= 0 ? opt.dynamic : env_int("SPC5_DYNAMIC", 0)) != 0 ? 1 : 0;
 
+  A->halves = 0;
   if (np == 0) return SPC5_OK;
   PlanParams P{np, nb, gp, vcap, bcap, vcap - 32, log2g, log2g_segment,
                A->block_rowptr, A->panel_vptr, staged ? 0 : 1,
                (int32_t)std::min<double>(std::max(8.0 * avg_v, 64.0), (double)vcap),
-               (int32_t)std::min<double>(std::max(8.0 * avg_b, 8.0), (double)bcap)};
+               (int32_t)std::min<double>(std::max(8.0 * avg_b, 8.0), (double)bcap),
+               INT64_MAX};
 
   Tmp<int32_t> bpanel(s), pf(s), pscan(s), tc(s), tbase(s), lf(s), lbase(s), tmp(s);
   CK(bpanel.alloc(nb), "alloc");
@@ -816,6 +840,35 @@ spc5_status plan_tiles(spc5_matrix *A, const uint32_t *mask32, const int32_t *bo
   CK(cudaMemcpyAsync(&counts[1], lbase.p + np, sizeof(int32_t), cudaMemcpyDeviceToHost, s), "rd");
   CK(cudaMemcpyAsync(&counts[2], pscan.p + nb, sizeof(int32_t), cudaMemcpyDeviceToHost, s), "rd");
   CK(cudaStreamSynchronize(s), "sync plan counts");
+  {
+    // The direct kernel deals tiles grid-stride over its resident warps W,
+    // so T tiles take ceil(T / W) rounds and the last one, T mod W tiles,
+    // keeps part of the GPU busy for a whole tile's time (27-point 100^3,
+    // beta(4,8): 31250 tiles over 7296 warps, a fifth round for 2066 of
+    // them).  When that round fills at most half the warps, its groups are
+    // cut into two tiles of half the panels with twice the lanes per row:
+    // each half tile takes about half a tile's time, but runs the general
+    // loop instead of a one-lane-per-row body (measured -7 % to +7 %), so
+    // spc5_tune tries it on the winning row-group plan.
+    const int per_sm = A->body == 4 ? 40 : (A->body == 6 ? 64 : 48);
+    const int64_t W = (int64_t)device_sm_count() * per_sm;
+    const int64_t T = counts[0], rem = W > 0 ? T % W : 0;
+    const int64_t ngroups = (np + gp - 1) / gp;
+    const bool want = (opt.halves >= 0 ? opt.halves : env_int("SPC5_HALVES", 0)) != 0;
+    A->halves = 0;
+    if (!staged && want && gp >= 2 && log2g < log2g_segment && T > W && rem > 0 &&
+        2 * rem <= W && rem <= ngroups) {
+      A->halves = 1;
+      P.half_from = ngroups - rem;
+      k_tile_counts<<<grid_for(np), kThreads, 0, s>>>(P, pscan.p, tc.p, lf.p);
+      CK(device_scan<int32_t>(np + 1, ReadI32Pad{tc.p, np}, WriteI32{tbase.p}, AddI32{}, 0,
+                              false, tmp.p, s),
+         "scan tiles");
+      CK(cudaMemcpyAsync(&counts[0], tbase.p + np, sizeof(int32_t), cudaMemcpyDeviceToHost, s),
+         "rd");
+      CK(cudaStreamSynchronize(s), "sync plan counts");
+    }
+  }
   A->ntiles = counts[0];
   A->nlong = counts[1];
   A->npieces = counts[2];

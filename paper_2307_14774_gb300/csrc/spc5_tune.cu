@@ -136,6 +136,22 @@ spc5_status tune(spc5_matrix *A, const void *x, void *y, int iters, cudaStream_t
       st = replan(A, s, o);
       if (st != SPC5_OK) return st;
     }
+    // and cutting the groups of the last round of tiles in halves
+    o.halves = 1;
+    st = replan(A, s, o);
+    if (st != SPC5_OK) return st;
+    const double uh = time_spmv(A, x, y, iters, s);
+    if (uh < 0) {
+      set_error("timing a candidate plan failed");
+      return SPC5_ECUDA;
+    }
+    if (uh < best) {
+      best = best_rows = uh;
+    } else {
+      o.halves = 0;
+      st = replan(A, s, o);
+      if (st != SPC5_OK) return st;
+    }
   }
   A->tuned_us = best;
   A->tuned_rows_us = best_rows;

@@ -54,7 +54,8 @@ class Info(ctypes.Structure):
                 ("hybrid", ctypes.c_int32), ("nscalars", ctypes.c_int64),
                 ("tuned_rows_us", ctypes.c_double), ("pieces", ctypes.c_int64),
                 ("scalar_pieces", ctypes.c_int64), ("body", ctypes.c_int32),
-                ("dynamic", ctypes.c_int32), ("transposed", ctypes.c_int32)]
+                ("dynamic", ctypes.c_int32), ("transposed", ctypes.c_int32),
+                ("halves", ctypes.c_int32)]
 
 
 class CGReport(ctypes.Structure):
