@@ -446,7 +446,8 @@ __global__ void k_check_offsets(int64_t npanels, const int32_t *block_rowptr,
 // ------------------------------------------------ panel-local conversion --
 //
 // When no panel holds more than kPanelCap entries (stencils, FEM meshes,
-// uniform rows: every matrix whose rows are not very long), one warp
+// uniform rows: every matrix whose rows are not very long; the kernels come
+// sized for panels of 1024 and of 2048 entries), one warp
 // converts a whole panel in shared memory, with the rule of the flat passes
 // above: the merged rank of every entry among the panel's rows (binary
 // searches in the other rows, now in shared memory), the union U in merged
@@ -457,22 +458,24 @@ __global__ void k_check_offsets(int64_t npanels, const int32_t *block_rowptr,
 // columns), a prefix sum of the counts places every panel's blocks, the
 // second writes them.  Nothing global is built per entry, so the
 // conversion reads the CSR twice and writes the beta(r,c) arrays once.
-constexpr int kPanelCap = 1024;      // entries of a panel
+constexpr int kPanelCap = 2048;      // entries of a panel (two capacities: 1024, 2048)
 constexpr int kPanelBlockCap = 256;  // blocks of a panel (the filling pass)
 
-// Shared memory of one warp (the counting pass needs the first two arrays
-// only, and runs more warps per CTA).
-template <bool FILL>
+// Shared memory of one warp for panels of at most CAP entries (the counting
+// pass needs the first two arrays only, and runs more warps per CTA).
+template <bool FILL, int CAP>
 struct PanelSmem {
-  int32_t col[kPanelCap];     // the panel's columns, row after row (CSR order)
-  int32_t uni[kPanelCap];     // merged columns (-1: not the first occurrence),
+  int32_t col[CAP];           // the panel's columns, row after row (CSR order)
+  int32_t uni[CAP];           // merged columns (-1: not the first occurrence),
                               // then the union U, then the blocks' value offsets
   int32_t bst[FILL ? kPanelBlockCap : 1];     // block starts
   uint32_t bmask[FILL ? kPanelBlockCap : 1];  // block masks
 };
-template <bool FILL>
+// Warps per CTA: 30 / 32 KB of shared memory per CTA at CAP = 1024, 18 /
+// 32 KB at CAP = 2048 (panels of 1024 to 2048 entries, FEM beta(8,4)).
+template <bool FILL, int CAP>
 struct PanelWarps {
-  static constexpr int v = FILL ? 3 : 4;  // 30 / 32 KB of shared memory per CTA
+  static constexpr int v = CAP <= 1024 ? (FILL ? 3 : 4) : (FILL ? 1 : 2);
 };
 
 // Row q of panel entry t (ro[q] <= t < ro[q + 1]) and ro[q].
@@ -507,19 +510,19 @@ __global__ void k_panel_max_entries(int64_t np, int64_t nrows, int r, const int3
 // FILL = false: cnt[p] = blocks of panel p, and the column checks.
 // FILL = true: block columns, masks (as 32-bit words), block value offsets,
 // values and value sources of every panel (brp = block_rowptr).
-template <bool FILL, typename Store>
-__global__ void __launch_bounds__(32 * PanelWarps<FILL>::v)
+template <bool FILL, int CAP, typename Store>
+__global__ void __launch_bounds__(32 * PanelWarps<FILL, CAP>::v)
     k_panel_convert(int64_t np, int64_t nrows, int64_t ncols, int r, int c,
                     const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
                     const double *__restrict__ vals, int32_t *cnt, const int32_t *brp,
                     int32_t *block_colidx, uint32_t *mask32, int32_t *boff,
                     typename Store::T *values, int32_t *value_src, int32_t *ubuf, int32_t *unum,
                     uint32_t *err) {
-  constexpr int kW = PanelWarps<FILL>::v;
-  __shared__ PanelSmem<FILL> sm_all[kW];
+  constexpr int kW = PanelWarps<FILL, CAP>::v;
+  __shared__ PanelSmem<FILL, CAP> sm_all[kW];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t lt = (1u << lane) - 1u;
-  PanelSmem<FILL> &S = sm_all[warp];
+  PanelSmem<FILL, CAP> &S = sm_all[warp];
   const int64_t nw = (int64_t)gridDim.x * kW;
   for (int64_t p = (int64_t)blockIdx.x * kW + warp; p < np; p += nw) {
     const int64_t r0 = p * r;
@@ -754,27 +757,30 @@ spc5_status alloc_outputs(spc5_matrix *A, int64_t nb, cudaStream_t s) {
   return SPC5_OK;
 }
 
-// The panel-local conversion (every panel at most kPanelCap entries; the
-// row pointers already checked).  *flat is set, and nothing converted, when
-// some panel has more than kPanelBlockCap blocks.
+// The panel-local conversion (every panel at most CAP entries; the row
+// pointers already checked).  *flat is set, and nothing converted, when some
+// panel has more than kPanelBlockCap blocks.
+template <int CAP>
 spc5_status convert_panels(spc5_matrix *A, const int32_t *rowptr, const int32_t *colidx,
                            const double *vals, uint32_t *err, cudaStream_t s, bool *flat) {
   *flat = false;
   const int64_t n = A->nrows, np = A->npanels;
   const int r = A->r, c = A->c;
   const int mask_bytes = r * c / 8;
-  // six CTAs of 32 KB per SM
-  auto grid_of = [&](int warps) {
+  // the CTAs of 18 to 32 KB that one SM holds
+  auto grid_of = [&](int warps, int per_sm) {
     const int64_t b = (np + warps - 1) / warps;
-    return (unsigned)std::min<int64_t>(std::max<int64_t>(b, 1), (int64_t)device_sm_count() * 6);
+    return (unsigned)std::min<int64_t>(std::max<int64_t>(b, 1),
+                                       (int64_t)device_sm_count() * per_sm);
   };
+  constexpr int kWc = PanelWarps<false, CAP>::v, kWf = PanelWarps<true, CAP>::v;
+  constexpr int kCtasc = 6, kCtasf = CAP <= 1024 ? 6 : 12;
   DevBuf<int32_t> cnt(s), scan_tmp(s), ubuf(s), unum(s);
   CK(cnt.alloc(np + 1), "alloc block counts");
   CK(ubuf.alloc(A->nnz), "alloc panel unions");
   CK(unum.alloc(np), "alloc panel union sizes");
   CK(scan_tmp.alloc(scan_tmp_elems(np + 1)), "alloc scan tmp");
-  k_panel_convert<false, StoreF64><<<grid_of(PanelWarps<false>::v), 32 * PanelWarps<false>::v, 0,
-                                      s>>>(
+  k_panel_convert<false, CAP, StoreF64><<<grid_of(kWc, kCtasc), 32 * kWc, 0, s>>>(
       np, n, A->ncols, r, c, rowptr, colidx, vals, cnt.p, nullptr, nullptr, nullptr, nullptr,
       nullptr, nullptr, ubuf.p, unum.p, err);
   uint32_t h[2] = {0, 0};
@@ -806,7 +812,7 @@ spc5_status convert_panels(spc5_matrix *A, const int32_t *rowptr, const int32_t 
   CK(mask32.alloc(nb), "alloc mask32");
   CK(boff.alloc(nb), "alloc boff");
 #define PANEL_FILL(STORE, T)                                                                  \
-  k_panel_convert<true, STORE><<<grid_of(PanelWarps<true>::v), 32 * PanelWarps<true>::v, 0, s>>>( \
+  k_panel_convert<true, CAP, STORE><<<grid_of(kWf, kCtasf), 32 * kWf, 0, s>>>(              \
       np, n, A->ncols, r, c, rowptr, colidx, vals, nullptr, A->block_rowptr, A->block_colidx, \
       mask32.p, boff.p, (T *)A->values, A->value_src, ubuf.p, unum.p, err)
   if (A->value_dtype == SPC5_F64)
@@ -859,7 +865,10 @@ spc5_status convert_device(spc5_matrix *A, const int32_t *rowptr, const int32_t 
       if ((int32_t)h[1] <= kPanelCap) {
         CK(cudaMemsetAsync(err.p + 1, 0, sizeof(uint32_t), s), "memset");
         bool flat = false;
-        spc5_status st = convert_panels(A, rowptr, colidx, vals, err.p, s, &flat);
+        spc5_status st =
+            (int32_t)h[1] <= 1024
+                ? convert_panels<1024>(A, rowptr, colidx, vals, err.p, s, &flat)
+                : convert_panels<2048>(A, rowptr, colidx, vals, err.p, s, &flat);
         if (st != SPC5_OK || !flat) return st;
       }
     }
