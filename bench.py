@@ -586,9 +586,10 @@ def grad_section(torch, spc5, synth, hbm, log, reps=10):
         # stored values + blocks + g + dx (written once)
         "spmv_t": (lambda: spc5.spc5_spmv_t(M, g, dx),
                    4 * A.nnz + meta + 4 * A.nrows + 4 * A.ncols),
-        # blocks + g + x + value_src + dvals
+        # blocks + g + x + the CSR row pointer + dvals (written from each
+        # row's CSR start; value_src is not read)
         "values_grad": (lambda: spc5.spc5_values_grad(M, g, x32, dvals),
-                        meta + 4 * A.nrows + 4 * A.ncols + 4 * A.nnz + 4 * A.nnz),
+                        meta + 4 * A.nrows + 4 * A.ncols + 4 * (A.nrows + 1) + 4 * A.nnz),
     }
     out["kernels"] = {}
 

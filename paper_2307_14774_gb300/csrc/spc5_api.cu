@@ -89,6 +89,7 @@ void free_matrix(spc5_matrix *A) {
   cudaFree(A->masks);
   cudaFree(A->values);
   cudaFree(A->value_src);
+  cudaFree(A->csr_rowptr);
   cudaFree(A->x_stage);
   cudaFree(A->y_stage);
   cudaFree(A->tiles);
@@ -204,6 +205,15 @@ spc5_status spc5_convert_csr(int64_t nrows, int64_t ncols, int64_t nnz, const in
   if (st == SPC5_OK && nnz > 0)
     st = stage(vals, (size_t)nnz * sizeof(double), 2, (const void **)&d_vals);
   if (st == SPC5_OK) st = convert_device(A, d_rowptr, d_colidx, d_vals, s);
+  if (st == SPC5_OK) {  // kept for the values gradient (4 bytes per row)
+    st = cuda_check(cudaMalloc((void **)&A->csr_rowptr, (size_t)(nrows + 1) * sizeof(int32_t)),
+                    "alloc CSR row pointer");
+    if (st == SPC5_OK)
+      st = cuda_check(cudaMemcpyAsync(A->csr_rowptr, d_rowptr, (size_t)(nrows + 1) * 4,
+                                      cudaMemcpyDeviceToDevice, s),
+                      "copy CSR row pointer");
+    if (st == SPC5_OK) A->device_bytes += (nrows + 1) * 4;
+  }
   for (void *p : tmp)
     if (p) cudaFreeAsync(p, s);
   if (st == SPC5_OK) st = cuda_check(cudaStreamSynchronize(s), "sync conversion");

@@ -9,8 +9,11 @@
 // from the panel offset plus popcount scans), so long panels are split into
 // bounded pieces here too; they need no row reduction.  The transpose
 // scatters with atomic adds (results are exact up to the order of the
-// additions).  Values are addressed through value_src, the CSR index of
-// every stored value, recorded by the converter.
+// additions).  The values gradient writes a row's entries from the row's
+// CSR start (kept by the converter), since a lane walks its row's entries
+// in column order, which is CSR order; pieces of long panels, which do not
+// see their rows' earlier entries, address them through value_src, the CSR
+// index of every stored value.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -26,10 +29,12 @@ constexpr unsigned kFull = 0xffffffffu;
 constexpr int kThreads = 256;
 
 
-// Calls f(row, col, mq, off, valid) for every block of the lane's row in the
+// Calls f(row, col, mq, off, rc) for every block of the lane's row in the
 // tile: row = global row, col = block start column, mq = the row's c-bit
-// mask, off = index of the row's first value of the block.
-template <int R, int C, typename F>
+// mask, off = index of the row's first value of the block, rc (COUNT only)
+// = the row's values in the tile's earlier blocks (a group scan of the row
+// bits over the G lanes of the row).
+template <int R, int C, bool COUNT = false, typename F>
 __device__ __forceinline__ void walk_tile(const Tile &cur, int lane,
                                           const int32_t *__restrict__ brp,
                                           const int32_t *__restrict__ vptr,
@@ -65,11 +70,13 @@ __device__ __forceinline__ void walk_tile(const Tile &cur, int lane,
   const int64_t row = p * R + q;
   const bool rvalid = pvalid && row < nrows;
   const int32_t maxnb = __reduce_max_sync(kFull, nbp);
+  int32_t rc = 0;
   for (int32_t it = 0; it < maxnb; it += G) {
     const int32_t idx = it + g;
     const bool valid = idx < nbp;
     const uint32_t m = valid ? (uint32_t)masks[bl + idx] : 0u;
     const int32_t col = valid ? bcol[bl + idx] : 0;
+    const uint32_t mq = (m >> (q * C)) & cmask;
     const int pc = __popc(m);
     int incl = pc;
     for (int o = 1; o < G; o <<= 1) {
@@ -78,7 +85,18 @@ __device__ __forceinline__ void walk_tile(const Tile &cur, int lane,
     }
     const int total = (G > 1) ? __shfl_sync(kFull, incl, G - 1, G) : pc;
     const int32_t off = v + (incl - pc) + __popc(m & row_low);
-    if (rvalid) f(row, col, (m >> (q * C)) & cmask, off);
+    int32_t rq = 0;
+    if (COUNT) {  // the row's values in the earlier blocks of this round
+      const int pq = __popc(mq);
+      int iq = pq;
+      for (int o = 1; o < G; o <<= 1) {
+        int t = __shfl_up_sync(kFull, iq, o, G);
+        if (g >= o) iq += t;
+      }
+      rq = rc + iq - pq;
+      rc += (G > 1) ? __shfl_sync(kFull, iq, G - 1, G) : pq;
+    }
+    if (rvalid) f(row, col, mq, off, rq);
     v += total;
   }
 }
@@ -95,7 +113,7 @@ __global__ void __launch_bounds__(kThreads)
        t += nwarps) {
     const Tile cur = tiles[t];
     walk_tile<R, C>(cur, lane, brp, vptr, bcol, masks, nrows,
-                    [&](int64_t row, int32_t col, uint32_t mq, int32_t off) {
+                    [&](int64_t row, int32_t col, uint32_t mq, int32_t off, int32_t) {
                       const AT gr = alpha * g[row];
                       while (mq) {
                         const int k = __ffs(mq) - 1;
@@ -112,22 +130,39 @@ __global__ void __launch_bounds__(kThreads)
                   const int32_t *__restrict__ brp, const int32_t *__restrict__ vptr,
                   const int32_t *__restrict__ bcol,
                   const typename MaskType<R, C>::T *__restrict__ masks,
-                  const int32_t *__restrict__ value_src, const AT *__restrict__ g,
-                  const AT *__restrict__ x, AT *__restrict__ dvals, AT alpha, int64_t nrows) {
+                  const int32_t *__restrict__ value_src, const int32_t *__restrict__ csr_rowptr,
+                  const AT *__restrict__ g, const AT *__restrict__ x, AT *__restrict__ dvals,
+                  AT alpha, int64_t nrows) {
   const int lane = threadIdx.x & 31;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < ntiles;
        t += nwarps) {
     const Tile cur = tiles[t];
-    walk_tile<R, C>(cur, lane, brp, vptr, bcol, masks, nrows,
-                    [&](int64_t row, int32_t col, uint32_t mq, int32_t off) {
-                      const AT gr = alpha * g[row];
-                      while (mq) {
-                        const int k = __ffs(mq) - 1;
-                        mq &= mq - 1u;
-                        dvals[value_src[off++]] = gr * x[col + k];
-                      }
-                    });
+    if ((cur.mode & kPartial) || !csr_rowptr) {  // a piece of a long panel: its rows'
+                                                 // earlier values are in other tiles, so
+                                                 // the positions come from value_src
+      walk_tile<R, C>(cur, lane, brp, vptr, bcol, masks, nrows,
+                      [&](int64_t row, int32_t col, uint32_t mq, int32_t off, int32_t) {
+                        const AT gr = alpha * g[row];
+                        while (mq) {
+                          const int k = __ffs(mq) - 1;
+                          mq &= mq - 1u;
+                          dvals[value_src[off++]] = gr * x[col + k];
+                        }
+                      });
+    } else {  // whole panels: a row's entries in column order are its CSR entries, written
+              // from the row's CSR start on (value_src is not read)
+      walk_tile<R, C, true>(cur, lane, brp, vptr, bcol, masks, nrows,
+                            [&](int64_t row, int32_t col, uint32_t mq, int32_t, int32_t rc) {
+                              const AT gr = alpha * g[row];
+                              AT *dst = dvals + csr_rowptr[row] + rc;
+                              while (mq) {
+                                const int k = __ffs(mq) - 1;
+                                mq &= mq - 1u;
+                                *dst++ = gr * x[col + k];
+                              }
+                            });
+    }
   }
 }
 
@@ -191,8 +226,8 @@ cudaError_t run_grad(const spc5_matrix *A, const void *g, const void *x, void *d
   if (A->ntiles > 0)
     k_values_grad<R, C, AT><<<tile_grid(A->ntiles), kThreads, 0, s>>>(
         A->tiles, A->ntiles, A->block_rowptr, A->panel_vptr, A->block_colidx,
-        (const MT *)A->masks, A->value_src, (const AT *)g, (const AT *)x, (AT *)dvals,
-        (AT)alpha, A->nrows);
+        (const MT *)A->masks, A->value_src, A->csr_rowptr, (const AT *)g, (const AT *)x,
+        (AT *)dvals, (AT)alpha, A->nrows);
   return cudaGetLastError();
 }
 

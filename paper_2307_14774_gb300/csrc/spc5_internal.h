@@ -98,6 +98,8 @@ struct spc5_matrix {
   void *masks = nullptr;            // nblocks * r * c / 8 bytes (+16 bytes of padding)
   void *values = nullptr;           // nnz values (+16 bytes of padding)
   int32_t *value_src = nullptr;     // CSR index of every stored value (nnz)
+  int32_t *csr_rowptr = nullptr;    // the conversion's CSR row pointer (nrows + 1): the
+                                    // values gradient writes a row's entries from it
   int64_t device_bytes = 0;
 
   // SpMV plan (built by the converter)
