@@ -7,6 +7,7 @@
 
 #include <atomic>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 
@@ -41,6 +42,36 @@ int device_sm_count() {
     cache[dev].store(n, std::memory_order_relaxed);
   }
   return n;
+}
+
+cudaError_t scratch_alloc(void **p, size_t bytes, cudaStream_t s) {
+  static std::atomic<cudaMemPool_t> pools[kMaxDevices];
+  static std::mutex mu;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaMallocAsync(p, bytes, s);
+  cudaMemPool_t pool = pools[dev].load(std::memory_order_acquire);
+  if (!pool) {
+    std::lock_guard<std::mutex> lock(mu);
+    pool = pools[dev].load(std::memory_order_relaxed);
+    if (!pool) {
+      cudaMemPoolProps props = {};
+      props.allocType = cudaMemAllocationTypePinned;
+      props.location.type = cudaMemLocationTypeDevice;
+      props.location.id = dev;
+      e = cudaMemPoolCreate(&pool, &props);
+      if (e != cudaSuccess) return e;
+      uint64_t keep = kScratchKeep;
+      e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+      if (e != cudaSuccess) {
+        cudaMemPoolDestroy(pool);
+        return e;
+      }
+      pools[dev].store(pool, std::memory_order_release);
+    }
+  }
+  return cudaMallocFromPoolAsync(p, bytes, pool, s);
 }
 
 bool supported_rc(int r, int c) {
@@ -192,7 +223,7 @@ spc5_status spc5_convert_csr(int64_t nrows, int64_t ncols, int64_t nnz, const in
       return SPC5_EINVAL;
     }
     if (pl == Placement::kDevice) return SPC5_OK;
-    spc5_status e = cuda_check(cudaMallocAsync(&tmp[slot], bytes > 0 ? bytes : 4, s), "alloc staging");
+    spc5_status e = cuda_check(scratch_alloc(&tmp[slot], bytes > 0 ? bytes : 4, s), "alloc staging");
     if (e != SPC5_OK) return e;
     e = cuda_check(cudaMemcpyAsync(tmp[slot], src, bytes, cudaMemcpyHostToDevice, s), "copy CSR");
     if (e != SPC5_OK) return e;

@@ -446,45 +446,48 @@ __global__ void k_check_offsets(int64_t npanels, const int32_t *block_rowptr,
 // ------------------------------------------------ panel-local conversion --
 //
 // When no panel holds more than kPanelCap entries (stencils, FEM meshes,
-// uniform rows: every matrix whose rows are not very long; the kernels come
-// sized for panels of 1024 and of 2048 entries), one warp
-// converts a whole panel in shared memory, with the rule of the flat passes
-// above: the merged rank of every entry among the panel's rows (binary
-// searches in the other rows, now in shared memory), the union U in merged
-// order, the greedy block starts over U (a ballot finds the first union
-// column not covered by the previous block, one step per block), then masks,
-// the blocks' value offsets (prefix sum of popcounts) and the value scatter.
-// Two passes over the panels: the first counts blocks (and checks the
-// columns), a prefix sum of the counts places every panel's blocks, the
-// second writes them.  Nothing global is built per entry, so the
-// conversion reads the CSR twice and writes the beta(r,c) arrays once.
+// uniform rows: every matrix whose rows are not very long; the kernel comes
+// sized for panels of 1024 and of 2048 entries), one warp converts a whole
+// panel in shared memory, with the rule of the flat passes above: the
+// panel's columns merged in (column, row) order (a tree of pairwise merges
+// of the sorted rows), the union U without repeats, the greedy block starts
+// over U (a ballot finds the first union column not covered by the previous
+// block, one step per block), then masks, the blocks' value offsets (prefix
+// sum of popcounts) and the value scatter.  One pass over the panels: a
+// panel's values start at its CSR offset e0 (it holds exactly its rows'
+// entries), so values and value sources go to their final places at once;
+// a panel has no more blocks than entries, so its blocks go to scratch
+// arrays at e0, with the panel's block count.  A prefix sum of the counts
+// then places every panel's blocks, and a compaction copies them there.
+// The values are read once, the columns once (twice for r >= 4).
 constexpr int kPanelCap = 2048;      // entries of a panel (two capacities: 1024, 2048)
-constexpr int kPanelBlockCap = 256;  // blocks of a panel (the filling pass)
+constexpr int kPanelBlockCap = 256;  // blocks of a panel
 
-// Shared memory of one warp for panels of at most CAP entries (the counting
-// pass needs the first two arrays only, and runs more warps per CTA).
-template <bool FILL, int CAP>
+// Shared memory of one warp for panels of at most CAP entries.
+template <int CAP>
 struct PanelSmem {
-  int32_t col[CAP];           // the panel's columns, row after row (CSR order)
-  int32_t uni[CAP];           // merged columns (-1: not the first occurrence),
-                              // then the union U, then the blocks' value offsets
-  int32_t bst[FILL ? kPanelBlockCap : 1];     // block starts
-  uint32_t bmask[FILL ? kPanelBlockCap : 1];  // block masks
+  int32_t col[CAP];                  // the panel's columns, row after row (CSR order)
+  int32_t uni[CAP];                  // merged columns (-1: not the first occurrence),
+                                     // then the union U, then every entry's block
+  int32_t bst[kPanelBlockCap];       // block starts
+  uint32_t bmask[kPanelBlockCap];    // block masks
+  int32_t boffs[kPanelBlockCap];     // block value offsets in the panel
 };
-// Warps per CTA: 30 / 32 KB of shared memory per CTA at CAP = 1024, 18 /
-// 32 KB at CAP = 2048 (panels of 1024 to 2048 entries, FEM beta(8,4)).
-template <bool FILL, int CAP>
+// Warps per CTA: 33 KB of shared memory per CTA at CAP = 1024, 19 KB at
+// CAP = 2048 (panels of 1024 to 2048 entries, FEM beta(8,4)).
+template <int CAP>
 struct PanelWarps {
-  static constexpr int v = CAP <= 1024 ? (FILL ? 3 : 4) : (FILL ? 1 : 2);
+  static constexpr int v = CAP <= 1024 ? 3 : 1;
 };
 
 // Row q of panel entry t (ro[q] <= t < ro[q + 1]) and ro[q].
-__device__ __forceinline__ int panel_row(int32_t t, const int32_t (&ro)[9], int nr,
+template <int R>
+__device__ __forceinline__ int panel_row(int32_t t, const int32_t (&ro)[R + 1], int nr,
                                          int32_t *rstart) {
   int q = 0;
   int32_t st = ro[0];
 #pragma unroll
-  for (int qq = 1; qq < 8; ++qq) {
+  for (int qq = 1; qq < R; ++qq) {
     if (qq < nr && t >= ro[qq]) {
       q = qq;
       st = ro[qq];
@@ -507,32 +510,34 @@ __global__ void k_panel_max_entries(int64_t np, int64_t nrows, int r, const int3
   if ((threadIdx.x & 31) == 0) atomicMax(out, mx);
 }
 
-// FILL = false: cnt[p] = blocks of panel p, and the column checks.
-// FILL = true: block columns, masks (as 32-bit words), block value offsets,
-// values and value sources of every panel (brp = block_rowptr).
-template <bool FILL, int CAP, typename Store>
-__global__ void __launch_bounds__(32 * PanelWarps<FILL, CAP>::v)
+// Every panel: cnt[p] = its blocks; its block starts, masks (as 32-bit
+// words) and value offsets at [e0, e0 + cnt[p]) of tcol, tmask, tboff; its
+// values and value sources at their final places.  A panel with a column
+// out of range or out of order is reported in err[0] and left out; a panel
+// of more than kPanelBlockCap blocks raises err[1] to its count and is left
+// out (the host then takes the flat passes).
+template <int CAP, int R, typename Store>
+__global__ void __launch_bounds__(32 * PanelWarps<CAP>::v)
     k_panel_convert(int64_t np, int64_t nrows, int64_t ncols, int r, int c,
                     const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
-                    const double *__restrict__ vals, int32_t *cnt, const int32_t *brp,
-                    int32_t *block_colidx, uint32_t *mask32, int32_t *boff,
-                    typename Store::T *values, int32_t *value_src, int32_t *ubuf, int32_t *unum,
-                    uint32_t *err) {
-  constexpr int kW = PanelWarps<FILL, CAP>::v;
-  __shared__ PanelSmem<FILL, CAP> sm_all[kW];
+                    const double *__restrict__ vals, int32_t *cnt, int32_t *tcol,
+                    uint32_t *tmask, int32_t *tboff, typename Store::T *values,
+                    int32_t *value_src, uint32_t *err) {
+  constexpr int kW = PanelWarps<CAP>::v;
+  __shared__ PanelSmem<CAP> sm_all[kW];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t lt = (1u << lane) - 1u;
-  PanelSmem<FILL, CAP> &S = sm_all[warp];
+  PanelSmem<CAP> &S = sm_all[warp];
   const int64_t nw = (int64_t)gridDim.x * kW;
   for (int64_t p = (int64_t)blockIdx.x * kW + warp; p < np; p += nw) {
     const int64_t r0 = p * r;
     const int nr = (int)((r0 + r <= nrows) ? r : nrows - r0);
     const int32_t rp = (lane <= nr) ? rowptr[r0 + lane] : 0;
     const int32_t e0 = __shfl_sync(0xffffffffu, rp, 0);
-    int32_t ro[9];
+    int32_t ro[R + 1];
 #pragma unroll
-    for (int q = 0; q < 9; ++q) ro[q] = __shfl_sync(0xffffffffu, rp, q < nr ? q : nr) - e0;
-    const int32_t ne = ro[8];
+    for (int q = 0; q <= R; ++q) ro[q] = __shfl_sync(0xffffffffu, rp, q < nr ? q : nr) - e0;
+    const int32_t ne = ro[R];
     __syncwarp();
     // eight loads in flight per lane (a loop that stores each load before
     // issuing the next waits one memory latency per 32 entries)
@@ -550,54 +555,86 @@ __global__ void __launch_bounds__(32 * PanelWarps<FILL, CAP>::v)
       }
     }
     __syncwarp();
-    int32_t nu = 0;
-    if (FILL) {  // the union the counting pass left at the panel's CSR offset
-      nu = unum[p];
-      for (int32_t t = lane; t < nu; t += 32) S.uni[t] = ubuf[e0 + t];
-      __syncwarp();
-    } else {  // counting pass: merge the panel's rows
-      // merged ranks: an entry's index in its row plus, for every other row,
-      // the entries with a smaller column (later rows) or a column not larger
-      // (earlier rows); a column already in an earlier row is a duplicate
-      uint32_t bad = 0;
-      for (int32_t t = lane; t < ne; t += 32) {
-        int32_t st;
-        const int q = panel_row(t, ro, nr, &st);
-        const int32_t x = S.col[t];
-        if (x < 0 || x >= ncols) bad |= kErrRange;
-        if (t > st && S.col[t - 1] >= x) bad |= kErrUnsorted;
-        int32_t rank = t - st;
-        bool dup = false;
-#pragma unroll
-        for (int qq = 0; qq < 8; ++qq) {
-          if (qq >= nr || qq == q) continue;
-          const int32_t lo = ro[qq], hi = ro[qq + 1];
-          const int32_t lb = lower_bound_i32(S.col, lo, hi, x);
-          int32_t k = lb - lo;
-          if (qq < q) {
-            const bool has = lb < hi && S.col[lb] == x;
-            k += has ? 1 : 0;
-            dup |= has;
-          }
-          rank += k;
-        }
-        S.uni[rank] = dup ? -1 : x;
-      }
+    // the columns: in range and strictly ascending in every row
+    uint32_t bad = 0;
+    for (int32_t t = lane; t < ne; t += 32) {
+      int32_t st;
+      panel_row<R>(t, ro, nr, &st);
+      const int32_t x = S.col[t];
+      if (x < 0 || x >= ncols) bad |= kErrRange;
+      if (t > st && S.col[t - 1] >= x) bad |= kErrUnsorted;
+    }
+    if (__any_sync(0xffffffffu, bad != 0u)) {
       if (bad) atomicOr(err, bad);
+      if (lane == 0) cnt[p] = 0;
       __syncwarp();
-      // the union U: merged columns without duplicates, in place
-      for (int32_t base = 0; base < ne; base += 32) {
-        const int32_t v = (base + lane < ne) ? S.uni[base + lane] : -1;
-        const bool keep = base + lane < ne && v >= 0;
-        const uint32_t ball = __ballot_sync(0xffffffffu, keep);
-        __syncwarp();
-        if (keep) S.uni[nu + __popc(ball & lt)] = v;
-        nu += __popc(ball);
-        __syncwarp();
+      continue;
+    }
+    // the panel's columns in (column, row) order: a tree of pairwise merges
+    // of sorted runs (rows, then pairs of rows, ...) between the two column
+    // buffers.  At a level of runs of h rows, an entry of a left run moves
+    // to its group's start plus its index in its run plus the entries of
+    // the right run with a smaller column; an entry of a right run counts
+    // the left run's entries with a column not larger (a stable merge).
+    // The counts are branch-free binary searches with as many steps as the
+    // longest run has bits.
+    int32_t *src = S.col, *dst = S.uni;
+#pragma unroll
+    for (int h = 1; h < R; h <<= 1) {
+      int32_t longest = 0;
+#pragma unroll
+      for (int k = 0; k < R / h; ++k) longest = max(longest, ro[(k + 1) * h] - ro[k * h]);
+      const int steps = 32 - __clz(longest);
+      __syncwarp();
+      for (int32_t t = lane; t < ne; t += 32) {
+        // the run of entry t: its start hs, its group's start gs, and the
+        // other run of the group [ss, se) (selects, no indexed registers)
+        bool left = true;
+        int32_t gs = ro[0], hs = ro[0], ss = ro[h], se = ro[2 * h];
+#pragma unroll
+        for (int kk = 1; kk < R / h; ++kk) {
+          if (t >= ro[kk * h]) {
+            left = (kk & 1) == 0;
+            hs = ro[kk * h];
+            gs = ro[(kk & ~1) * h];
+            ss = ro[(kk ^ 1) * h];
+            se = ro[((kk ^ 1) + 1) * h];
+          }
+        }
+        const int32_t x = src[t];
+        int32_t base = ss, len = se - ss;
+        for (int s = 0; s < steps; ++s) {
+          if (len > 0) {
+            const int32_t half = len >> 1;
+            const int32_t v = src[base + half];
+            const bool before = left ? v < x : v <= x;
+            base = before ? base + half + 1 : base;
+            len = before ? len - half - 1 : half;
+          }
+        }
+        dst[gs + (t - hs) + (base - ss)] = x;
       }
-      // kept for the filling pass (the union is no longer than the panel)
-      for (int32_t t = lane; t < nu; t += 32) ubuf[e0 + t] = S.uni[t];
-      if (lane == 0) unum[p] = nu;
+      int32_t *tmp = src;
+      src = dst;
+      dst = tmp;
+    }
+    __syncwarp();
+    // the union U: the merged columns without repeats, into uni (in place
+    // when the merge ended there: the previous chunk's last column is kept
+    // in a register, so no lane reads a slot already rewritten)
+    int32_t nu = 0, last = -1;
+    for (int32_t base = 0; base < ne; base += 32) {
+      const bool in = base + lane < ne;
+      const int32_t v = in ? src[base + lane] : -1;
+      int32_t prev = __shfl_up_sync(0xffffffffu, v, 1);
+      if (lane == 0) prev = last;
+      last = __shfl_sync(0xffffffffu, v, 31);
+      const bool keep = in && v != prev;
+      const uint32_t ball = __ballot_sync(0xffffffffu, keep);
+      __syncwarp();
+      if (keep) S.uni[nu + __popc(ball & lt)] = v;
+      nu += __popc(ball);
+      __syncwarp();
     }
     // greedy block starts: the first union column not covered opens a block
     int32_t nbk = 0;
@@ -609,36 +646,58 @@ __global__ void __launch_bounds__(32 * PanelWarps<FILL, CAP>::v)
         const uint32_t ball = __ballot_sync(0xffffffffu, in && (long long)u >= thr);
         if (!ball) break;
         const int32_t sb = __shfl_sync(0xffffffffu, u, __ffs(ball) - 1);
-        if (FILL && lane == 0 && nbk < kPanelBlockCap) S.bst[nbk] = sb;
+        if (lane == 0 && nbk < kPanelBlockCap) S.bst[nbk] = sb;
         ++nbk;
         thr = (long long)sb + c;
       }
     }
-    if (!FILL) {
-      if (lane == 0) {
-        cnt[p] = nbk;
-        if (nbk > kPanelBlockCap) atomicMax((int32_t *)err + 1, nbk);
-      }
+    if (lane == 0) cnt[p] = nbk;
+    if (nbk > kPanelBlockCap) {
+      if (lane == 0) atomicMax((int32_t *)err + 1, nbk);
+      __syncwarp();
       continue;
     }
     __syncwarp();
-    const int32_t gb0 = brp[p];
-    if (gb0 + nbk != brp[p + 1] || nbk > kPanelBlockCap) {  // cannot happen: both passes
-                                                            // count alike, the host checked
-      if (lane == 0) atomicOr(err, kErrInternal);
-      continue;
+    if (R >= 4) {  // merges of two levels and more wrote over the CSR-order columns
+      for (int32_t t0 = 0; t0 < ne; t0 += 256) {
+        int32_t v[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int32_t t = t0 + i * 32 + lane;
+          v[i] = t < ne ? colidx[e0 + t] : 0;
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int32_t t = t0 + i * 32 + lane;
+          if (t < ne) S.col[t] = v[i];
+        }
+      }
+      __syncwarp();
     }
     for (int32_t i = lane; i < nbk; i += 32) {
-      block_colidx[gb0 + i] = S.bst[i];
+      tcol[e0 + i] = S.bst[i];
       S.bmask[i] = 0u;
     }
     __syncwarp();
-    // masks: an entry's block is the last start not after its column
+    // masks: an entry's block is the last start not after its column (the
+    // columns are checked, so every entry lies in [bst[b], bst[b] + c));
+    // kept per entry for the value scatter (the union is no longer needed)
+    const int bsteps = 32 - __clz(nbk);
     for (int32_t t = lane; t < ne; t += 32) {
       int32_t st;
-      const int q = panel_row(t, ro, nr, &st);
+      const int q = panel_row<R>(t, ro, nr, &st);
       const int32_t x = S.col[t];
-      const int32_t b = lower_bound_i32(S.bst, 0, nbk, x + 1) - 1;
+      int32_t b = 0, len = nbk;  // first start > x, by branch-free halving
+      for (int s = 0; s < bsteps; ++s) {
+        if (len > 0) {
+          const int32_t half = len >> 1;
+          const bool le = S.bst[b + half] <= x;
+          b = le ? b + half + 1 : b;
+          len = le ? len - half - 1 : half;
+        }
+      }
+      --b;
+      S.uni[t] = b;
       atomicOr(&S.bmask[b], 1u << (q * c + (x - S.bst[b])));
     }
     __syncwarp();
@@ -655,9 +714,9 @@ __global__ void __launch_bounds__(32 * PanelWarps<FILL, CAP>::v)
         if (lane >= o) incl += t2;
       }
       if (in) {
-        S.uni[base + lane] = run + incl - pc;
-        mask32[gb0 + base + lane] = m;
-        boff[gb0 + base + lane] = e0 + run + incl - pc;
+        S.boffs[base + lane] = run + incl - pc;
+        tmask[e0 + base + lane] = m;
+        tboff[e0 + base + lane] = e0 + run + incl - pc;
       }
       run += __shfl_sync(0xffffffffu, incl, 31);
     }
@@ -675,17 +734,41 @@ __global__ void __launch_bounds__(32 * PanelWarps<FILL, CAP>::v)
         const int32_t t = t0 + i * 32 + lane;
         if (t < ne) {
           int32_t st;
-          const int q = panel_row(t, ro, nr, &st);
+          const int q = panel_row<R>(t, ro, nr, &st);
           const int32_t x = S.col[t];
-          const int32_t b = lower_bound_i32(S.bst, 0, nbk, x + 1) - 1;
+          const int32_t b = S.uni[t];
           const int bit = q * c + (x - S.bst[b]);
-          const int32_t dst = e0 + S.uni[b] + __popc(S.bmask[b] & ((1u << bit) - 1u));
+          const int32_t dst = e0 + S.boffs[b] + __popc(S.bmask[b] & ((1u << bit) - 1u));
           values[dst] = Store::cvt(v[i]);
           value_src[dst] = e0 + t;
         }
       }
     }
     __syncwarp();
+  }
+}
+
+// Moves every panel's blocks from its CSR offset to its place (brp =
+// block_rowptr): block columns, masks (32-bit and packed), value offsets.
+// Eight lanes per panel.
+template <typename MaskT>
+__global__ void k_panel_compact(int64_t np, int r, const int32_t *rowptr,
+                                const int32_t *brp, const int32_t *tcol, const uint32_t *tmask,
+                                const int32_t *tboff, int32_t *block_colidx, MaskT *masks,
+                                uint32_t *mask32, int32_t *boff) {
+  const int64_t gl = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 3;
+  const int sl = threadIdx.x & 7;
+  const int64_t ng = ((int64_t)gridDim.x * blockDim.x) >> 3;
+  for (int64_t p = gl; p < np; p += ng) {
+    const int32_t e0 = rowptr[p * r];
+    const int32_t g0 = brp[p], n = brp[p + 1] - g0;
+    for (int32_t i = sl; i < n; i += 8) {
+      const uint32_t m = tmask[e0 + i];
+      block_colidx[g0 + i] = tcol[e0 + i];
+      masks[g0 + i] = (MaskT)m;
+      mask32[g0 + i] = m;
+      boff[g0 + i] = tboff[e0 + i];
+    }
   }
 }
 
@@ -699,7 +782,7 @@ struct DevBuf {
   T *p = nullptr;
   cudaStream_t s;
   explicit DevBuf(cudaStream_t st) : s(st) {}
-  cudaError_t alloc(int64_t n) { return cudaMallocAsync((void **)&p, (size_t)std::max<int64_t>(n, 1) * sizeof(T), s); }
+  cudaError_t alloc(int64_t n) { return scratch_alloc((void **)&p, (size_t)std::max<int64_t>(n, 1) * sizeof(T), s); }
   ~DevBuf() {
     if (p) cudaFreeAsync(p, s);
   }
@@ -735,21 +818,28 @@ spc5_status err_to_status(uint32_t err) {
 
 namespace {
 
-// Output arrays of a conversion with nb blocks (every array padded by 16
-// bytes: the staged SpMV copies 16-byte aligned windows that may end up to
-// 15 bytes past the last element).
-spc5_status alloc_outputs(spc5_matrix *A, int64_t nb, cudaStream_t s) {
-  const int64_t nnz = A->nnz, np = A->npanels;
-  const int mask_bytes = A->r * A->c / 8;
+// Output arrays of a conversion (every array padded by 16 bytes: the staged
+// SpMV copies 16-byte aligned windows that may end up to 15 bytes past the
+// last element): those sized by the entries, then those sized by the nb
+// blocks.
+spc5_status alloc_values(spc5_matrix *A, cudaStream_t s) {
+  const int64_t nnz = A->nnz;
   const size_t vsize = A->value_dtype == SPC5_F64 ? 8 : A->value_dtype == SPC5_F32 ? 4 : 2;
   CK(cudaMalloc(&A->values, (size_t)nnz * vsize + 16), "alloc values");
   CK(cudaMalloc((void **)&A->value_src, (size_t)nnz * sizeof(int32_t) + 16), "alloc value_src");
   CK(cudaMalloc((void **)&A->dev_error, sizeof(uint32_t)), "alloc error word");
   CK(cudaMemsetAsync(A->dev_error, 0, sizeof(uint32_t), s), "zero error word");
+  return SPC5_OK;
+}
+
+spc5_status alloc_blocks(spc5_matrix *A, int64_t nb, cudaStream_t s) {
+  const int64_t nnz = A->nnz, np = A->npanels;
+  const int mask_bytes = A->r * A->c / 8;
+  const size_t vsize = A->value_dtype == SPC5_F64 ? 8 : A->value_dtype == SPC5_F32 ? 4 : 2;
   CK(cudaMalloc((void **)&A->block_colidx, (size_t)nb * sizeof(int32_t) + 16), "alloc colidx");
   CK(cudaMalloc(&A->masks, (size_t)nb * mask_bytes + 16), "alloc masks");
-  CK(cudaMemsetAsync(A->block_colidx, 0, (size_t)nb * sizeof(int32_t) + 16, s), "zero colidx");
-  CK(cudaMemsetAsync(A->masks, 0, (size_t)nb * mask_bytes + 16, s), "zero masks");
+  CK(cudaMemsetAsync((char *)A->block_colidx + nb * sizeof(int32_t), 0, 16, s), "zero colidx pad");
+  CK(cudaMemsetAsync((char *)A->masks + nb * mask_bytes, 0, 16, s), "zero masks pad");
   A->nblocks = nb;
   A->device_bytes = (int64_t)(2 * (np + 1) * sizeof(int32_t) + 32 + nnz * vsize + 16 +
                              nnz * sizeof(int32_t) + 16) +
@@ -757,80 +847,105 @@ spc5_status alloc_outputs(spc5_matrix *A, int64_t nb, cudaStream_t s) {
   return SPC5_OK;
 }
 
+void release(void **p) {
+  cudaFree(*p);
+  *p = nullptr;
+}
+
 // The panel-local conversion (every panel at most CAP entries; the row
-// pointers already checked).  *flat is set, and nothing converted, when some
+// pointers already checked).  *flat is set, and nothing kept, when some
 // panel has more than kPanelBlockCap blocks.
 template <int CAP>
 spc5_status convert_panels(spc5_matrix *A, const int32_t *rowptr, const int32_t *colidx,
                            const double *vals, uint32_t *err, cudaStream_t s, bool *flat) {
   *flat = false;
-  const int64_t n = A->nrows, np = A->npanels;
+  const int64_t n = A->nrows, np = A->npanels, nnz = A->nnz;
   const int r = A->r, c = A->c;
   const int mask_bytes = r * c / 8;
-  // the CTAs of 18 to 32 KB that one SM holds
-  auto grid_of = [&](int warps, int per_sm) {
-    const int64_t b = (np + warps - 1) / warps;
-    return (unsigned)std::min<int64_t>(std::max<int64_t>(b, 1),
-                                       (int64_t)device_sm_count() * per_sm);
-  };
-  constexpr int kWc = PanelWarps<false, CAP>::v, kWf = PanelWarps<true, CAP>::v;
-  constexpr int kCtasc = 6, kCtasf = CAP <= 1024 ? 6 : 12;
-  DevBuf<int32_t> cnt(s), scan_tmp(s), ubuf(s), unum(s);
+  // the CTAs of 19 to 33 KB that one SM holds
+  constexpr int kW = PanelWarps<CAP>::v;
+  constexpr int kCtas = CAP <= 1024 ? 6 : 11;
+  const unsigned grid = (unsigned)std::min<int64_t>(std::max<int64_t>((np + kW - 1) / kW, 1),
+                                                    (int64_t)device_sm_count() * kCtas);
+  DevBuf<int32_t> cnt(s), scan_tmp(s), tcol(s), tboff(s);
+  DevBuf<uint32_t> tmask(s);
   CK(cnt.alloc(np + 1), "alloc block counts");
-  CK(ubuf.alloc(A->nnz), "alloc panel unions");
-  CK(unum.alloc(np), "alloc panel union sizes");
   CK(scan_tmp.alloc(scan_tmp_elems(np + 1)), "alloc scan tmp");
-  k_panel_convert<false, CAP, StoreF64><<<grid_of(kWc, kCtasc), 32 * kWc, 0, s>>>(
-      np, n, A->ncols, r, c, rowptr, colidx, vals, cnt.p, nullptr, nullptr, nullptr, nullptr,
-      nullptr, nullptr, ubuf.p, unum.p, err);
-  uint32_t h[2] = {0, 0};
-  CK(cudaMemcpyAsync(h, err, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s), "read err");
-  CK(cudaStreamSynchronize(s), "sync validation");
-  if (h[0]) return err_to_status(h[0]);
-  if ((int32_t)h[1] > kPanelBlockCap) {
-    *flat = true;
-    return SPC5_OK;
-  }
-  uint32_t herr = 0;
+  CK(tcol.alloc(nnz), "alloc block scratch");
+  CK(tmask.alloc(nnz), "alloc block scratch");
+  CK(tboff.alloc(nnz), "alloc block scratch");
+  spc5_status st = alloc_values(A, s);
+  if (st != SPC5_OK) return st;
   CK(cudaMalloc((void **)&A->block_rowptr, (size_t)(np + 1) * sizeof(int32_t) + 16),
      "alloc block_rowptr");
   CK(cudaMalloc((void **)&A->panel_vptr, (size_t)(np + 1) * sizeof(int32_t) + 16),
      "alloc panel_vptr");
+#define PANEL_PASS(RR, STORE, T)                                                           \
+  k_panel_convert<CAP, RR, STORE><<<grid, 32 * kW, 0, s>>>(                                  \
+      np, n, A->ncols, r, c, rowptr, colidx, vals, cnt.p, tcol.p, tmask.p, tboff.p,          \
+      (T *)A->values, A->value_src, err)
+#define PANEL_PASS_R(RR)                        \
+  if (A->value_dtype == SPC5_F64)               \
+    PANEL_PASS(RR, StoreF64, double);           \
+  else if (A->value_dtype == SPC5_F32)          \
+    PANEL_PASS(RR, StoreF32, float);            \
+  else                                          \
+    PANEL_PASS(RR, StoreBF16, uint16_t)
+  if (r == 1) {
+    PANEL_PASS_R(1);
+  } else if (r == 2) {
+    PANEL_PASS_R(2);
+  } else if (r == 4) {
+    PANEL_PASS_R(4);
+  } else {
+    PANEL_PASS_R(8);
+  }
+#undef PANEL_PASS_R
+#undef PANEL_PASS
   CK(device_scan<int32_t>(np + 1, ReadI32Pad{cnt.p, np}, WriteI32{A->block_rowptr}, AddI32{}, 0,
                           false, scan_tmp.p, s),
      "scan block counts");
+  k_panel_vptr<<<grid_for(np + 1), kThreads, 0, s>>>(np, n, r, rowptr, A->panel_vptr);
+  uint32_t h[2] = {0, 0};
   int32_t nb32 = 0;
+  CK(cudaMemcpyAsync(h, err, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s), "read err");
   CK(cudaMemcpyAsync(&nb32, A->block_rowptr + np, sizeof(int32_t), cudaMemcpyDeviceToHost, s),
      "read nb");
-  CK(cudaStreamSynchronize(s), "sync nb");
+  CK(cudaStreamSynchronize(s), "sync panel pass");
+  if (h[0]) return err_to_status(h[0]);
+  if ((int32_t)h[1] > kPanelBlockCap) {  // the flat passes allocate their own outputs
+    release(&A->values);
+    release((void **)&A->value_src);
+    release((void **)&A->dev_error);
+    release((void **)&A->block_rowptr);
+    release((void **)&A->panel_vptr);
+    *flat = true;
+    return SPC5_OK;
+  }
   const int64_t nb = nb32;
-  spc5_status st = alloc_outputs(A, nb, s);
+  st = alloc_blocks(A, nb, s);
   if (st != SPC5_OK) return st;
-  k_panel_vptr<<<grid_for(np + 1), kThreads, 0, s>>>(np, n, r, rowptr, A->panel_vptr);
   DevBuf<uint32_t> mask32(s);
   DevBuf<int32_t> boff(s);
   CK(mask32.alloc(nb), "alloc mask32");
   CK(boff.alloc(nb), "alloc boff");
-#define PANEL_FILL(STORE, T)                                                                  \
-  k_panel_convert<true, CAP, STORE><<<grid_of(kWf, kCtasf), 32 * kWf, 0, s>>>(              \
-      np, n, A->ncols, r, c, rowptr, colidx, vals, nullptr, A->block_rowptr, A->block_colidx, \
-      mask32.p, boff.p, (T *)A->values, A->value_src, ubuf.p, unum.p, err)
-  if (A->value_dtype == SPC5_F64)
-    PANEL_FILL(StoreF64, double);
-  else if (A->value_dtype == SPC5_F32)
-    PANEL_FILL(StoreF32, float);
-  else
-    PANEL_FILL(StoreBF16, uint16_t);
-#undef PANEL_FILL
+  const unsigned cgrid = (unsigned)std::min<int64_t>(std::max<int64_t>((np + 31) / 32, 1),
+                                                     (int64_t)device_sm_count() * 8);
+#define PANEL_COMPACT(MT)                                                                  \
+  k_panel_compact<MT><<<cgrid, kThreads, 0, s>>>(np, r, rowptr, A->block_rowptr, tcol.p,  \
+                                                 tmask.p, tboff.p, A->block_colidx,       \
+                                                 (MT *)A->masks, mask32.p, boff.p)
   if (mask_bytes == 1)
-    k_pack_masks<uint8_t><<<grid_for(nb), kThreads, 0, s>>>(nb, mask32.p, (uint8_t *)A->masks);
+    PANEL_COMPACT(uint8_t);
   else if (mask_bytes == 2)
-    k_pack_masks<uint16_t><<<grid_for(nb), kThreads, 0, s>>>(nb, mask32.p, (uint16_t *)A->masks);
+    PANEL_COMPACT(uint16_t);
   else
-    k_pack_masks<uint32_t><<<grid_for(nb), kThreads, 0, s>>>(nb, mask32.p, (uint32_t *)A->masks);
+    PANEL_COMPACT(uint32_t);
+#undef PANEL_COMPACT
   spc5_status pst = plan_tiles(A, mask32.p, boff.p, s);
   if (pst != SPC5_OK) return pst;
   CK(cudaGetLastError(), "conversion kernels");
+  uint32_t herr = 0;
   CK(cudaMemcpyAsync(&herr, err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s), "read err");
   CK(cudaStreamSynchronize(s), "sync conversion");
   if (herr) return err_to_status(herr);

@@ -175,6 +175,16 @@ bool supported_rc(int r, int c);
 // Multiprocessor count of the current device (looked up once per device).
 int device_sm_count();
 
+// Stream-ordered scratch of the builders (conversion, tile planning,
+// transposition, hybrid split, CSR staging), freed with cudaFreeAsync: it
+// comes from a private memory pool of the current device that keeps up to
+// kScratchKeep bytes mapped between calls, so that a conversion does not map
+// and unmap gigabytes of scratch every time (mapping is most of the host
+// time of a large conversion).  Memory above that is returned to the device
+// at the next synchronisation, as with the default pool.
+constexpr uint64_t kScratchKeep = 8ull << 30;
+cudaError_t scratch_alloc(void **p, size_t bytes, cudaStream_t s);
+
 // Largest device ordinal the library's per-device tables hold, plus one.
 constexpr int kMaxDevices = 64;
 

@@ -457,7 +457,7 @@ struct Tmp {
   cudaStream_t s;
   explicit Tmp(cudaStream_t st) : s(st) {}
   cudaError_t alloc(int64_t n) {
-    return cudaMallocAsync((void **)&p, (size_t)std::max<int64_t>(n, 1) * sizeof(T), s);
+    return scratch_alloc((void **)&p, (size_t)std::max<int64_t>(n, 1) * sizeof(T), s);
   }
   ~Tmp() {
     if (p) cudaFreeAsync(p, s);

@@ -156,7 +156,7 @@ struct Buf {
   cudaStream_t s;
   explicit Buf(cudaStream_t st) : s(st) {}
   cudaError_t alloc(int64_t n) {
-    return cudaMallocAsync((void **)&p, (size_t)std::max<int64_t>(n, 1) * sizeof(T), s);
+    return scratch_alloc((void **)&p, (size_t)std::max<int64_t>(n, 1) * sizeof(T), s);
   }
   ~Buf() {
     if (p) cudaFreeAsync(p, s);
