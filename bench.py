@@ -476,21 +476,33 @@ def dense_section(torch, spc5, synth, stream, hbm, log, n=2048, reps=20, tune=Tr
             "write) before every timed launch; median of " + str(reps), "rows": rows}
 
 
-def cg_section(torch, spc5, synth, stream, hbm, log):
+def cg_section(torch, spc5, synth, stream, hbm, log, tune=True):
     """Mixed-precision iterative-refinement CG on the SPD 27-point Poisson
     matrix on 128^3 (26 on the diagonal, -1 off it), b ~ U[-1,1), to
     ||b - A x|| / ||b|| <= 1e-10, with the inner solve in FP32, BF16 and (as
-    the all-FP64 reference) FP64 storage; the outer residual is FP64."""
+    the all-FP64 reference) FP64 storage; the outer residual is FP64.  Both
+    matrices are tuned first, as every benchmarked matrix is."""
     A = synth.workload("poisson27_128")
     b = synth.vector_uniform(A.nrows, seed=8)
     dev = [torch.from_numpy(a).cuda() for a in (A.rowptr, A.colidx, A.vals)]
     db = torch.from_numpy(b).cuda()
     A64 = spc5.spc5_convert_csr(A.nrows, A.ncols, A.nnz, *dev, r=4, c=8, stream=stream)
+    x64 = torch.empty(A.ncols, dtype=torch.float64, device="cuda")
+    y64 = torch.empty(A.nrows, dtype=torch.float64, device="cuda")
+    x32 = torch.empty(A.ncols, dtype=torch.float32, device="cuda")
+    y32 = torch.empty(A.nrows, dtype=torch.float32, device="cuda")
+    if tune:
+        spc5.spc5_tune(A64, x64, y64, iters=3)
     out = {"matrix": "27-point Poisson 128^3", "n": A.nrows, "nnz": A.nnz, "tol": 1e-10,
-           "rows": []}
+           "outer_plan": plan_label(A64.info()), "rows": []}
     for name, code in (("f32", spc5.SPC5_F32), ("bf16", spc5.SPC5_BF16), ("f64", spc5.SPC5_F64)):
         Alo = spc5.spc5_convert_csr(A.nrows, A.ncols, A.nnz, *dev, store_dtype=code, r=4, c=8,
                                     stream=stream)
+        if tune:
+            if code == spc5.SPC5_F64:
+                spc5.spc5_tune(Alo, x64, y64, iters=3)
+            else:
+                spc5.spc5_tune(Alo, x32, y32, iters=3)
         for _ in range(2):  # first run warms up; second is timed
             dx = torch.zeros(A.nrows, dtype=torch.float64, device="cuda")
             torch.cuda.synchronize()
@@ -511,7 +523,7 @@ def cg_section(torch, spc5, synth, stream, hbm, log):
         vbytes = 11 * A.nrows * (8 if code == spc5.SPC5_F64 else 4)
         it_bytes = algorithmic_bytes(ilo) + vbytes
         us_it = secs / max(1, rep["inner_iters"]) * 1e6
-        out["rows"].append({"inner": name, "seconds": round(secs, 4), **rep,
+        out["rows"].append({"inner": name, "plan": plan_label(ilo), "seconds": round(secs, 4), **rep,
                             "relres_check": relres,
                             "us_per_inner_iter": round(us_it, 2),
                             "bytes_per_inner_iter": int(it_bytes),
@@ -939,7 +951,7 @@ def run_native(args):
     if not args.no_batched and rank == 0:
         result["batched"] = batched_section(torch, spc5, synth, stream, hbm, log)
     if not args.no_cg and rank == 0:
-        result["ircg"] = cg_section(torch, spc5, synth, stream, hbm, log)
+        result["ircg"] = cg_section(torch, spc5, synth, stream, hbm, log, tune=not args.no_tune)
     if not args.no_grad and rank == 0:
         result["autograd"] = grad_section(torch, spc5, synth, hbm, log)
     if not args.no_dense and rank == 0:

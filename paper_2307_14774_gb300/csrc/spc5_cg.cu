@@ -10,8 +10,11 @@
 // One inner iteration is a fixed sequence of kernels whose scalars (alpha,
 // beta, r.r) live in device memory; it is captured once as a CUDA graph and
 // replayed, and the host reads r.r only every few iterations.  Reductions
-// are two-pass (per-block partials, then one block in fixed order), so the
-// solver is deterministic for a deterministic SpMV.
+// are two-level (per-block partials, then one block sums them in fixed
+// order), so the solver is deterministic for a deterministic SpMV.  In the
+// inner iteration the second level runs in the last block of the first to
+// finish (a ticket counter) and computes alpha or beta right there, so an
+// iteration is the SpMV plus three launches.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -60,6 +63,47 @@ __global__ void __launch_bounds__(kT) k_dot_final(const double *part, int nparts
   if (threadIdx.x == 0) *out = s;
 }
 
+// The last of the grid's blocks to finish (ticket) sums the partials in
+// block order, as k_dot_final does, and its thread 0 stores the sum in
+// *out; returns true in that block only.  The ticket is reset for the next
+// launch.  Each block publishes its partial with a fence before taking its
+// ticket, and the last block reads the partials through L2.
+__device__ __forceinline__ bool last_block_sum(double s, double *part, unsigned *ticket,
+                                               double *out) {
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = s;
+    __threadfence();
+    last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return false;
+  __threadfence();
+  double t = 0.0;
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += kT) t += __ldcg(part + i);
+  t = block_sum(t);
+  if (threadIdx.x == 0) {
+    *out = t;
+    *ticket = 0u;
+  }
+  return true;
+}
+
+// p.q, then alpha = rr / p.q (one launch of the inner iteration)
+template <typename T>
+__global__ void __launch_bounds__(kT) k_dot_alpha(int64_t n, const T *p, const T *q,
+                                                  double *part, unsigned *ticket, Scal *sc) {
+  double s = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x; i < n; i += (int64_t)gridDim.x * kT)
+    s += (double)p[i] * (double)q[i];
+  s = block_sum(s);
+  double pq;
+  if (last_block_sum(s, part, ticket, &pq) && threadIdx.x == 0) {
+    sc->pq = pq;
+    sc->alpha = (pq != 0.0) ? sc->rr / pq : 0.0;
+  }
+}
+
 // p = r, rr = rr_new (start of the inner solve), d = 0.
 template <typename T>
 __global__ void k_cg_start(int64_t n, const T *r, T *p, T *d) {
@@ -69,20 +113,15 @@ __global__ void k_cg_start(int64_t n, const T *r, T *p, T *d) {
   }
 }
 
-__global__ void k_scalars_alpha(Scal *s) { s->alpha = (s->pq != 0.0) ? s->rr / s->pq : 0.0; }
-__global__ void k_scalars_beta(Scal *s) {
-  s->beta = (s->rr != 0.0) ? s->rr_new / s->rr : 0.0;
-  s->rr = s->rr_new;
-}
 __global__ void k_scalars_init(Scal *s) {
   s->rr = s->rr_new;
   s->rr0 = s->rr_new;
 }
 
-// d += alpha p; r -= alpha q; partial sums of r.r
+// d += alpha p; r -= alpha q; r.r, then beta = r.r / rr and rr = r.r
 template <typename T>
-__global__ void __launch_bounds__(kT) k_cg_update(int64_t n, const Scal *sc, const T *p,
-                                                  const T *q, T *d, T *r, double *part) {
+__global__ void __launch_bounds__(kT) k_cg_update(int64_t n, Scal *sc, const T *p, const T *q,
+                                                  T *d, T *r, double *part, unsigned *ticket) {
   const T a = (T)sc->alpha;
   double s = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x; i < n; i += (int64_t)gridDim.x * kT) {
@@ -92,7 +131,12 @@ __global__ void __launch_bounds__(kT) k_cg_update(int64_t n, const Scal *sc, con
     s += (double)ri * (double)ri;
   }
   s = block_sum(s);
-  if (threadIdx.x == 0) part[blockIdx.x] = s;
+  double rr_new;
+  if (last_block_sum(s, part, ticket, &rr_new) && threadIdx.x == 0) {
+    sc->rr_new = rr_new;
+    sc->beta = (sc->rr != 0.0) ? rr_new / sc->rr : 0.0;
+    sc->rr = rr_new;
+  }
 }
 
 // p = r + beta p
@@ -156,7 +200,10 @@ spc5_status ircg(const spc5_matrix *A64, const spc5_matrix *Alo, const double *b
   Buf<double> r64, part, dev_nrm;
   Buf<T> rlo, p, q, d;
   Buf<Scal> sc;
+  Buf<unsigned> ticket;
   CK(r64.alloc(n), "alloc");
+  CK(ticket.alloc(1), "alloc");
+  CK(cudaMemsetAsync(ticket.p, 0, sizeof(unsigned), s), "zero ticket");
   CK(part.alloc(kRedBlocks), "alloc");
   CK(dev_nrm.alloc(2), "alloc");
   CK(rlo.alloc(n), "alloc");
@@ -190,12 +237,8 @@ spc5_status ircg(const spc5_matrix *A64, const spc5_matrix *Alo, const double *b
                               "begin capture");
   if (st == SPC5_OK) {
     spc5_status sst = spmv_device(Alo, p.p, q.p, 1.0, 0.0, cs);
-    k_dot_partial<T><<<kRedBlocks, kT, 0, cs>>>(n, p.p, q.p, part.p);
-    k_dot_final<<<1, kT, 0, cs>>>(part.p, kRedBlocks, &sc.p->pq);
-    k_scalars_alpha<<<1, 1, 0, cs>>>(sc.p);
-    k_cg_update<T><<<kRedBlocks, kT, 0, cs>>>(n, sc.p, p.p, q.p, d.p, rlo.p, part.p);
-    k_dot_final<<<1, kT, 0, cs>>>(part.p, kRedBlocks, &sc.p->rr_new);
-    k_scalars_beta<<<1, 1, 0, cs>>>(sc.p);
+    k_dot_alpha<T><<<kRedBlocks, kT, 0, cs>>>(n, p.p, q.p, part.p, ticket.p, sc.p);
+    k_cg_update<T><<<kRedBlocks, kT, 0, cs>>>(n, sc.p, p.p, q.p, d.p, rlo.p, part.p, ticket.p);
     k_cg_dir<T><<<g, kT, 0, cs>>>(n, sc.p, rlo.p, p.p);
     st = cuda_check(cudaStreamEndCapture(cs, &graph), "end capture");
     if (st == SPC5_OK && sst != SPC5_OK) st = sst;

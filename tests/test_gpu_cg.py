@@ -50,3 +50,24 @@ def test_ircg_zero_rhs_and_rejections():
     assert rep["outer_iters"] == 0 and float(dx.abs().max()) == 0.0
     with pytest.raises(spc5.SPC5Error):
         spc5.spc5_ircg(A32, A32, db, dx)  # the outer matrix must be FP64
+
+
+def test_ircg_is_deterministic():
+    """Two solves of one system give the same iterates bit for bit: every
+    reduction sums its per-block partials in block order (the last block to
+    finish does it), and the SpMV is deterministic."""
+    torch = torch_cuda()
+    A = synth.stencil27(30, 30, 30, values="poisson")
+    rp, ci, vv = to_device(A)
+    A64 = spc5.spc5_convert_csr(A.nrows, A.ncols, A.nnz, rp, ci, vv, r=4, c=8)
+    A32 = spc5.spc5_convert_csr(A.nrows, A.ncols, A.nnz, rp, ci, vv, store_dtype=spc5.SPC5_F32,
+                                r=4, c=8)
+    db = torch.from_numpy(synth.vector_uniform(A.nrows, seed=5)).cuda()
+    xs, reps = [], []
+    for _ in range(2):
+        dx = torch.zeros(A.nrows, dtype=torch.float64, device="cuda")
+        reps.append(spc5.spc5_ircg(A64, A32, db, dx, tol=1e-10, max_outer=30, inner_tol=1e-3,
+                                   max_inner=500))
+        xs.append(dx.cpu().numpy())
+    assert reps[0] == reps[1]
+    assert np.array_equal(xs[0], xs[1])
