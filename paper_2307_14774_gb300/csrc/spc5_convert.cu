@@ -449,8 +449,9 @@ __global__ void k_check_offsets(int64_t npanels, const int32_t *block_rowptr,
 // uniform rows: every matrix whose rows are not very long; the kernel comes
 // sized for panels of 1024 and of 2048 entries), one warp converts a whole
 // panel in shared memory, with the rule of the flat passes above: the
-// panel's columns merged in (column, row) order (a tree of pairwise merges
-// of the sorted rows), the union U without repeats, the greedy block starts
+// panel's columns merged in column order (a tree of pairwise merges of the
+// sorted rows, each split among the lanes by merge path), the union U
+// without repeats, the greedy block starts
 // over U (a ballot finds the first union column not covered by the previous
 // block, one step per block), then masks, the blocks' value offsets (prefix
 // sum of popcounts) and the value scatter.  One pass over the panels: a
@@ -572,47 +573,43 @@ __global__ void __launch_bounds__(32 * PanelWarps<CAP>::v)
     }
     // the panel's columns in (column, row) order: a tree of pairwise merges
     // of sorted runs (rows, then pairs of rows, ...) between the two column
-    // buffers.  At a level of runs of h rows, an entry of a left run moves
-    // to its group's start plus its index in its run plus the entries of
-    // the right run with a smaller column; an entry of a right run counts
-    // the left run's entries with a column not larger (a stable merge).
-    // The counts are branch-free binary searches with as many steps as the
-    // longest run has bits.
+    // buffers.  Each merge of two runs A and B is split into 32 equal
+    // pieces of its output (merge path): a lane finds how many of A's
+    // entries precede its piece by one binary search along the piece's
+    // diagonal (A's entry first on equal columns), then writes its piece
+    // by a sequential merge, one comparison per entry.
     int32_t *src = S.col, *dst = S.uni;
 #pragma unroll
     for (int h = 1; h < R; h <<= 1) {
-      int32_t longest = 0;
-#pragma unroll
-      for (int k = 0; k < R / h; ++k) longest = max(longest, ro[(k + 1) * h] - ro[k * h]);
-      const int steps = 32 - __clz(longest);
       __syncwarp();
-      for (int32_t t = lane; t < ne; t += 32) {
-        // the run of entry t: its start hs, its group's start gs, and the
-        // other run of the group [ss, se) (selects, no indexed registers)
-        bool left = true;
-        int32_t gs = ro[0], hs = ro[0], ss = ro[h], se = ro[2 * h];
 #pragma unroll
-        for (int kk = 1; kk < R / h; ++kk) {
-          if (t >= ro[kk * h]) {
-            left = (kk & 1) == 0;
-            hs = ro[kk * h];
-            gs = ro[(kk & ~1) * h];
-            ss = ro[(kk ^ 1) * h];
-            se = ro[((kk ^ 1) + 1) * h];
+      for (int g = 0; g < R / (2 * h); ++g) {
+        const int32_t a0 = ro[2 * g * h], b0 = ro[(2 * g + 1) * h], b1 = ro[(2 * g + 2) * h];
+        const int32_t na = b0 - a0, nb = b1 - b0, n = na + nb;
+        const int32_t K = (n + 31) >> 5;
+        const int32_t d = min(lane * K, n), dend = min(d + K, n);
+        int32_t lo = max(0, d - nb), hi = min(d, na);
+        while (lo < hi) {
+          const int32_t mid = (lo + hi) >> 1;
+          if (src[a0 + mid] <= src[b0 + d - mid - 1])
+            lo = mid + 1;
+          else
+            hi = mid;
+        }
+        int32_t i = lo, j = d - lo;
+        int32_t va = i < na ? src[a0 + i] : INT_MAX;
+        int32_t vb = j < nb ? src[b0 + j] : INT_MAX;
+        for (int32_t o = d; o < dend; ++o) {
+          const bool ta = va <= vb;
+          dst[a0 + o] = ta ? va : vb;
+          if (ta) {
+            ++i;
+            va = i < na ? src[a0 + i] : INT_MAX;
+          } else {
+            ++j;
+            vb = j < nb ? src[b0 + j] : INT_MAX;
           }
         }
-        const int32_t x = src[t];
-        int32_t base = ss, len = se - ss;
-        for (int s = 0; s < steps; ++s) {
-          if (len > 0) {
-            const int32_t half = len >> 1;
-            const int32_t v = src[base + half];
-            const bool before = left ? v < x : v <= x;
-            base = before ? base + half + 1 : base;
-            len = before ? len - half - 1 : half;
-          }
-        }
-        dst[gs + (t - hs) + (base - ss)] = x;
       }
       int32_t *tmp = src;
       src = dst;
