@@ -612,9 +612,11 @@ spc5_status plan_flat(spc5_matrix *A, const int32_t *boff, cudaStream_t s,
   A->flat = A->kernel == 0 ? flat : 0;
   const bool expanded = A->flat == 2;
 
+  if (A->flat == 0) return SPC5_OK;  // row groups or staged: no second tile set
+
   int32_t counts[3] = {0, 0, 0};
   Tmp<int32_t> bpanel(s), pf(s), pscan(s), tc(s), lf(s), tbase(s), lbase(s), tmp(s);
-  if (!expanded) {  // block-balanced tiles (also built, unused, for row groups)
+  if (!expanded) {  // block-balanced tiles
     int dev = 0, sms = 1;
     CK(cudaGetDevice(&dev), "cudaGetDevice");
     CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "sm count");
