@@ -447,7 +447,7 @@ __global__ void k_check_offsets(int64_t npanels, const int32_t *block_rowptr,
 //
 // When no panel holds more than kPanelCap entries (stencils, FEM meshes,
 // uniform rows: every matrix whose rows are not very long; the kernel comes
-// sized for panels of 1024 and of 2048 entries), one warp converts a whole
+// sized for panels of 256, 1024 and 2048 entries), one warp converts a whole
 // panel in shared memory, with the rule of the flat passes above: the
 // panel's columns merged in column order (a tree of pairwise merges of the
 // sorted rows, each split among the lanes by merge path), the union U
@@ -461,7 +461,7 @@ __global__ void k_check_offsets(int64_t npanels, const int32_t *block_rowptr,
 // arrays at e0, with the panel's block count.  A prefix sum of the counts
 // then places every panel's blocks, and a compaction copies them there.
 // The values are read once, the columns once (twice for r >= 4).
-constexpr int kPanelCap = 2048;      // entries of a panel (two capacities: 1024, 2048)
+constexpr int kPanelCap = 2048;      // entries of a panel (capacities 256, 1024, 2048)
 constexpr int kPanelBlockCap = 256;  // blocks of a panel
 
 // Shared memory of one warp for panels of at most CAP entries.
@@ -474,11 +474,14 @@ struct PanelSmem {
   uint32_t bmask[kPanelBlockCap];    // block masks
   int32_t boffs[kPanelBlockCap];     // block value offsets in the panel
 };
-// Warps per CTA: 33 KB of shared memory per CTA at CAP = 1024, 19 KB at
-// CAP = 2048 (panels of 1024 to 2048 entries, FEM beta(8,4)).
+// Warps per CTA: 40 KB of shared memory per CTA at CAP = 256 (four CTAs of
+// eight warps per SM, registers capped for that), 33 KB at CAP = 1024 (six
+// CTAs of three), 19 KB at CAP = 2048 (eleven CTAs of one).  Smaller panels
+// leave room for more warps, which hide more of the searches' latency.
 template <int CAP>
 struct PanelWarps {
-  static constexpr int v = CAP <= 1024 ? 3 : 1;
+  static constexpr int v = CAP <= 256 ? 8 : (CAP <= 1024 ? 3 : 1);
+  static constexpr int per_sm = CAP <= 256 ? 4 : (CAP <= 1024 ? 6 : 11);
 };
 
 // Row q of panel entry t (ro[q] <= t < ro[q + 1]) and ro[q].
@@ -518,7 +521,7 @@ __global__ void k_panel_max_entries(int64_t np, int64_t nrows, int r, const int3
 // of more than kPanelBlockCap blocks raises err[1] to its count and is left
 // out (the host then takes the flat passes).
 template <int CAP, int R, typename Store>
-__global__ void __launch_bounds__(32 * PanelWarps<CAP>::v)
+__global__ void __launch_bounds__(32 * PanelWarps<CAP>::v, CAP <= 256 ? PanelWarps<CAP>::per_sm : 1)
     k_panel_convert(int64_t np, int64_t nrows, int64_t ncols, int r, int c,
                     const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
                     const double *__restrict__ vals, int32_t *cnt, int32_t *tcol,
@@ -618,9 +621,11 @@ __global__ void __launch_bounds__(32 * PanelWarps<CAP>::v)
     __syncwarp();
     // the union U: the merged columns without repeats, into uni (in place
     // when the merge ended there: the previous chunk's last column is kept
-    // in a register, so no lane reads a slot already rewritten)
-    int32_t nu = 0, last = -1;
-    for (int32_t base = 0; base < ne; base += 32) {
+    // in a register, so no lane reads a slot already rewritten).  One row
+    // (r = 1) is its own union: U is the row's columns, left in col.
+    const int32_t *U = R == 1 ? S.col : S.uni;
+    int32_t nu = R == 1 ? ne : 0, last = -1;
+    for (int32_t base = 0; base < (R == 1 ? 0 : ne); base += 32) {
       const bool in = base + lane < ne;
       const int32_t v = in ? src[base + lane] : -1;
       int32_t prev = __shfl_up_sync(0xffffffffu, v, 1);
@@ -633,20 +638,25 @@ __global__ void __launch_bounds__(32 * PanelWarps<CAP>::v)
       nu += __popc(ball);
       __syncwarp();
     }
-    // greedy block starts: the first union column not covered opens a block
+    // greedy block starts: the first union column not covered opens a block.
+    // For r = 1 every union column is an entry, and its block (the last
+    // start opened at or before it) goes to uni for the masks and the scatter
     int32_t nbk = 0;
     long long thr = LLONG_MIN;
     for (int32_t base = 0; base < nu; base += 32) {
       const bool in = base + lane < nu;
-      const int32_t u = in ? S.uni[base + lane] : 0;
+      const int32_t u = in ? U[base + lane] : 0;
+      int32_t mine = nbk - 1;
       while (true) {
         const uint32_t ball = __ballot_sync(0xffffffffu, in && (long long)u >= thr);
         if (!ball) break;
         const int32_t sb = __shfl_sync(0xffffffffu, u, __ffs(ball) - 1);
         if (lane == 0 && nbk < kPanelBlockCap) S.bst[nbk] = sb;
+        if (u >= sb) mine = nbk;
         ++nbk;
         thr = (long long)sb + c;
       }
+      if (R == 1 && in) S.uni[base + lane] = mine;
     }
     if (lane == 0) cnt[p] = nbk;
     if (nbk > kPanelBlockCap) {
@@ -679,12 +689,13 @@ __global__ void __launch_bounds__(32 * PanelWarps<CAP>::v)
     // masks: an entry's block is the last start not after its column (the
     // columns are checked, so every entry lies in [bst[b], bst[b] + c));
     // kept per entry for the value scatter (the union is no longer needed)
-    const int bsteps = 32 - __clz(nbk);
+    const int bsteps = R == 1 ? 0 : 32 - __clz(nbk);
     for (int32_t t = lane; t < ne; t += 32) {
       int32_t st;
       const int q = panel_row<R>(t, ro, nr, &st);
       const int32_t x = S.col[t];
-      int32_t b = 0, len = nbk;  // first start > x, by branch-free halving
+      int32_t b = R == 1 ? S.uni[t] + 1 : 0, len = nbk;  // first start > x, by
+                                                        // branch-free halving
       for (int s = 0; s < bsteps; ++s) {
         if (len > 0) {
           const int32_t half = len >> 1;
@@ -859,9 +870,9 @@ spc5_status convert_panels(spc5_matrix *A, const int32_t *rowptr, const int32_t 
   const int64_t n = A->nrows, np = A->npanels, nnz = A->nnz;
   const int r = A->r, c = A->c;
   const int mask_bytes = r * c / 8;
-  // the CTAs of 19 to 33 KB that one SM holds
+  // the CTAs of 19 to 40 KB that one SM holds
   constexpr int kW = PanelWarps<CAP>::v;
-  constexpr int kCtas = CAP <= 1024 ? 6 : 11;
+  constexpr int kCtas = PanelWarps<CAP>::per_sm;
   const unsigned grid = (unsigned)std::min<int64_t>(std::max<int64_t>((np + kW - 1) / kW, 1),
                                                     (int64_t)device_sm_count() * kCtas);
   DevBuf<int32_t> cnt(s), scan_tmp(s), tcol(s), tboff(s);
@@ -978,9 +989,11 @@ spc5_status convert_device(spc5_matrix *A, const int32_t *rowptr, const int32_t 
         CK(cudaMemsetAsync(err.p + 1, 0, sizeof(uint32_t), s), "memset");
         bool flat = false;
         spc5_status st =
-            (int32_t)h[1] <= 1024
-                ? convert_panels<1024>(A, rowptr, colidx, vals, err.p, s, &flat)
-                : convert_panels<2048>(A, rowptr, colidx, vals, err.p, s, &flat);
+            (int32_t)h[1] <= 256
+                ? convert_panels<256>(A, rowptr, colidx, vals, err.p, s, &flat)
+                : (int32_t)h[1] <= 1024
+                      ? convert_panels<1024>(A, rowptr, colidx, vals, err.p, s, &flat)
+                      : convert_panels<2048>(A, rowptr, colidx, vals, err.p, s, &flat);
         if (st != SPC5_OK || !flat) return st;
       }
     }
