@@ -447,8 +447,16 @@ __global__ void k_group_efficiency(const Tile *tiles, int64_t ntiles, const int3
       slots += (int64_t)per_round * ((mx + G - 1) / G);
     }
   }
-  atomicAdd(&acc[0], used);
-  atomicAdd(&acc[1], slots);
+  // one atomic per warp: same-address atomics from every thread were most
+  // of this kernel's time
+  for (int o = 16; o > 0; o >>= 1) {
+    used += __shfl_xor_sync(0xffffffffu, used, o);
+    slots += __shfl_xor_sync(0xffffffffu, slots, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(&acc[0], used);
+    atomicAdd(&acc[1], slots);
+  }
 }
 
 template <typename T>
