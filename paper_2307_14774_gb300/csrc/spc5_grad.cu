@@ -132,12 +132,13 @@ __global__ void __launch_bounds__(kThreads)
                   const typename MaskType<R, C>::T *__restrict__ masks,
                   const int32_t *__restrict__ value_src, const int32_t *__restrict__ csr_rowptr,
                   const AT *__restrict__ g, const AT *__restrict__ x, AT *__restrict__ dvals,
-                  AT alpha, int64_t nrows) {
+                  AT alpha, int64_t nrows, bool pieces_only) {
   const int lane = threadIdx.x & 31;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < ntiles;
        t += nwarps) {
     const Tile cur = tiles[t];
+    if (pieces_only && !(cur.mode & kPartial)) continue;
     if ((cur.mode & kPartial) || !csr_rowptr) {  // a piece of a long panel: its rows'
                                                  // earlier values are in other tiles, so
                                                  // the positions come from value_src
@@ -163,6 +164,52 @@ __global__ void __launch_bounds__(kThreads)
                               }
                             });
     }
+  }
+}
+
+// Values gradient by panels: one warp per panel, 32 / r lanes per row (a
+// segment tile of the whole panel), so a row's lanes take consecutive
+// blocks and write a contiguous run of the row's CSR entries per round,
+// where the row-group tiles (one lane per row) write 32 scattered rows.
+// Panels cut into pieces (listed, ascending, in long_panels) are left to
+// the piece tiles of k_values_grad.
+template <int R, int C, typename AT>
+__global__ void __launch_bounds__(kThreads)
+    k_values_grad_panels(int64_t npanels, const int32_t *__restrict__ brp,
+                         const int32_t *__restrict__ vptr, const int32_t *__restrict__ bcol,
+                         const typename MaskType<R, C>::T *__restrict__ masks,
+                         const int32_t *__restrict__ long_panels, int64_t nlong,
+                         const int32_t *__restrict__ csr_rowptr, const AT *__restrict__ g,
+                         const AT *__restrict__ x, AT *__restrict__ dvals, AT alpha,
+                         int64_t nrows) {
+  constexpr int kLog2G = 5 - Log2<R>::v;
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; p < npanels;
+       p += nwarps) {
+    if (nlong > 0) {  // is p cut into pieces?
+      int64_t lo = 0, hi = nlong;
+      while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (long_panels[mid] < p)
+          lo = mid + 1;
+        else
+          hi = mid;
+      }
+      if (lo < nlong && long_panels[lo] == p) continue;
+    }
+    const Tile cur{(int32_t)p, (int32_t)p + 1, brp[p], brp[p + 1], vptr[p], vptr[p + 1], 0,
+                   kSegment | kLog2G};
+    walk_tile<R, C, true>(cur, lane, brp, vptr, bcol, masks, nrows,
+                          [&](int64_t row, int32_t col, uint32_t mq, int32_t, int32_t rc) {
+                            const AT gr = alpha * g[row];
+                            AT *dst = dvals + csr_rowptr[row] + rc;
+                            while (mq) {
+                              const int k = __ffs(mq) - 1;
+                              mq &= mq - 1u;
+                              *dst++ = gr * x[col + k];
+                            }
+                          });
   }
 }
 
@@ -223,11 +270,17 @@ template <int R, int C, typename AT>
 cudaError_t run_grad(const spc5_matrix *A, const void *g, const void *x, void *dvals,
                      double alpha, cudaStream_t s) {
   using MT = typename MaskType<R, C>::T;
-  if (A->ntiles > 0)
+  const bool by_panels = A->csr_rowptr != nullptr;
+  if (by_panels && A->npanels > 0)
+    k_values_grad_panels<R, C, AT><<<tile_grid(A->npanels), kThreads, 0, s>>>(
+        A->npanels, A->block_rowptr, A->panel_vptr, A->block_colidx, (const MT *)A->masks,
+        A->long_panels, A->nlong, A->csr_rowptr, (const AT *)g, (const AT *)x, (AT *)dvals,
+        (AT)alpha, A->nrows);
+  if (A->ntiles > 0 && (!by_panels || A->nlong > 0))
     k_values_grad<R, C, AT><<<tile_grid(A->ntiles), kThreads, 0, s>>>(
         A->tiles, A->ntiles, A->block_rowptr, A->panel_vptr, A->block_colidx,
         (const MT *)A->masks, A->value_src, A->csr_rowptr, (const AT *)g, (const AT *)x,
-        (AT *)dvals, (AT)alpha, A->nrows);
+        (AT *)dvals, (AT)alpha, A->nrows, by_panels);
   return cudaGetLastError();
 }
 
