@@ -136,11 +136,11 @@ typedef struct {
  * the device before any index is trusted.  Explicitly stored zeros are kept.
  *
  * Memory: besides the handle's arrays, a conversion takes temporary scratch
- * (about 12 bytes per entry) from a private stream-ordered memory pool of
- * the device.  The pool keeps up to 8 GiB of it mapped between calls, so
- * that later conversions skip the mapping; the process holds that memory
- * until it exits, and anything above 8 GiB is returned at the next
- * synchronisation.
+ * (about 12 bytes per entry, more for very long rows) from a private
+ * stream-ordered memory pool of the device.  The pool keeps up to 8 GiB of
+ * it mapped between calls, so that later conversions skip the mapping; the
+ * process holds that memory until it exits, and anything above 8 GiB is
+ * returned at the next synchronisation.
  */
 spc5_status spc5_convert_csr(int64_t nrows, int64_t ncols, int64_t nnz, const int32_t *rowptr,
                              const int32_t *colidx, const void *vals, spc5_dtype vals_dtype,
