@@ -688,25 +688,42 @@ __global__ void __launch_bounds__(32 * PanelWarps<CAP>::v, CAP <= 256 ? PanelWar
     __syncwarp();
     // masks: an entry's block is the last start not after its column (the
     // columns are checked, so every entry lies in [bst[b], bst[b] + c));
-    // kept per entry for the value scatter (the union is no longer needed)
-    const int bsteps = R == 1 ? 0 : 32 - __clz(nbk);
-    for (int32_t t = lane; t < ne; t += 32) {
-      int32_t st;
-      const int q = panel_row<R>(t, ro, nr, &st);
-      const int32_t x = S.col[t];
-      int32_t b = R == 1 ? S.uni[t] + 1 : 0, len = nbk;  // first start > x, by
-                                                        // branch-free halving
-      for (int s = 0; s < bsteps; ++s) {
-        if (len > 0) {
-          const int32_t half = len >> 1;
-          const bool le = S.bst[b + half] <= x;
-          b = le ? b + half + 1 : b;
-          len = le ? len - half - 1 : half;
+    // kept per entry for the value scatter (the union is no longer needed).
+    // Each lane takes a contiguous run of entries: within a row the columns
+    // and so the blocks ascend, so the lane finds a row's first block by a
+    // binary search and then steps forward (for r = 1 the greedy pass has
+    // recorded every entry's block)
+    {
+      const int32_t K = (ne + 31) >> 5;
+      const int32_t t0 = min(lane * K, ne), t1 = min(t0 + K, ne);
+      int32_t b = 0, rowend = -1;
+      int q = 0;
+      for (int32_t t = t0; t < t1; ++t) {
+        const int32_t x = S.col[t];
+        if (R == 1) {
+          b = S.uni[t];
+        } else if (t >= rowend) {  // first entry of the run, or a new row
+          int32_t st;
+          q = panel_row<R>(t, ro, nr, &st);
+#pragma unroll
+          for (int qq = 0; qq < R; ++qq)
+            if (qq == q) rowend = ro[qq + 1];
+          int32_t lo = 0, hi = nbk;  // first start > x
+          while (lo < hi) {
+            const int32_t mid = (lo + hi) >> 1;
+            if (S.bst[mid] <= x)
+              lo = mid + 1;
+            else
+              hi = mid;
+          }
+          b = lo - 1;
+          S.uni[t] = b;
+        } else {
+          while (b + 1 < nbk && S.bst[b + 1] <= x) ++b;
+          S.uni[t] = b;
         }
+        atomicOr(&S.bmask[b], 1u << (q * c + (x - S.bst[b])));
       }
-      --b;
-      S.uni[t] = b;
-      atomicOr(&S.bmask[b], 1u << (q * c + (x - S.bst[b])));
     }
     __syncwarp();
     // the blocks' value offsets: exclusive prefix of the popcounts
