@@ -121,6 +121,13 @@ __global__ void k_mark_panels(PlanParams P, int32_t *mark) {
   }
 }
 
+// *flag = 1 if some panel is cut into pieces (set to 0 beforehand).
+__global__ void k_any_long(PlanParams P, int32_t *flag) {
+  GRID_STRIDE(p, P.npanels) {
+    if (panel_long(P, p)) *flag = 1;
+  }
+}
+
 // Piece starts inside long panels.
 __global__ void k_piece_flags(PlanParams P, const int32_t *bpanel, const int32_t *boff,
                               int32_t *pf) {
@@ -827,17 +834,29 @@ spc5_status plan_tiles(spc5_matrix *A, const uint32_t *mask32, const int32_t *bo
   CK(tbase.alloc(np + 1), "alloc");
   CK(lbase.alloc(np + 1), "alloc");
   CK(tmp.alloc(scan_tmp_elems(std::max<int64_t>(nb, np) + 1)), "alloc");
-  if (nb > 0) {
+  // The block-level passes (each block's panel, piece starts and their
+  // prefix sum) only serve panels cut into pieces: without any (stencils,
+  // FEM meshes, uniform rows) the piece prefix is all zeros.
+  int32_t any_long = 0;
+  if (nb > 0 && np > 0) {
+    CK(cudaMemsetAsync(tc.p, 0, sizeof(int32_t), s), "memset");
+    k_any_long<<<grid_for(np), kThreads, 0, s>>>(P, tc.p);
+    CK(cudaMemcpyAsync(&any_long, tc.p, sizeof(int32_t), cudaMemcpyDeviceToHost, s), "rd");
+    CK(cudaStreamSynchronize(s), "sync long panels");
+  }
+  if (any_long) {
     CK(cudaMemsetAsync(bpanel.p, 0, (size_t)nb * sizeof(int32_t), s), "memset");
     if (np > 1) k_mark_panels<<<grid_for(np), kThreads, 0, s>>>(P, bpanel.p);
     CK(device_scan<int32_t>(nb, ReadI32{bpanel.p}, WriteI32{bpanel.p}, AddI32{}, 0, true, tmp.p,
                             s),
        "scan panels");
     k_piece_flags<<<grid_for(nb), kThreads, 0, s>>>(P, bpanel.p, boff, pf.p);
+    CK(device_scan<int32_t>(nb + 1, ReadI32Pad{pf.p, nb}, WriteI32{pscan.p}, AddI32{}, 0, false,
+                            tmp.p, s),
+       "scan pieces");
+  } else {
+    CK(cudaMemsetAsync(pscan.p, 0, (size_t)(nb + 1) * sizeof(int32_t), s), "zero pieces");
   }
-  CK(device_scan<int32_t>(nb + 1, ReadI32Pad{pf.p, nb}, WriteI32{pscan.p}, AddI32{}, 0, false,
-                          tmp.p, s),
-     "scan pieces");
   k_tile_counts<<<grid_for(np), kThreads, 0, s>>>(P, pscan.p, tc.p, lf.p);
   CK(device_scan<int32_t>(np + 1, ReadI32Pad{tc.p, np}, WriteI32{tbase.p}, AddI32{}, 0, false,
                           tmp.p, s),
